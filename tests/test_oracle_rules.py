@@ -1,0 +1,174 @@
+"""Pins for the oracle's quadrature rules and modified moments (CPU).
+
+Independent references: high-order Gauss integration of piecewise
+polynomials, adaptive quadrature (scipy QUADPACK) of the log-singular
+moments, the paper's own recurrence (eq. recIq) at small sizes, closed-form
+log integrals of monomials, and the closed-form benchmark of eq. testdiff.
+"""
+import json
+import os
+from math import comb
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+
+from oracle import rules
+from oracle.discretization import Discretization
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gauss_exact_products(disc, g=12):
+    """int_I B-bar_j B_i for all (j, i) with a high-order composite Gauss rule."""
+    t, w = disc.fine_gauss(g)
+    return disc.fine_basis(t)[0] @ (w[:, None] * disc.test_basis(t)[0].T)
+
+
+@pytest.mark.parametrize("closed", [True, False])
+@pytest.mark.parametrize("d,nh,nref", [(2, 10, 1), (3, 8, 2), (4, 9, 2), (5, 8, 1)])
+def test_regular_rules_exact_on_whole_exactness_space(closed, d, nh, nref):
+    """Eq. reg_exactness for every j (the j outside J^(i) are exact too)."""
+    disc = Discretization(0.0, 1.0, nh, d, nref, closed)
+    W = rules.regular_rules(disc)
+    lhs = disc.collocation() @ W
+    ref = _gauss_exact_products(disc)
+    assert np.max(np.abs(lhs - ref)) < 1e-13 * max(1.0, np.max(np.abs(ref))) * 10
+
+
+@pytest.mark.parametrize("closed", [True, False])
+def test_regular_rules_minimum_norm_and_support(closed):
+    disc = Discretization(0.0, 1.0, 9, 3, 2, closed)
+    W = rules.regular_rules(disc)
+    Bc = disc.collocation()
+    for i in range(disc.n):
+        Ni = disc.support_nodes(i)
+        outside = np.setdiff1d(np.arange(disc.Nq), Ni)
+        assert np.all(W[outside, i] == 0.0)
+        # the minimum-norm solution lies in the row space of the local matrix
+        Bi = Bc[np.ix_(disc.overlapping_fine(i), Ni)]
+        y, *_ = np.linalg.lstsq(Bi.T, W[Ni, i], rcond=None)
+        np.testing.assert_allclose(Bi.T @ y, W[Ni, i], atol=1e-12)
+
+
+def test_rules_do_not_depend_on_exactness_basis():
+    """Clamped and uniform-extended bases span the same exactness space, so the
+    minimum-norm rules (regular and singular) must coincide."""
+    a = Discretization(0.0, 1.0, 10, 3, 2, True)
+    b = Discretization(0.0, 1.0, 10, 3, 2, True)
+    d, M = 3, b.M
+    b.fine_knots = np.concatenate([[0.0] * d, b.hf * np.arange(M + 1), [1.0] * d])
+    b.fine_knots[d + M] = 1.0
+    np.testing.assert_allclose(rules.regular_rules(a), rules.regular_rules(b), atol=1e-12)
+    np.testing.assert_allclose(rules.singular_rules(a), rules.singular_rules(b), atol=1e-12)
+
+
+def _k2(disc, s, t):
+    v = np.log(np.abs(t - s))
+    if disc.closed:
+        L = disc.L
+        v = v + np.log(np.abs(t - s + L)) + np.log(np.abs(t - s - L)) - 2 * np.log(L)
+    return v
+
+
+@pytest.mark.parametrize("closed", [True, False])
+def test_moments_against_adaptive_quadrature(closed):
+    disc = Discretization(0.0, 1.0, 6, 3, 2, closed)
+    rng = np.random.default_rng(1)
+    s = np.concatenate([disc.eta[[0, 1, 5, 12, disc.Nq - 1]], rng.uniform(0, 1, 3)])
+    mu = rules.moments(disc, s)
+    for p, sp in enumerate(s):
+        for j in range(disc.NE):
+            lo = max(disc.fine_knots[j], 0.0)
+            hi = min(disc.fine_knots[j + disc.d + 1], 1.0)
+            pts = [x for x in list(disc.fine_knots) + [sp, sp - 1, sp + 1] if lo < x < hi]
+            f = lambda t: disc.fine_basis(np.array([t]))[0][j, 0] * _k2(disc, sp, t)
+            ref, err = quad(f, lo, hi, points=sorted(set(pts)) or None, limit=400,
+                            epsabs=1e-14, epsrel=1e-13)
+            assert abs(mu[p, j] - ref) < 2e-12, (p, j, mu[p, j], ref)
+
+
+def _recurrence_moments(knots, d, s, a, b):
+    """The paper's recurrence eq. recIq in absolute powers of t, started from
+    the closed-form base integrals (Sect. 4.2)."""
+    def F(z, j):
+        return 0.0 if z == 0 else z ** (j + 1) / (j + 1) * (np.log(abs(z)) - 1.0 / (j + 1))
+    nb0 = len(knots) - 1
+    I = {}
+    for i in range(nb0):
+        ti, ti1 = knots[i], knots[i + 1]
+        for k in range(d + 1):
+            if ti < ti1 and ti >= a - 1e-15 and ti1 <= b + 1e-15:
+                I[(i, 0, k)] = sum(comb(k, j) * s ** (k - j) * (F(ti1 - s, j) - F(ti - s, j))
+                                   for j in range(k + 1))
+            else:
+                I[(i, 0, k)] = 0.0
+    for r in range(1, d + 1):
+        for i in range(nb0 - r):
+            for q in range(d + 1 - r):
+                v = 0.0
+                if knots[i + r] > knots[i]:
+                    v += (I[(i, r - 1, q + 1)] - knots[i] * I[(i, r - 1, q)]) / (knots[i + r] - knots[i])
+                if knots[i + r + 1] > knots[i + 1]:
+                    v += (knots[i + r + 1] * I[(i + 1, r - 1, q)] - I[(i + 1, r - 1, q + 1)]) / \
+                        (knots[i + r + 1] - knots[i + 1])
+                I[(i, r, q)] = v
+    return np.array([I[(j, d, 0)] for j in range(nb0 - d)])
+
+
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_moments_against_paper_recurrence(d):
+    """Open arc on [-1, 1] (the setting of Table 1): the oracle's stable
+    element-local evaluation agrees with eq. recIq where the latter is still
+    accurate (small N_h)."""
+    disc = Discretization(-1.0, 1.0, 8, d, 1, False)
+    mu = rules.moments(disc, disc.eta)
+    for m, s in enumerate(disc.eta):
+        rec = _recurrence_moments(disc.fine_knots, d, s, -1.0, 1.0)
+        np.testing.assert_allclose(mu[m], rec, atol=1e-11)
+
+
+def _log_monomial(s, k, a, b):
+    """int_a^b t^k ln|t - s| dt in closed form (binomial expansion in z = t - s)."""
+    def F(z, j):
+        return 0.0 if z == 0 else z ** (j + 1) / (j + 1) * (np.log(abs(z)) - 1.0 / (j + 1))
+    return sum(comb(k, j) * s ** (k - j) * (F(b - s, j) - F(a - s, j)) for j in range(k + 1))
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 5])
+def test_singular_rules_exact_for_monomials(d):
+    """Sect. 4.2, test 1: the monomials up to t^d are integrated exactly against ln|t - s|."""
+    disc = Discretization(-1.0, 1.0, 10, d, 1, False)
+    Ws = rules.singular_rules(disc)
+    for k in range(d + 1):
+        ref = np.array([_log_monomial(s, k, -1.0, 1.0) for s in disc.eta])
+        np.testing.assert_allclose(Ws @ disc.eta ** k, ref, atol=5e-13)
+
+
+def test_singular_rules_match_dense_minimum_norm():
+    disc = Discretization(0.0, 1.0, 8, 3, 2, True)
+    Ws = rules.singular_rules(disc)
+    Bc = disc.collocation()
+    Mu = rules.moments(disc, disc.eta)
+    dense = np.linalg.lstsq(Bc, Mu.T, rcond=None)[0].T           # minimum-norm, SVD
+    np.testing.assert_allclose(Ws, dense, atol=1e-12)
+    np.testing.assert_allclose(Ws @ Bc.T, Mu, atol=1e-13)
+
+
+def test_table1_testdiff_error_decreases_and_is_below_printed_values():
+    """Sect. 4.2, test 3 (eq. testdiff): the error of the singular rule on
+    sqrt(1-t^2)/(t^2+25) decreases monotonically with N_h.  Table 1 prints
+    ERR for this integrand; the knot vector and N_ref behind those numbers are
+    not stated, so they serve as an upper bound only."""
+    with open(os.path.join(GOLDEN, "table1_err_testdiff.json")) as fh:
+        tab = json.load(fh)
+    v = lambda t: np.sqrt(np.maximum(1 - t * t, 0)) / (t * t + 25)
+    exact = lambda s: np.pi * np.log(2) + np.pi * np.sqrt(26) / 5 * np.log(np.sqrt(25 + s * s) / (5 + np.sqrt(26)))
+    for d in (2, 3):
+        errs = []
+        for nh in tab["N_h"][:3]:
+            disc = Discretization(-1.0, 1.0, nh, d, 1, False)
+            Q = rules.singular_rules(disc) @ v(disc.eta)
+            errs.append(np.sum((Q - exact(disc.eta)) ** 2) / np.sum(Q ** 2))
+        assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:]))
+        assert all(e <= p for e, p in zip(errs, tab["ERR"][str(d)]))
