@@ -1,0 +1,194 @@
+/*
+ * igs.h -- C ABI of the GB300 IgA-SGBEM assembly and solve library.
+ *
+ * The library assembles and solves the symmetric Galerkin system A alpha = beta
+ * of the 2D Laplace Dirichlet problem on a spline / NURBS boundary curve by the
+ * weighted-quadrature method of Aimi, Calabro, Diligenti, Sampoli, Sangalli,
+ * Sestini, "Efficient assembly based on B-spline tailored quadrature rules for
+ * the IgA-SGBEM" (arXiv:1703.10016):
+ *
+ *   A_ij = -(1/2pi) int_I B_i(s) J(s) int_I ln|f(s)-f(t)| B_j(t) J(t) dt ds     (Sect. 3.1, eq. final_1)
+ *
+ * split as ln|f(s)-f(t)| = K1(s,t) + K2(s,t) (Sect. 3.1), with K1 integrated by
+ * the regular weighted rules of Algorithm 1 in both variables (eq. IK1e2) and K2
+ * by the regular outer rule and the singular (modified-moment) inner rules of
+ * Algorithm 2 (eq. IK1e2_bis).  For closed curves K2 is the periodic three-image
+ * logarithm ln|x| + ln|x+L| + ln|x-L| - 2 ln L, x = t - s, L = |I|.
+ *
+ * Conventions common to every entry point
+ *   - Return value: IGS_OK (0) or a negative IGS_E_* code.  No C++ exception
+ *     crosses the ABI.  igs_last_error() returns a message for the most recent
+ *     failure on the calling thread.
+ *   - Input arrays are copied during the call; the caller keeps ownership.
+ *     Output arrays are caller-provided.  Handles, rules, factors and device
+ *     work buffers are owned by the library and released by igs_destroy_*.
+ *   - "HOST" pointers are ordinary host memory (pageable or pinned); "DEVICE"
+ *     pointers are device memory on the context's GPU.
+ *   - All device work is issued on the context's stream (borrowed if the caller
+ *     passed one).  Every entry point returns after its results are complete
+ *     in the caller's buffers (the call synchronises the stream when it must
+ *     hand data back to the host, and otherwise records completion on the stream:
+ *     device outputs are valid for later work on the same stream).
+ *   - Calls on one problem handle must be serialised by the caller; distinct
+ *     problems may be used from distinct threads only with distinct contexts.
+ */
+#ifndef IGS_H
+#define IGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define IGS_OK                   0
+#define IGS_E_INVALID_ARG       -1   /* bad size, pointer, knot vector, degree ... */
+#define IGS_E_NO_MEMORY         -2   /* device or host allocation failed          */
+#define IGS_E_CUDA              -3   /* a CUDA runtime call failed                */
+#define IGS_E_NOT_SPD           -4   /* Cholesky met a non-positive pivot         */
+#define IGS_E_NOT_CONVERGED     -5   /* iterative refinement missed its tolerance */
+#define IGS_E_TIMEOUT           -6   /* a bounded device wait gave up             */
+#define IGS_E_ADMISSION_REFUSED -7   /* request does not fit the memory budget    */
+#define IGS_E_STATE             -8   /* call out of order (e.g. solve before assemble) */
+
+/* precision tiers */
+#define IGS_FP64   0   /* every step in FP64                                                    */
+#define IGS_MIXED  1   /* kernel evaluation + contraction in FP32 (float-float node differences),
+                          rules and moments in FP64; FP32 Cholesky + FP64 iterative refinement   */
+
+/* memory kinds / element types of caller buffers */
+#define IGS_MEM_HOST    0
+#define IGS_MEM_DEVICE  1
+#define IGS_F64         0
+#define IGS_F32         1
+
+typedef struct igs_ctx_s*  igs_ctx;
+typedef struct igs_geom_s* igs_geom;
+typedef struct igs_prob_s* igs_prob;
+
+/* Sizes of a problem (all counts are of the paper's Sect. 3-4 objects). */
+typedef struct igs_info {
+    int32_t n;          /* N_DoF: number of test/trial functions (closed: N_h)            */
+    int32_t degree;     /* d: degree of the discretisation and exactness spaces           */
+    int32_t n_elems;    /* N_h: uniform elements of the discretisation                    */
+    int32_t n_ref;      /* N_ref: refinement of the exactness space (Sect. 4)             */
+    int32_t n_quad;     /* N_quad = 2d + 2 N_ref N_h - 1 nodes eta (Sect. 4)              */
+    int32_t n_exact;    /* N_E = N_ref N_h + d exactness functions (Sect. 4)              */
+    int32_t n_rhs_pts;  /* N_quad + N_GQ points where u_D is sampled (igs_rhs_points)     */
+    int32_t closed;     /* 1 for a closed curve (interior problem), 0 for an open arc     */
+    int32_t precision;  /* IGS_FP64 or IGS_MIXED                                          */
+    int32_t rules_ready, assembled, factored;
+    int64_t device_bytes; /* device memory currently held by the problem                  */
+} igs_info;
+
+/* Per-phase device times of the most recent calls on a problem (milliseconds,
+ * CUDA events on the context stream); 0 for phases not run. */
+typedef struct igs_timing {
+    float rules_ms, geometry_ms, assemble_ms, rhs_ms, factor_ms, solve_ms;
+    int32_t ir_iterations;
+    int32_t kernel_launches;   /* library kernels launched by the most recent call */
+} igs_timing;
+
+/* ----------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to borrow (NULL: the library creates and owns one).  Errors: INVALID_ARG
+ * (bad device), CUDA. */
+int igs_create(igs_ctx* out, int device, void* cuda_stream);
+
+/* Release the context.  Geometries and problems created from it must have
+ * been destroyed first (else IGS_E_STATE). */
+int igs_destroy(igs_ctx ctx);
+
+/* Message of the last failing call on this thread ("" if none).  The string
+ * is owned by the library and valid until the next call on this thread. */
+const char* igs_last_error(void);
+
+/* ---------------------------------------------------------------- geometry */
+
+/* Boundary curve f(s) = sum_i Q_i R_i(s) (Sect. 3): a degree-`degree` B-spline
+ * (weights == NULL) or NURBS (weights[n_ctrl] > 0) on the extended knot vector
+ * knots[n_knots], n_knots = n_ctrl + degree + 1, non-decreasing; the parameter
+ * interval is I = [knots[degree], knots[n_ctrl]].  ctrl_xy is row-major
+ * n_ctrl x 2 (x, y).  closed = 1 declares a closed curve (f(a) = f(b); closed
+ * curves must be at least C^1 across the seam and oriented counter-clockwise;
+ * the periodic convention of Sect. 3 repeats the first `degree` control points
+ * at the end, a clamped closed curve repeats the first point).  All arrays are
+ * HOST memory and copied.  Errors: INVALID_ARG. */
+int igs_create_geometry(igs_ctx ctx, igs_geom* out, int degree, const double* knots, int n_knots,
+                        const double* ctrl_xy, const double* weights, int n_ctrl, int closed);
+int igs_destroy_geometry(igs_geom geom);
+
+/* ----------------------------------------------------------------- problem */
+
+/* Discretise on `n_elems` uniform elements of I with degree-`degree` B-splines
+ * (periodic for a closed curve, clamped for an open arc), exactness space
+ * refined `n_ref` times (Sect. 4), precision IGS_FP64 or IGS_MIXED.
+ * Limits: 2 <= degree <= 5, 1 <= n_ref <= 4, closed: n_elems >= 2(degree+1),
+ * n_ref * n_elems >= 3.  Errors: INVALID_ARG. */
+int igs_create_problem(igs_geom geom, igs_prob* out, int degree, int n_elems, int n_ref, int precision);
+int igs_destroy_problem(igs_prob prob);
+int igs_problem_info(igs_prob prob, igs_info* out);
+int igs_problem_timing(igs_prob prob, igs_timing* out);
+
+/* Build the weighted quadrature rules on the device (FP64):
+ *   node vector eta (Sect. 4), regular rules w^(i) by Algorithm 1 (minimum-norm
+ *   solution of the local exactness system, eq. reg_exactness), the Gram matrix
+ *   G = (B)(B)^T of the collocation matrix and its banded Cholesky factor, the
+ *   modified moments mu_j(eta_m) (eq. mod_mom_gen) and the singular rules
+ *   w^{eta_m} = (B)^T G^{-1} mu(eta_m) of Algorithm 2.
+ * The rules depend only on (n_elems, degree, n_ref, closed) and are reused by
+ * every later assemble.  Idempotent.  Errors: NO_MEMORY, CUDA. */
+int igs_build_weighted_rules(igs_prob prob);
+
+/* Assemble A (n x n) on the device (eqs. IK1e2 and IK1e2_bis, A = -(I_K1 + I_K2)/(2 pi)).
+ * Builds the rules first if needed, then evaluates the geometry at the nodes.
+ * The matrix is kept inside the problem for igs_solve.  If A_out != NULL it is
+ * also copied out, row-major with leading dimension `ld` >= n (elements), in
+ * element type `dtype` (IGS_F64 or IGS_F32) to `mem` (IGS_MEM_HOST/DEVICE).
+ * Errors: INVALID_ARG (ld < n, bad dtype/mem), NO_MEMORY, CUDA. */
+int igs_assemble(igs_prob prob, void* A_out, int64_t ld, int mem, int dtype);
+
+/* Points where the Dirichlet datum u_D must be sampled for igs_build_rhs:
+ * the N_quad nodes f(eta_n), then the N_GQ composite Gauss points of the
+ * double-layer inner rule (Sect. 5, b2).  Writes `count` = n_rhs_pts and, if
+ * xy_out != NULL and capacity >= count, the points row-major count x 2 (HOST).
+ * Requires the rules (built on demand).  Errors: INVALID_ARG, CUDA. */
+int igs_rhs_points(igs_prob prob, double* xy_out, int64_t capacity, int64_t* count);
+
+/* Right-hand side of Sect. 5 for `nrhs` data sets.  uD (HOST) holds, for each
+ * data set k, n_rhs_pts values u_D at the points of igs_rhs_points, data set k
+ * at uD[k * n_rhs_pts].  Interior (closed) problem: beta = b1/2 - b2/(2pi)
+ * (eq. seconda_BIE); open arc: beta = b1 (eq. prima_BIE).  beta is kept in the
+ * problem for igs_solve; if beta_out != NULL it is also written (HOST, n x nrhs,
+ * data set k at beta_out[k * n]).  Errors: INVALID_ARG, NO_MEMORY, CUDA. */
+int igs_build_rhs(igs_prob prob, const double* uD, int nrhs, double* beta_out);
+
+/* Solve (A + A^T)/2 alpha = beta (eq. sistlin) by Cholesky.  FP64 tier: FP64
+ * factorisation.  MIXED tier: FP32 factorisation and FP64 iterative refinement
+ * until ||beta - A_s alpha|| <= 1e-10 ||beta|| (at most 30 steps).
+ * beta: NULL to use the problem's last igs_build_rhs result, else `mem`
+ * memory, n x nrhs (data set k at beta[k*n]).  alpha_out: `mem` memory, same
+ * layout.  resid_out: NULL or HOST array of nrhs final relative residuals.
+ * The factor is kept and reused until the next igs_assemble.
+ * Errors: STATE (not assembled / no rhs), NOT_SPD, NOT_CONVERGED, CUDA. */
+int igs_solve(igs_prob prob, const double* beta, int nrhs, double* alpha_out, double* resid_out, int mem);
+
+/* Diagnostic download of the rules for parity checks (HOST outputs, FP64):
+ *   eta[n_quad]; W_band[n_quad * (degree+1)]: W_band[m*(d+1)+r] = w^(i)_m for
+ *   the test function i = (first(m) + r) mod n containing eta_m (0 if none),
+ *   first[n_quad]: first(m) (may be >= n for the seam node eta = b);
+ *   Ws[n_quad * n_quad] (row m = w^{eta_m}, NULL to skip).
+ * Any output pointer may be NULL.  Errors: STATE, CUDA. */
+int igs_get_rules(igs_prob prob, double* eta, double* W_band, int32_t* first, double* Ws);
+
+/* Diagnostic download of the geometry at the nodes (HOST, FP64): xy[n_quad*2]
+ * (f(eta_n)), J[n_quad] (|f'(eta_n)|).  Errors: STATE, CUDA. */
+int igs_get_node_geometry(igs_prob prob, double* xy, double* J);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGS_H */

@@ -1,0 +1,265 @@
+// Fused assembly of A = -(I_K1 + I_K2)/(2 pi) (Sect. 5, eqs. IK1e2 and IK1e2_bis).
+//
+// With P = diag(J(eta)) W (regular rules, Algorithm 1), Q = diag(J(eta)) B_test and
+// the singular rules W^s (Algorithm 2):
+//     I_K1 = P^T C0 P,  C0[a,b] = K1(eta_a, eta_b)          (eq. IK1e2)
+//     I_K2 = P^T W^s Q                                       (eq. IK1e2_bis)
+// so A = -(1/2pi) P^T (C0 P + W^s Q).  One CTA owns a TILE x TILE block of A;
+// the node ranges of its rows (A-range) and columns (B-range) follow from the
+// index sets N^(i).  Stage 1 (sum factorisation, cf. Algorithm 3): each thread
+// owns one A-range node a and walks the B-range in order, evaluating the kernel
+// K1(eta_a, eta_b) on the fly and accumulating S1[a][j] = sum_b C0 P + W^s Q in a
+// sliding register window of the d+1 columns j whose support holds b.  Stage 2
+// contracts S1 with the row weights P.  C0 is never stored.
+//
+// K1 = ln|f(s)-f(t)| - K2(s,t) is evaluated as (1/2) ln(|f(s)-f(t)|^2 / D(t-s)^2)
+// with D = exp(K2): D(x) = |x| (open arc) or |x| |x+L| |x-L| / L^2 (closed
+// curve, three-image log).  The factors x+L and L-x are formed as
+// eta_b + (L - eta_a) and (L - eta_b) + eta_a, sums of non-negative numbers, so
+// the corner region keeps full relative accuracy.  In the FP32 tier the node
+// coordinates are float-float pairs: the differences are taken hi-hi plus lo-lo,
+// which keeps their relative error at FP32 rounding even for adjacent nodes.
+// Limits (eq. F1_lim and the corner limit): K1(s,s) = ln J(s);
+// K1(a,b) = K1(b,a) = ln J - ln 2 on a closed curve.
+#include "igs_internal.h"
+
+namespace igs {
+
+constexpr int kTile = 32;
+
+struct NodeD { double x, y, e, eb, lnJ; };
+struct NodeF { float xh, xl, yh, yl, eh, el, ebh, ebl, lnJ; };
+
+template <typename T> struct NodeOf;
+template <> struct NodeOf<double> { using type = NodeD; };
+template <> struct NodeOf<float> { using type = NodeF; };
+
+__global__ void k_prep_d(int Nq, int d, double L, const double* __restrict__ geo, const double* __restrict__ eta,
+                         const double* __restrict__ W, const double* __restrict__ Bt, NodeD* __restrict__ nodes,
+                         double* __restrict__ P, double* __restrict__ Q) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nq) return;
+    const double J = geo[4 * Nq + m];
+    NodeD r;
+    r.x = geo[m]; r.y = geo[Nq + m]; r.e = eta[m] - eta[0]; r.eb = L - r.e; r.lnJ = log(J);
+    if (m == Nq - 1) { r.e = L; r.eb = 0.0; }
+    if (m == 0) { r.e = 0.0; r.eb = L; }
+    nodes[m] = r;
+    for (int k = 0; k <= d; ++k) {
+        P[m * (d + 1) + k] = J * W[m * (d + 1) + k];
+        Q[m * (d + 1) + k] = J * Bt[m * (d + 1) + k];
+    }
+}
+
+__device__ __forceinline__ void split(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+__global__ void k_prep_f(int Nq, int d, double L, const double* __restrict__ geo, const double* __restrict__ eta,
+                         const double* __restrict__ W, const double* __restrict__ Bt, NodeF* __restrict__ nodes,
+                         float* __restrict__ P, float* __restrict__ Q) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nq) return;
+    const double J = geo[4 * Nq + m];
+    double e = eta[m] - eta[0], eb = L - e;
+    if (m == Nq - 1) { e = L; eb = 0.0; }
+    if (m == 0) { e = 0.0; eb = L; }
+    NodeF r;
+    split(geo[m], r.xh, r.xl);
+    split(geo[Nq + m], r.yh, r.yl);
+    split(e, r.eh, r.el);
+    split(eb, r.ebh, r.ebl);
+    r.lnJ = (float)log(J);
+    nodes[m] = r;
+    for (int k = 0; k <= d; ++k) {
+        P[m * (d + 1) + k] = (float)(J * W[m * (d + 1) + k]);
+        Q[m * (d + 1) + k] = (float)(J * Bt[m * (d + 1) + k]);
+    }
+}
+
+// K1 between two distinct, non-corner nodes.
+__device__ __forceinline__ double k1_pair(const NodeD& a, const NodeD& b, int closed, double invL2) {
+    const double dx = b.x - a.x, dy = b.y - a.y;
+    double D = fabs(b.e - a.e);
+    if (closed) D *= (b.e + a.eb) * (b.eb + a.e) * invL2;
+    return 0.5 * log((dx * dx + dy * dy) / (D * D));
+}
+__device__ __forceinline__ float k1_pair(const NodeF& a, const NodeF& b, int closed, float invL2) {
+    const float dx = (b.xh - a.xh) + (b.xl - a.xl);
+    const float dy = (b.yh - a.yh) + (b.yl - a.yl);
+    float D = fabsf((b.eh - a.eh) + (b.el - a.el));
+    if (closed) D *= ((b.eh + a.ebh) + (b.el + a.ebl)) * ((b.ebh + a.eh) + (b.ebl + a.el)) * invL2;
+    return 0.5f * logf((dx * dx + dy * dy) / (D * D));
+}
+
+__device__ __forceinline__ int pmod(int u, int N) {
+    int m = u % N;
+    return m < 0 ? m + N : m;
+}
+__device__ __forceinline__ int pdiv(int u, int N) {   // floor(u / N)
+    return (u >= 0) ? u / N : -((-u + N - 1) / N);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_assemble_tile(
+    int n, int Nq, int closed, T invL2, const int* __restrict__ lo, const int* __restrict__ hi,
+    const int* __restrict__ jfirst, const typename NodeOf<T>::type* __restrict__ nodes, const T* __restrict__ P,
+    const T* __restrict__ Q, const T* __restrict__ WsT, T* __restrict__ A, int64_t ld, int maxr) {
+    using Node = typename NodeOf<T>::type;
+    constexpr int D1 = D + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int i0 = blockIdx.y * kTile, j0 = blockIdx.x * kTile;
+    const int ni = min(kTile, n - i0), nj = min(kTile, n - j0);
+    const int uA0 = lo[i0], Na = hi[i0 + ni - 1] - uA0 + 1;
+    const int uB0 = lo[j0], Nb = hi[j0 + nj - 1] - uB0 + 1;
+    // shared layout
+    Node* sB = (Node*)smem;
+    T* sPB = (T*)(sB + maxr);
+    T* sQB = sPB + maxr * D1;
+    T* sPA = sQB + maxr * D1;
+    T* sS1 = sPA + maxr * D1;                         // [maxr][kTile + 1]
+    int* sJB = (int*)(sS1 + maxr * (kTile + 1));
+    int* sMB = sJB + maxr;
+    int* sJA = sMB + maxr;
+
+    for (int v = threadIdx.x; v < Nb; v += blockDim.x) {
+        const int u = uB0 + v, m = pmod(u, Nq), per = pdiv(u, Nq);
+        sB[v] = nodes[m];
+        sMB[v] = m;
+        sJB[v] = jfirst[m] + n * per - j0;
+        for (int r = 0; r < D1; ++r) { sPB[v * D1 + r] = P[m * D1 + r]; sQB[v * D1 + r] = Q[m * D1 + r]; }
+    }
+    for (int v = threadIdx.x; v < Na; v += blockDim.x) {
+        const int u = uA0 + v, m = pmod(u, Nq), per = pdiv(u, Nq);
+        sJA[v] = jfirst[m] + n * per - i0;
+        for (int r = 0; r < D1; ++r) sPA[v * D1 + r] = P[m * D1 + r];
+    }
+    __syncthreads();
+
+    const T ln2 = (T)0.69314718055994530942;
+    for (int a = threadIdx.x; a < Na; a += blockDim.x) {
+        const int ma = pmod(uA0 + a, Nq);
+        const Node na = nodes[ma];
+        T acc[D1];
+#pragma unroll
+        for (int r = 0; r < D1; ++r) acc[r] = (T)0;
+        int jcur = sJB[0];
+        T* row = sS1 + a * (kTile + 1);
+        for (int v = 0; v < Nb; ++v) {
+            const int jf = sJB[v];
+            while (jcur < jf) {
+                if (jcur >= 0 && jcur < nj) row[jcur] = acc[0];
+#pragma unroll
+                for (int r = 0; r < D; ++r) acc[r] = acc[r + 1];
+                acc[D] = (T)0;
+                ++jcur;
+            }
+            const int mb = sMB[v];
+            T c0;
+            if (mb == ma) c0 = na.lnJ;
+            else if (closed && (ma + mb == Nq - 1) && (ma == 0 || mb == 0)) c0 = na.lnJ - ln2;
+            else c0 = k1_pair(na, sB[v], closed, invL2);
+            const T ws = WsT[(size_t)mb * Nq + ma];
+#pragma unroll
+            for (int r = 0; r < D1; ++r) acc[r] += sPB[v * D1 + r] * c0 + sQB[v * D1 + r] * ws;
+        }
+#pragma unroll
+        for (int r = 0; r < D1; ++r)
+            if (jcur + r >= 0 && jcur + r < nj) row[jcur + r] = acc[r];
+    }
+    __syncthreads();
+
+    const T scale = (T)(-1.0 / (2.0 * kPi));
+    for (int idx = threadIdx.x; idx < ni * nj; idx += blockDim.x) {
+        const int il = idx / nj, jl = idx % nj;
+        const int i = i0 + il;
+        const int a0 = lo[i] - uA0, a1 = hi[i] - uA0;
+        T s = (T)0;
+        for (int a = a0; a <= a1; ++a) {
+            const int r = il - sJA[a];
+            if (r >= 0 && r <= D) s += sPA[a * D1 + r] * sS1[a * (kTile + 1) + jl];
+        }
+        A[(size_t)i * ld + j0 + jl] = scale * s;
+    }
+}
+
+template <typename T>
+static size_t tile_smem(int maxr, int d) {
+    using Node = typename NodeOf<T>::type;
+    return maxr * sizeof(Node) + (size_t)maxr * (d + 1) * 3 * sizeof(T) + (size_t)maxr * (kTile + 1) * sizeof(T) +
+           3 * sizeof(int) * maxr + 64;
+}
+
+template <typename T, int D>
+static void launch_tile(igs_prob p, int maxr, cudaStream_t s) {
+    const Plan& P = p->plan;
+    const size_t sm = tile_smem<T>(maxr, D);
+    auto kern = k_assemble_tile<T, D>;
+    IGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int nt = (P.n + kTile - 1) / kTile;
+    dim3 grid(nt, nt);
+    const T* ws = std::is_same<T, float>::value ? (const T*)p->d_WsT32 : (const T*)p->d_WsT;
+    kern<<<grid, 256, sm, s>>>(P.n, P.Nq, P.closed, (T)(1.0 / (P.L * P.L)), p->d_lo, p->d_hi, p->d_jfirst,
+                               (const typename NodeOf<T>::type*)p->d_nodes, (const T*)p->d_P, (const T*)p->d_Q, ws,
+                               (T*)p->d_A, (int64_t)P.n, maxr);
+    IGS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+static void launch_tile_deg(igs_prob p, int maxr, cudaStream_t s) {
+    switch (p->plan.d) {
+        case 2: launch_tile<T, 2>(p, maxr, s); break;
+        case 3: launch_tile<T, 3>(p, maxr, s); break;
+        case 4: launch_tile<T, 4>(p, maxr, s); break;
+        case 5: launch_tile<T, 5>(p, maxr, s); break;
+        default: throw Error(IGS_E_INVALID_ARG, "unsupported degree");
+    }
+}
+
+static int max_tile_range(const Plan& P) {
+    int mx = 0;
+    for (int i0 = 0; i0 < P.n; i0 += kTile) {
+        int i1 = std::min(P.n, i0 + kTile) - 1;
+        mx = std::max(mx, P.hi[i1] - P.lo[i0] + 1);
+    }
+    return mx;
+}
+
+void geometry_nodes(igs_prob p) {
+    const Plan& P = p->plan;
+    cudaStream_t s = p->geom->ctx->stream;
+    const int Nq = P.Nq, D1 = P.d + 1;
+    if (!p->d_geo) p->d_geo = (double*)dev_alloc(p, sizeof(double) * 5 * Nq);
+    geometry_eval(p->geom, p->d_eta, Nq, p->d_geo, s);
+    p->launches++;
+    const bool mixed = p->precision == IGS_MIXED;
+    if (!p->d_nodes) {
+        p->d_nodes = dev_alloc(p, (mixed ? sizeof(NodeF) : sizeof(NodeD)) * Nq);
+        p->d_P = dev_alloc(p, (mixed ? sizeof(float) : sizeof(double)) * Nq * D1);
+        p->d_Q = dev_alloc(p, (mixed ? sizeof(float) : sizeof(double)) * Nq * D1);
+    }
+    if (mixed)
+        k_prep_f<<<(Nq + 127) / 128, 128, 0, s>>>(Nq, P.d, P.L, p->d_geo, p->d_eta, p->d_W, p->d_Bt,
+                                                  (NodeF*)p->d_nodes, (float*)p->d_P, (float*)p->d_Q);
+    else
+        k_prep_d<<<(Nq + 127) / 128, 128, 0, s>>>(Nq, P.d, P.L, p->d_geo, p->d_eta, p->d_W, p->d_Bt,
+                                                  (NodeD*)p->d_nodes, (double*)p->d_P, (double*)p->d_Q);
+    p->launches++;
+    IGS_CUDA(cudaGetLastError());
+    p->geometry_ready = 1;
+}
+
+void assemble_matrix(igs_prob p) {
+    const Plan& P = p->plan;
+    cudaStream_t s = p->geom->ctx->stream;
+    const bool mixed = p->precision == IGS_MIXED;
+    const size_t esz = mixed ? sizeof(float) : sizeof(double);
+    if (!p->d_A) p->d_A = dev_alloc(p, esz * (size_t)P.n * P.n);
+    const int maxr = max_tile_range(P);
+    if (mixed) launch_tile_deg<float>(p, maxr, s);
+    else launch_tile_deg<double>(p, maxr, s);
+    p->launches++;
+}
+
+}  // namespace igs

@@ -1,0 +1,147 @@
+// Internal declarations of the IgA-SGBEM GB300 library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/igs.h"
+
+namespace igs {
+
+constexpr int kMaxDegree = 5;
+constexpr int kMaxNref = 4;
+constexpr int kMaxGeomDegree = 7;
+constexpr int kGaussRhs = 4;          // Gauss points per refined element for the b2 inner rule
+constexpr double kPi = 3.14159265358979323846;
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+std::string cuda_msg(cudaError_t e, const char* what, const char* file, int line);
+
+#define IGS_CUDA(call)                                                           \
+    do {                                                                          \
+        cudaError_t _e = (call);                                                  \
+        if (_e != cudaSuccess) {                                                  \
+            throw ::igs::Error(IGS_E_CUDA, ::igs::cuda_msg(_e, #call, __FILE__, __LINE__)); \
+        }                                                                         \
+    } while (0)
+
+struct Error {
+    int code;
+    std::string msg;
+    Error(int c, std::string m) : code(c), msg(std::move(m)) {}
+};
+
+// ------------------------------------------------------------------ plan
+// Integer description of the discretisation (Sect. 3-4).  Node positions are
+// kept in units of h_f / den with den = 2 (d + 1), so every node of Sect. 4
+// (d+2 uniform points in the first and last refined element, midpoints and
+// breakpoints elsewhere) has an integer position.
+struct Plan {
+    int n = 0, d = 0, Nh = 0, Nref = 0, M = 0, Nq = 0, NE = 0, closed = 0;
+    int den = 0;
+    double a = 0, b = 0, L = 0, h = 0, hf = 0;
+    std::vector<int> pos_num;     // [Nq]   position * den (units of h_f)
+    std::vector<int> jfirst;      // [Nq]   first test function (unrolled) whose band holds the node
+    std::vector<int> member;      // [Nq]   bit r set if B_{jfirst+r}(eta) != 0
+    std::vector<int> fspan;       // [Nq]   refined element holding the node (0..M-1)
+    std::vector<int> lo, hi;      // [n]    unrolled node range of N^(i)
+    std::vector<int> jlo1, jhi1, jlo2, jhi2;  // [n] exactness functions J^(i) (1-2 ranges)
+    std::vector<int> elo1, ehi1, elo2, ehi2;  // [n] refined elements of supp(B_i) (half-open)
+    std::vector<int> gfirst, glast;           // [NE] node range touching supp(B-bar_j)
+    int max_nodes_i = 0, max_fine_i = 0;      // largest |N^(i)|, |J^(i)|
+    int max_tile_nodes = 0;                   // largest node range of a row tile
+    std::vector<double> piece;    // [(d+1)*(d+1)] cardinal B-spline pieces: N_d(l+u) = sum_k piece[l*(d+1)+k] u^k
+    std::vector<double> series;   // [(d+1)*kSeries] far-field log series coefficients
+};
+constexpr int kSeries = 30;
+
+int build_plan(Plan& p, double a, double b, int Nh, int d, int Nref, int closed, std::string& err);
+
+}  // namespace igs
+
+// ------------------------------------------------------------------ handles
+struct igs_ctx_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int live_geoms = 0, live_probs = 0;
+};
+
+struct igs_geom_s {
+    igs_ctx ctx = nullptr;
+    int degree = 0, n_ctrl = 0, n_knots = 0, closed = 0, rational = 0;
+    double a = 0, b = 0;
+    double* d_knots = nullptr;
+    double* d_ctrl = nullptr;    // n_ctrl x 2
+    double* d_w = nullptr;       // n_ctrl (all ones for a B-spline)
+    int live_probs = 0;
+};
+
+struct igs_prob_s {
+    igs_geom geom = nullptr;
+    igs::Plan plan;
+    int precision = IGS_FP64;
+    int rules_ready = 0, geometry_ready = 0, assembled = 0, factored = 0;
+    int64_t bytes = 0;
+    igs_timing timing{};
+    int launches = 0;
+
+    // plan arrays on device
+    int *d_pos = nullptr, *d_jfirst = nullptr, *d_member = nullptr, *d_fspan = nullptr;
+    int *d_lo = nullptr, *d_hi = nullptr;
+    int *d_jr = nullptr;          // [n][8]: jlo1,jhi1,jlo2,jhi2,elo1,ehi1,elo2,ehi2
+    int *d_gfirst = nullptr, *d_glast = nullptr;
+    double *d_piece = nullptr, *d_series = nullptr;
+
+    // rules (FP64)
+    double* d_eta = nullptr;      // [Nq]
+    double* d_Bf = nullptr;       // [Nq][d+1] exactness functions e..e+d at the node (e = fspan)
+    double* d_Bt = nullptr;       // [Nq][d+1] test functions jfirst..jfirst+d at the node
+    double* d_W = nullptr;        // [Nq][d+1] regular weights w^(jfirst+r)_m
+    double* d_G = nullptr;        // [NE][d+1] Cholesky factor of G (row j: L(j, j-r))
+    double* d_Z = nullptr;        // [NE][Nq] G^{-1} mu(eta_m) (work)
+    double* d_WsT = nullptr;      // [Nq][Nq] transposed singular rules: WsT[n][m] = w^{eta_m}_n
+    float* d_WsT32 = nullptr;     // FP32 copy (MIXED tier)
+    int* d_flag = nullptr;        // device status word
+
+    // geometry at nodes
+    double* d_geo = nullptr;      // [5][Nq]: x, y, x', y', J
+    void* d_nodes = nullptr;      // tier-specific node records
+    void* d_P = nullptr;          // [Nq][d+1] J * W (tier type)
+    void* d_Q = nullptr;          // [Nq][d+1] J * B_test (tier type)
+
+    // matrix and solve
+    void* d_A = nullptr;          // [n][n] tier type (row-major)
+    void* d_F = nullptr;          // [n][n] Cholesky factor (tier type)
+    double* d_As64 = nullptr;     // (A+A^T)/2 in FP64 for residuals (MIXED)
+    int rhs_n = 0;
+    double* d_beta = nullptr;     // [nrhs][n]
+    double* d_rhs_geo = nullptr;  // [5][Ng] geometry at the rhs Gauss points
+    double* d_rhs_w = nullptr;    // [Ng] Gauss weights
+    double* d_rhs_t = nullptr;    // [Ng] Gauss abscissae
+    int Ng = 0;
+};
+
+namespace igs {
+// allocation helpers (stream-ordered, accounted on the problem)
+void* dev_alloc(igs_prob p, size_t bytes);
+void dev_free_raw(igs_prob p, void* ptr);
+template <typename T>
+inline void dev_free(igs_prob p, T*& ptr) {
+    if (ptr) dev_free_raw(p, (void*)ptr);
+    ptr = nullptr;
+}
+
+// phases (implemented in the .cu files)
+void rules_build(igs_prob p);
+void geometry_eval(igs_geom g, const double* d_t, int count, double* d_out, cudaStream_t s);
+void geometry_nodes(igs_prob p);
+void assemble_matrix(igs_prob p);
+void rhs_prepare(igs_prob p);
+void rhs_build(igs_prob p, const double* d_uD, int nrhs);
+void solve_system(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double* resid);
+}  // namespace igs

@@ -1,0 +1,426 @@
+// Weighted quadrature rules on the device (FP64): Sect. 4, Algorithms 1 and 2.
+#include <cmath>
+
+#include "bspline_dev.cuh"
+#include "igs_internal.h"
+
+namespace igs {
+
+constexpr int kMaxLocalNodes = 64;   // |N^(i)| bound (d <= 5, N_ref <= 4)
+constexpr int kMaxLocalFine = 40;    // |J^(i)| bound
+
+// Gauss-Legendre nodes/weights on [0,1] for 1..6 points (row g-1), filled by the host.
+__constant__ double c_gauss_x[6][6];
+__constant__ double c_gauss_w[6][6];
+
+// --------------------------------------------------------------- nodes, bands
+// eta_m = a + h_f * pos_m; exactness functions at the node from the cardinal
+// pieces; test functions jfirst..jfirst+d (cyclic: cardinal pieces in coarse
+// coordinates; clamped: Cox-de Boor on the clamped knot vector).
+__global__ void k_nodes_bands(int Nq, int d, int den, int Nref, int M, int closed, double a, double b, double hf,
+                              const int* __restrict__ pos, const int* __restrict__ jfirst,
+                              const int* __restrict__ member, const int* __restrict__ fspan,
+                              const double* __restrict__ piece, const double* __restrict__ tknots, int ntb,
+                              double* __restrict__ eta, double* __restrict__ Bf, double* __restrict__ Bt) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nq) return;
+    const int P = pos[m];
+    double t = (m == Nq - 1) ? b : a + hf * (double(P) / den);
+    eta[m] = t;
+    // exactness functions e..e+d at local coordinate u in element e
+    const int e = fspan[m];
+    const double u = double(P - e * den) / den;
+    for (int r = 0; r <= d; ++r) Bf[m * (d + 1) + r] = piece_eval(piece, d, d - r, u);
+    // test functions
+    const int cunit = den * Nref;
+    const int jf = jfirst[m];
+    if (closed) {
+        const double uc = double(P - jf * cunit) / cunit;
+        for (int r = 0; r <= d; ++r)
+            Bt[m * (d + 1) + r] = ((member[m] >> r) & 1) ? piece_eval(piece, d, d - r, uc) : 0.0;
+    } else {
+        double N[kMaxDegree + 1];
+        int span = find_span(tknots, ntb, d, t);
+        basis_funs(tknots, span, d, t, N);
+        for (int r = 0; r <= d; ++r) {
+            int idx = jf + r - (span - d);
+            double v = (idx >= 0 && idx <= d) ? N[idx] : 0.0;
+            Bt[m * (d + 1) + r] = ((member[m] >> r) & 1) ? v : 0.0;
+        }
+    }
+}
+
+// ----------------------------------------------------------------- Algorithm 1
+// One thread per test function i: mu^(i)_j = int B-bar_j B_i by Gauss with d+1
+// points per refined element (exact), local collocation matrix (B)^(i), and the
+// minimum-norm solution of (B)^(i) w = mu^(i) by Householder QR of (B)^(i)T.
+__device__ double test_value(int closed, int d, int Nref, int n, const double* piece, const double* tknots, int ntb,
+                             int iu, double pos_c, double t) {
+    if (closed) {
+        double loc = pos_c - (iu - d);                // position inside the support [0, d+1]
+        if (loc <= 0.0 || loc >= d + 1) return 0.0;
+        int l = (int)floor(loc);
+        if (l > d) l = d;
+        return piece_eval(piece, d, l, loc - l);
+    }
+    double N[kMaxDegree + 1];
+    int span = find_span(tknots, ntb, d, t);
+    basis_funs(tknots, span, d, t, N);
+    int idx = iu - (span - d);
+    return (idx >= 0 && idx <= d) ? N[idx] : 0.0;
+}
+
+__global__ void __launch_bounds__(64) k_regular(int n, int Nq, int d, int Nref, int M, int closed, double a, double hf,
+                                                const int* __restrict__ lo, const int* __restrict__ hi,
+                                                const int* __restrict__ jr, const int* __restrict__ jfirst,
+                                                const int* __restrict__ fspan, const double* __restrict__ Bf,
+                                                const double* __restrict__ piece, const double* __restrict__ tknots,
+                                                int ntb, double* __restrict__ W, int* __restrict__ flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double A[kMaxLocalNodes][kMaxLocalFine];    // (B)^(i)T, Householder vectors below the diagonal
+    double mu[kMaxLocalFine], diag[kMaxLocalFine], beta[kMaxLocalFine], z[kMaxLocalNodes];
+    int fj[kMaxLocalFine];
+    const int u0 = lo[i], nN = hi[i] - lo[i] + 1;
+    const int* R = jr + 8 * i;
+    int nJ = 0;
+    for (int j = R[0]; j <= R[1]; ++j) fj[nJ++] = j;
+    for (int j = R[2]; j <= R[3]; ++j) fj[nJ++] = j;
+    if (nN > kMaxLocalNodes || nJ > kMaxLocalFine || nJ > nN) { atomicOr(flag, 1); return; }
+
+    // mu^(i)_j over the refined elements of supp(B_i)
+    for (int q = 0; q < nJ; ++q) mu[q] = 0.0;
+    const int g = d + 1;
+    for (int part = 0; part < 2; ++part) {
+        const int e0 = R[4 + 2 * part], e1 = R[5 + 2 * part];
+        const int iu = (closed && part == 1) ? i + n : i;          // wrapped copy near b
+        for (int e = e0; e < e1; ++e) {
+            for (int k = 0; k < g; ++k) {
+                const double x = c_gauss_x[g - 1][k], wq = c_gauss_w[g - 1][k] * hf;
+                const double t = a + hf * (e + x);
+                const double bi = test_value(closed, d, Nref, n, piece, tknots, ntb, iu, (e + x) / Nref, t);
+                if (bi == 0.0) continue;
+                for (int r = 0; r <= d; ++r) {
+                    const int j = e + r;                           // B-bar_{e+r} on element e
+                    const double bj = piece_eval(piece, d, d - r, x);
+                    for (int q = 0; q < nJ; ++q)
+                        if (fj[q] == j) { mu[q] += wq * bj * bi; break; }
+                }
+            }
+        }
+    }
+    // local matrix, transposed: A[ul][q] = B-bar_{fj[q]}(eta_{m(ul)})
+    for (int ul = 0; ul < nN; ++ul) {
+        int m = (u0 + ul) % Nq;
+        if (m < 0) m += Nq;
+        const int e = fspan[m];
+        for (int q = 0; q < nJ; ++q) {
+            const int r = fj[q] - e;
+            A[ul][q] = (r >= 0 && r <= d) ? Bf[m * (d + 1) + r] : 0.0;
+        }
+    }
+    // Householder QR of A (nN x nJ)
+    for (int k = 0; k < nJ; ++k) {
+        double nrm = 0.0;
+        for (int r = k; r < nN; ++r) nrm += A[r][k] * A[r][k];
+        nrm = sqrt(nrm);
+        if (nrm == 0.0) { atomicOr(flag, 2); return; }
+        const double alpha = (A[k][k] > 0) ? -nrm : nrm;
+        A[k][k] -= alpha;
+        double vn = 0.0;
+        for (int r = k; r < nN; ++r) vn += A[r][k] * A[r][k];
+        beta[k] = (vn > 0) ? 2.0 / vn : 0.0;
+        diag[k] = alpha;
+        for (int c = k + 1; c < nJ; ++c) {
+            double s = 0.0;
+            for (int r = k; r < nN; ++r) s += A[r][k] * A[r][c];
+            s *= beta[k];
+            for (int r = k; r < nN; ++r) A[r][c] -= s * A[r][k];
+        }
+    }
+    // R^T y = mu
+    for (int k = 0; k < nJ; ++k) {
+        double s = mu[k];
+        for (int c = 0; c < k; ++c) s -= A[c][k] * z[c];
+        z[k] = s / diag[k];
+    }
+    for (int r = nJ; r < nN; ++r) z[r] = 0.0;
+    // w = H_0 ... H_{nJ-1} [y; 0]
+    for (int k = nJ - 1; k >= 0; --k) {
+        double s = 0.0;
+        for (int r = k; r < nN; ++r) s += A[r][k] * z[r];
+        s *= beta[k];
+        for (int r = k; r < nN; ++r) z[r] -= s * A[r][k];
+    }
+    // scatter into the node bands: slot r with jfirst[m] + r = unrolled index of i
+    for (int ul = 0; ul < nN; ++ul) {
+        const int u = u0 + ul;
+        int m = u % Nq;
+        if (m < 0) m += Nq;
+        const int iu = (u < 0) ? i + n : i;
+        const int r = iu - jfirst[m];
+        if (r < 0 || r > d) { atomicOr(flag, 4); continue; }
+        W[m * (d + 1) + r] = z[ul];
+    }
+}
+
+// ----------------------------------------------------------------- Gram matrix
+// G = (B)(B)^T, upper band G[j][r] = sum_m B-bar_j(eta_m) B-bar_{j+r}(eta_m).
+__global__ void k_gram(int NE, int d, const int* __restrict__ gfirst, const int* __restrict__ glast,
+                       const int* __restrict__ fspan, const double* __restrict__ Bf, double* __restrict__ G) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= NE) return;
+    double acc[kMaxDegree + 1];
+    for (int r = 0; r <= d; ++r) acc[r] = 0.0;
+    for (int m = gfirst[j]; m <= glast[j]; ++m) {
+        const int e = fspan[m];
+        const int rj = j - e;
+        if (rj < 0 || rj > d) continue;
+        const double bj = Bf[m * (d + 1) + rj];
+        for (int r = 0; r <= d; ++r) {
+            const int rk = rj + r;
+            if (rk <= d) acc[r] += bj * Bf[m * (d + 1) + rk];
+        }
+    }
+    for (int r = 0; r <= d; ++r) G[j * (d + 1) + r] = acc[r];
+}
+
+// Banded Cholesky G = L L^T in place (one thread; L(j, j-r) stored at L[j][r]).
+__global__ void k_chol_band(int NE, int d, const double* __restrict__ G, double* __restrict__ L, int* __restrict__ flag) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int j = 0; j < NE; ++j) {
+        const int k0 = (j - d > 0) ? j - d : 0;
+        for (int k = k0; k <= j; ++k) {
+            double s = G[k * (d + 1) + (j - k)];
+            for (int p = k0; p < k; ++p) s -= L[j * (d + 1) + (j - p)] * L[k * (d + 1) + (k - p)];
+            if (k < j) {
+                L[j * (d + 1) + (j - k)] = s / L[k * (d + 1)];
+            } else {
+                if (!(s > 0.0)) { atomicOr(flag, 8); return; }
+                L[j * (d + 1)] = sqrt(s);
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------- moments
+// L_k(c) = int_0^1 u^k ln|u - c| du, k = 0..d: closed form of the paper's base
+// integrals in local coordinates near the element, log series far from it.
+__device__ __forceinline__ double base_F(double z, int j) {
+    if (z == 0.0) return 0.0;
+    double zp = z;
+    for (int q = 0; q < j; ++q) zp *= z;
+    return zp / (j + 1) * (log(fabs(z)) - 1.0 / (j + 1));
+}
+
+__device__ void local_log_moments(double c, int d, const double* __restrict__ series, double* Lk) {
+    const double del = c - 0.5;
+    if (fabs(del) <= 2.5) {
+        // z = u - c: u^k = sum_i C(k,i) c^{k-i} z^i
+        double F1[kMaxDegree + 1], F0[kMaxDegree + 1];
+        for (int i = 0; i <= d; ++i) { F1[i] = base_F(1.0 - c, i); F0[i] = base_F(-c, i); }
+        for (int k = 0; k <= d; ++k) {
+            double s = 0.0, binom = 1.0, cp = 1.0;
+            // sum over i = k..0 with c^{k-i}
+            for (int i = k; i >= 0; --i) {
+                s += binom * cp * (F1[i] - F0[i]);
+                // next: i-1, binom C(k, i-1) = C(k,i) * i / (k-i+1), cp *= c
+                binom = binom * i / (k - i + 1);
+                cp *= c;
+            }
+            Lk[k] = s;
+        }
+    } else {
+        const double lg = log(fabs(del)), rho = 1.0 / del;
+        for (int k = 0; k <= d; ++k) {
+            const double* S = series + k * kSeries;
+            double acc = 0.0;
+            for (int q = kSeries - 1; q >= 1; --q) acc = (acc + S[q]) * rho;
+            Lk[k] = lg / (k + 1) - acc;
+        }
+    }
+}
+
+// mu_j(eta_m) for j in a block of 128, m = blockIdx.y; output Z[j][m].
+__global__ void __launch_bounds__(128) k_moments(int Nq, int NE, int M, int d, int den, int closed, double hf, double L,
+                                                 const int* __restrict__ pos, const int* __restrict__ rows,
+                                                 const double* __restrict__ piece, const double* __restrict__ series,
+                                                 double* __restrict__ Z, int ldz) {
+    __shared__ double E[128 + kMaxDegree][kMaxDegree + 1];
+    const int m = rows ? rows[blockIdx.y] : blockIdx.y;
+    const int col = blockIdx.y;
+    const int j0 = blockIdx.x * 128;
+    const double s_units = double(pos[m]) / den;                  // (eta_m - a) / h_f
+    const double lhf = log(hf);
+    for (int t = threadIdx.x; t < 128 + d; t += blockDim.x) {
+        const int e = j0 - d + t;
+        double acc[kMaxDegree + 1];
+        for (int k = 0; k <= d; ++k) acc[k] = 0.0;
+        if (e >= 0 && e < M) {
+            const int nimg = closed ? 3 : 1;
+            for (int im = 0; im < nimg; ++im) {
+                const double shift = (im == 0) ? 0.0 : (im == 1 ? -double(M) : double(M));
+                double Lk[kMaxDegree + 1];
+                local_log_moments(s_units + shift - e, d, series, Lk);
+                for (int k = 0; k <= d; ++k) acc[k] += hf * (lhf / (k + 1) + Lk[k]);
+            }
+            if (closed) {
+                const double c2 = 2.0 * log(L) * hf;
+                for (int k = 0; k <= d; ++k) acc[k] -= c2 / (k + 1);
+            }
+        }
+        for (int k = 0; k <= d; ++k) E[t][k] = acc[k];
+    }
+    __syncthreads();
+    const int j = j0 + threadIdx.x;
+    if (j >= NE) return;
+    double mu = 0.0;
+    for (int l = 0; l <= d; ++l) {                                  // element e = j - d + l
+        const int e = j - d + l;
+        if (e < 0 || e >= M) continue;
+        for (int k = 0; k <= d; ++k) mu += piece[l * (d + 1) + k] * E[threadIdx.x + l][k];
+    }
+    Z[(size_t)j * ldz + col] = mu;
+}
+
+// z = G^{-1} mu in place, one thread per column (node).
+__global__ void k_gsolve(int NE, int d, int ncol, const double* __restrict__ L, double* __restrict__ Z, int ldz) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncol) return;
+    for (int j = 0; j < NE; ++j) {
+        double s = Z[(size_t)j * ldz + c];
+        const int p0 = (j - d > 0) ? j - d : 0;
+        for (int p = p0; p < j; ++p) s -= L[j * (d + 1) + (j - p)] * Z[(size_t)p * ldz + c];
+        Z[(size_t)j * ldz + c] = s / L[j * (d + 1)];
+    }
+    for (int j = NE - 1; j >= 0; --j) {
+        double s = Z[(size_t)j * ldz + c];
+        const int p1 = (j + d < NE - 1) ? j + d : NE - 1;
+        for (int p = j + 1; p <= p1; ++p) s -= L[p * (d + 1) + (p - j)] * Z[(size_t)p * ldz + c];
+        Z[(size_t)j * ldz + c] = s / L[j * (d + 1)];
+    }
+}
+
+// WsT[nn][m] = w^{eta_m}_{nn} = sum_r B-bar_{e+r}(eta_nn) z_m[e+r], e = fspan[nn].
+__global__ void k_ws(int Nq, int d, const int* __restrict__ fspan, const double* __restrict__ Bf,
+                     const double* __restrict__ Z, int ldz, double* __restrict__ WsT, float* __restrict__ WsT32) {
+    const int nn = blockIdx.y;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nq) return;
+    const int e = fspan[nn];
+    double s = 0.0;
+    for (int r = 0; r <= d; ++r) s += Bf[nn * (d + 1) + r] * Z[(size_t)(e + r) * ldz + m];
+    WsT[(size_t)nn * Nq + m] = s;
+    if (WsT32) WsT32[(size_t)nn * Nq + m] = (float)s;
+}
+
+// ------------------------------------------------------------------ driver
+static void upload_gauss() {
+    static bool done = false;
+    if (done) return;
+    double gx[6][6] = {}, gw[6][6] = {};
+    for (int g = 1; g <= 6; ++g) {
+        // Golub-Welsch free: Newton on Legendre polynomials
+        for (int k = 0; k < g; ++k) {
+            double x = cos(kPi * (k + 0.75) / (g + 0.5));
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1, p1 = x;
+                for (int q = 2; q <= g; ++q) { double p2 = ((2 * q - 1) * x * p1 - (q - 1) * p0) / q; p0 = p1; p1 = p2; }
+                double pn = (g == 1) ? x : p1, pm = (g == 1) ? 1 : p0;
+                double dp = g * (x * pn - pm) / (x * x - 1);
+                double dx = pn / dp;
+                x -= dx;
+                if (fabs(dx) < 1e-16) break;
+            }
+            double p0 = 1, p1 = x;
+            for (int q = 2; q <= g; ++q) { double p2 = ((2 * q - 1) * x * p1 - (q - 1) * p0) / q; p0 = p1; p1 = p2; }
+            double pn = (g == 1) ? x : p1, pm = (g == 1) ? 1 : p0;
+            double dp = g * (x * pn - pm) / (x * x - 1);
+            gx[g - 1][k] = (1.0 - x) / 2.0;
+            gw[g - 1][k] = 1.0 / ((1 - x * x) * dp * dp);      // 2/((1-x^2)P'^2) / 2
+        }
+    }
+    IGS_CUDA(cudaMemcpyToSymbol(c_gauss_x, gx, sizeof(gx)));
+    IGS_CUDA(cudaMemcpyToSymbol(c_gauss_w, gw, sizeof(gw)));
+    done = true;
+}
+
+void rules_build(igs_prob p) {
+    const Plan& P = p->plan;
+    cudaStream_t s = p->geom->ctx->stream;
+    const int d = P.d, Nq = P.Nq, NE = P.NE, n = P.n, D1 = d + 1;
+    upload_gauss();
+    cudaEvent_t e0, e1;
+    IGS_CUDA(cudaEventCreate(&e0));
+    IGS_CUDA(cudaEventCreate(&e1));
+    IGS_CUDA(cudaEventRecord(e0, s));
+    int launches = 0;
+
+    p->d_eta = (double*)dev_alloc(p, sizeof(double) * Nq);
+    p->d_Bf = (double*)dev_alloc(p, sizeof(double) * Nq * D1);
+    p->d_Bt = (double*)dev_alloc(p, sizeof(double) * Nq * D1);
+    p->d_W = (double*)dev_alloc(p, sizeof(double) * Nq * D1);
+    p->d_G = (double*)dev_alloc(p, sizeof(double) * NE * D1);
+    double* d_L = (double*)dev_alloc(p, sizeof(double) * NE * D1);
+    IGS_CUDA(cudaMemsetAsync(p->d_W, 0, sizeof(double) * Nq * D1, s));
+    IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s));
+
+    // test knot vector
+    std::vector<double> tk;
+    if (P.closed) {
+        for (int k = 0; k <= P.Nh + 2 * d; ++k) tk.push_back(P.a + P.h * (k - d));
+    } else {
+        for (int k = 0; k < d; ++k) tk.push_back(P.a);
+        for (int k = 0; k <= P.Nh; ++k) tk.push_back(k == P.Nh ? P.b : P.a + P.h * k);
+        for (int k = 0; k < d; ++k) tk.push_back(P.b);
+    }
+    double* d_tk = (double*)dev_alloc(p, sizeof(double) * tk.size());
+    IGS_CUDA(cudaMemcpyAsync(d_tk, tk.data(), sizeof(double) * tk.size(), cudaMemcpyHostToDevice, s));
+    const int ntb = int(tk.size()) - d - 1;
+
+    k_nodes_bands<<<(Nq + 127) / 128, 128, 0, s>>>(Nq, d, P.den, P.Nref, P.M, P.closed, P.a, P.b, P.hf, p->d_pos,
+                                                   p->d_jfirst, p->d_member, p->d_fspan, p->d_piece, d_tk, ntb,
+                                                   p->d_eta, p->d_Bf, p->d_Bt);
+    ++launches;
+    k_regular<<<(n + 63) / 64, 64, 0, s>>>(n, Nq, d, P.Nref, P.M, P.closed, P.a, P.hf, p->d_lo, p->d_hi, p->d_jr,
+                                           p->d_jfirst, p->d_fspan, p->d_Bf, p->d_piece, d_tk, ntb, p->d_W, p->d_flag);
+    ++launches;
+    k_gram<<<(NE + 127) / 128, 128, 0, s>>>(NE, d, p->d_gfirst, p->d_glast, p->d_fspan, p->d_Bf, p->d_G);
+    ++launches;
+    k_chol_band<<<1, 1, 0, s>>>(NE, d, p->d_G, d_L, p->d_flag);
+    ++launches;
+    IGS_CUDA(cudaGetLastError());
+
+    // singular rules, dense: Z = G^{-1} Mu^T, WsT = (B)^T Z
+    p->d_Z = (double*)dev_alloc(p, sizeof(double) * (size_t)NE * Nq);
+    dim3 gm((NE + 127) / 128, Nq);
+    k_moments<<<gm, 128, 0, s>>>(Nq, NE, P.M, d, P.den, P.closed, P.hf, P.L, p->d_pos, nullptr, p->d_piece,
+                                 p->d_series, p->d_Z, Nq);
+    ++launches;
+    k_gsolve<<<(Nq + 127) / 128, 128, 0, s>>>(NE, d, Nq, d_L, p->d_Z, Nq);
+    ++launches;
+    p->d_WsT = (double*)dev_alloc(p, sizeof(double) * (size_t)Nq * Nq);
+    if (p->precision == IGS_MIXED) p->d_WsT32 = (float*)dev_alloc(p, sizeof(float) * (size_t)Nq * Nq);
+    dim3 gw((Nq + 255) / 256, Nq);
+    k_ws<<<gw, 256, 0, s>>>(Nq, d, p->d_fspan, p->d_Bf, p->d_Z, Nq, p->d_WsT, p->d_WsT32);
+    ++launches;
+    IGS_CUDA(cudaGetLastError());
+
+    int flag = 0;
+    IGS_CUDA(cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    IGS_CUDA(cudaEventRecord(e1, s));
+    IGS_CUDA(cudaStreamSynchronize(s));
+    float ms = 0;
+    IGS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dev_free(p, p->d_Z);
+    dev_free(p, d_L);
+    dev_free(p, d_tk);
+    p->timing.rules_ms = ms;
+    p->launches += launches;
+    if (flag) throw Error(IGS_E_INVALID_ARG, "rule construction failed (flag " + std::to_string(flag) + ")");
+    p->rules_ready = 1;
+}
+
+}  // namespace igs

@@ -1,0 +1,232 @@
+"""Thin Python binding of the C ABI in include/igs.h (ctypes).
+
+Each function here has the name of the C entry point it calls and does only
+argument marshalling (numpy / torch buffers to pointers, return-code to
+exception).  Every step of the computation runs in libigs.so; there is no
+Python or CPU fallback: if the library is missing the import fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libigs.so")
+
+IGS_OK = 0
+IGS_E_INVALID_ARG = -1
+IGS_E_NO_MEMORY = -2
+IGS_E_CUDA = -3
+IGS_E_NOT_SPD = -4
+IGS_E_NOT_CONVERGED = -5
+IGS_E_TIMEOUT = -6
+IGS_E_ADMISSION_REFUSED = -7
+IGS_E_STATE = -8
+IGS_FP64, IGS_MIXED = 0, 1
+IGS_MEM_HOST, IGS_MEM_DEVICE = 0, 1
+IGS_F64, IGS_F32 = 0, 1
+
+EXPORTED = [
+    "igs_create", "igs_destroy", "igs_last_error", "igs_create_geometry", "igs_destroy_geometry",
+    "igs_create_problem", "igs_destroy_problem", "igs_problem_info", "igs_problem_timing",
+    "igs_build_weighted_rules", "igs_assemble", "igs_rhs_points", "igs_build_rhs", "igs_solve",
+    "igs_get_rules", "igs_get_node_geometry",
+]
+
+
+class IgsError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where} failed ({code}): {msg}")
+        self.code = code
+
+
+class igs_info(C.Structure):
+    _fields_ = [("n", C.c_int32), ("degree", C.c_int32), ("n_elems", C.c_int32), ("n_ref", C.c_int32),
+                ("n_quad", C.c_int32), ("n_exact", C.c_int32), ("n_rhs_pts", C.c_int32), ("closed", C.c_int32),
+                ("precision", C.c_int32), ("rules_ready", C.c_int32), ("assembled", C.c_int32),
+                ("factored", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+class igs_timing(C.Structure):
+    _fields_ = [("rules_ms", C.c_float), ("geometry_ms", C.c_float), ("assemble_ms", C.c_float),
+                ("rhs_ms", C.c_float), ("factor_ms", C.c_float), ("solve_ms", C.c_float),
+                ("ir_iterations", C.c_int32), ("kernel_launches", C.c_int32)]
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1703_10016_gb300.build.build_library()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, dp = C.c_void_p, C.c_int, C.c_int64, C.POINTER(C.c_double)
+    lib.igs_last_error.restype = C.c_char_p
+    sigs = {
+        "igs_create": [C.POINTER(vp), i32, vp],
+        "igs_destroy": [vp],
+        "igs_create_geometry": [vp, C.POINTER(vp), i32, vp, i32, vp, vp, i32, i32],
+        "igs_destroy_geometry": [vp],
+        "igs_create_problem": [vp, C.POINTER(vp), i32, i32, i32, i32],
+        "igs_destroy_problem": [vp],
+        "igs_problem_info": [vp, C.POINTER(igs_info)],
+        "igs_problem_timing": [vp, C.POINTER(igs_timing)],
+        "igs_build_weighted_rules": [vp],
+        "igs_assemble": [vp, vp, i64, i32, i32],
+        "igs_rhs_points": [vp, vp, i64, C.POINTER(i64)],
+        "igs_build_rhs": [vp, vp, i32, vp],
+        "igs_solve": [vp, vp, i32, vp, vp, i32],
+        "igs_get_rules": [vp, vp, vp, vp, vp],
+        "igs_get_node_geometry": [vp, vp, vp],
+    }
+    for name, args in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != IGS_OK:
+        raise IgsError(rc, where, _lib.igs_last_error().decode())
+
+
+def _ptr(a) -> C.c_void_p | None:
+    """Raw pointer of a numpy array (host) or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------- entry points
+def igs_create(device: int = 0, stream: int | None = None) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(_lib.igs_create(C.byref(h), device, C.c_void_p(stream) if stream else None), "igs_create")
+    return h
+
+
+def igs_destroy(ctx) -> None:
+    _check(_lib.igs_destroy(ctx), "igs_destroy")
+
+
+def igs_last_error() -> str:
+    return _lib.igs_last_error().decode()
+
+
+def igs_create_geometry(ctx, degree: int, knots, ctrl_xy, weights, closed: bool) -> C.c_void_p:
+    knots, ctrl = _f64(knots), _f64(ctrl_xy).reshape(-1, 2)
+    w = None if weights is None else _f64(weights)
+    h = C.c_void_p()
+    _check(_lib.igs_create_geometry(ctx, C.byref(h), int(degree), _ptr(knots), len(knots), _ptr(ctrl),
+                                    _ptr(w), len(ctrl), int(bool(closed))), "igs_create_geometry")
+    return h
+
+
+def igs_destroy_geometry(geom) -> None:
+    _check(_lib.igs_destroy_geometry(geom), "igs_destroy_geometry")
+
+
+def igs_create_problem(geom, degree: int, n_elems: int, n_ref: int, precision: int) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(_lib.igs_create_problem(geom, C.byref(h), int(degree), int(n_elems), int(n_ref), int(precision)),
+           "igs_create_problem")
+    return h
+
+
+def igs_destroy_problem(prob) -> None:
+    _check(_lib.igs_destroy_problem(prob), "igs_destroy_problem")
+
+
+def igs_problem_info(prob) -> igs_info:
+    out = igs_info()
+    _check(_lib.igs_problem_info(prob, C.byref(out)), "igs_problem_info")
+    return out
+
+
+def igs_problem_timing(prob) -> igs_timing:
+    out = igs_timing()
+    _check(_lib.igs_problem_timing(prob, C.byref(out)), "igs_problem_timing")
+    return out
+
+
+def igs_build_weighted_rules(prob) -> None:
+    _check(_lib.igs_build_weighted_rules(prob), "igs_build_weighted_rules")
+
+
+def igs_assemble(prob, A_out=None, ld: int | None = None, mem: int | None = None, dtype: int | None = None) -> None:
+    """A_out: None, a host numpy array or a torch tensor (host or CUDA), n x ld."""
+    if A_out is None:
+        _check(_lib.igs_assemble(prob, None, 0, 0, 0), "igs_assemble")
+        return
+    if ld is None:
+        ld = A_out.shape[1]
+    if mem is None:
+        mem = IGS_MEM_DEVICE if (hasattr(A_out, "is_cuda") and A_out.is_cuda) else IGS_MEM_HOST
+    if dtype is None:
+        dtype = IGS_F32 if str(A_out.dtype).endswith("float32") else IGS_F64
+    _check(_lib.igs_assemble(prob, _ptr(A_out), int(ld), int(mem), int(dtype)), "igs_assemble")
+
+
+def igs_rhs_points(prob) -> np.ndarray:
+    cnt = C.c_int64()
+    _check(_lib.igs_rhs_points(prob, None, 0, C.byref(cnt)), "igs_rhs_points")
+    xy = np.empty((cnt.value, 2), dtype=np.float64)
+    _check(_lib.igs_rhs_points(prob, _ptr(xy), cnt.value, C.byref(cnt)), "igs_rhs_points")
+    return xy
+
+
+def igs_build_rhs(prob, uD, return_beta: bool = True) -> np.ndarray | None:
+    """uD: (nrhs, n_rhs_pts) values at igs_rhs_points (HOST)."""
+    u = _f64(uD)
+    if u.ndim == 1:
+        u = u[None, :]
+    nrhs = u.shape[0]
+    beta = np.empty((nrhs, igs_problem_info(prob).n), dtype=np.float64) if return_beta else None
+    _check(_lib.igs_build_rhs(prob, _ptr(u), nrhs, _ptr(beta)), "igs_build_rhs")
+    return beta
+
+
+def igs_solve(prob, beta=None, nrhs: int = 1, alpha_out=None, mem: int = IGS_MEM_HOST):
+    """Returns (alpha, residuals).  beta: None (use the built rhs) or (nrhs, n)."""
+    n = igs_problem_info(prob).n
+    if beta is not None and mem == IGS_MEM_HOST:
+        beta = _f64(beta).reshape(-1, n)
+        nrhs = beta.shape[0]
+    if alpha_out is None:
+        alpha_out = np.empty((nrhs, n), dtype=np.float64)
+    res = np.empty(nrhs, dtype=np.float64)
+    _check(_lib.igs_solve(prob, _ptr(beta), int(nrhs), _ptr(alpha_out), _ptr(res), int(mem)), "igs_solve")
+    return alpha_out, res
+
+
+def igs_get_rules(prob, with_ws: bool = False):
+    info = igs_problem_info(prob)
+    nq, d1 = info.n_quad, info.degree + 1
+    eta = np.empty(nq)
+    wb = np.empty((nq, d1))
+    first = np.empty(nq, dtype=np.int32)
+    ws = np.empty((nq, nq)) if with_ws else None
+    _check(_lib.igs_get_rules(prob, _ptr(eta), _ptr(wb), _ptr(first), _ptr(ws)), "igs_get_rules")
+    return eta, wb, first, ws
+
+
+def igs_get_node_geometry(prob):
+    nq = igs_problem_info(prob).n_quad
+    xy = np.empty((nq, 2))
+    J = np.empty(nq)
+    _check(_lib.igs_get_node_geometry(prob, _ptr(xy), _ptr(J)), "igs_get_node_geometry")
+    return xy, J
