@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark: assembled entries/s and solves/s of the weighted-quadrature
+IgA-SGBEM path on the star workload (r = 0.4(1 + 0.2 cos 5 theta), 256-point
+periodic cubic, n = 2048 DoF, degree 3, N_ref = 2, u = log|x - (2,1)|).
+
+One step = one request through the whole path on the device: geometry at the
+nodes, fused assembly of A, right-hand side, Cholesky factorisation and solve
+(MIXED tier: FP32 factor + FP64 iterative refinement to 1e-10).  Rules are
+built once per discretisation (untimed) and reused, as a serving process does.
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SM_COUNT = 152
+FP32_LANES = 128          # FP32 FMA lanes per SM
+SM_MAX_MHZ = 2070.0
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--degree", type=int, default=3)
+    ap.add_argument("--nref", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+# --------------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1703_10016_gb300 import build as build_mod
+    build_mod.build_library()
+    from paper_1703_10016_gb300 import igs
+    from paper_1703_10016_gb300 import workloads as wl
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    n, d, nref = args.n, args.degree, args.nref
+    curve = wl.star_curve()
+    data = wl.Harmonic("log", (2.0, 1.0))
+    ctx = igs.igs_create(local_rank, stream.cuda_stream)
+    geom = igs.igs_create_geometry(ctx, curve.degree, curve.knots, curve.ctrl, curve.weights, curve.closed)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def make(tier):
+        prob = igs.igs_create_problem(geom, d, n, nref, tier)
+        igs.igs_build_weighted_rules(prob)
+        xy = igs.igs_rhs_points(prob)
+        uD = torch.tensor(data.value(xy[:, 0], xy[:, 1])[None, :], dtype=torch.float64, device=dev)
+        alpha = torch.empty((1, n), dtype=torch.float64, device=dev)
+        return prob, uD, alpha
+
+    def step(prob, uD, alpha, times, launches, phases):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        igs.igs_assemble(prob)
+        t = igs.igs_problem_timing(prob)
+        ph = {"geometry": t.geometry_ms, "assemble": t.assemble_ms}
+        nl = t.kernel_launches
+        igs.igs_build_rhs(prob, uD, return_beta=False)
+        t = igs.igs_problem_timing(prob)
+        ph["rhs"] = t.rhs_ms
+        nl += t.kernel_launches
+        _, res = igs.igs_solve(prob, None, 1, alpha, igs.IGS_MEM_DEVICE)
+        t = igs.igs_problem_timing(prob)
+        ph["factor"], ph["solve"] = t.factor_ms, t.solve_ms
+        nl += t.kernel_launches
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        launches.append(nl)
+        phases.append(ph)
+        flush.zero_()                       # evict L2 between steps (outside the timed events)
+        torch.cuda.synchronize()
+        return res[0], t.ir_iterations
+
+    results = {}
+    for name, tier, steps in (("mixed", igs.IGS_MIXED, args.steps), ("fp64", igs.IGS_FP64, max(args.fp64_steps, 1))):
+        prob, uD, alpha = make(tier)
+        scratch = ([], [], [])
+        for _ in range(args.warmup):
+            step(prob, uD, alpha, *scratch)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local_rank)
+        if name == "mixed":
+            clocks.start()
+        times, launches, phases = [], [], []
+        wall0 = time.perf_counter()
+        last = None
+        for _ in range(steps):
+            last = step(prob, uD, alpha, times, launches, phases)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        ck = clocks.stop() if name == "mixed" else None
+        total_ms = sum(times)
+        if world > 1:
+            tt = torch.tensor([total_ms], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(tt.item())
+        A = torch.empty((n, n), dtype=torch.float64, device=dev)
+        igs.igs_assemble(prob, A)
+        results[name] = dict(times=times, total_ms=total_ms, wall=wall, launches=launches, phases=phases,
+                             resid=last[0], ir=last[1], clocks=ck, A=A, prob=prob, uD=uD, steps=steps)
+
+    A32, A64 = results["mixed"]["A"], results["fp64"]["A"]
+    rel_err = float(torch.linalg.norm(A32 - A64) / torch.linalg.norm(A64))
+    bands = {}
+    idx = torch.arange(n, device=dev)
+    dist = (idx[:, None] - idx[None, :]).abs()
+    dist = torch.minimum(dist, n - dist)
+    for label, lo, hi in (("near(|i-j|<=d+1)", 0, d + 1), ("mid(<=8(d+1))", d + 2, 8 * (d + 1)), ("far", 8 * (d + 1) + 1, n)):
+        msk = (dist >= lo) & (dist <= hi)
+        bands[label] = float(torch.linalg.norm((A32 - A64)[msk]) / torch.linalg.norm(A64[msk]))
+
+    # ------------------------------------------------------------------ roofline (assembly kernel)
+    info = igs.igs_problem_info(results["mixed"]["prob"])
+    nq = info.n_quad
+    flops_per_pair = 14 + 4 * (d + 1)          # kernel value (log, division counted as 1) + P/Q contractions
+    algo_flops = nq * nq * flops_per_pair + 2 * n * n * (2 * (d + 1) * nref + 1)
+    asm_ms = statistics.mean(p["assemble"] for p in results["mixed"]["phases"])
+    achieved = algo_flops / (asm_ms * 1e-3) / 1e12
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+    mixed = results["mixed"]
+    step_ms = mixed["total_ms"] / mixed["steps"]
+    value = world * n * n * mixed["steps"] / (mixed["total_ms"] * 1e-3)
+    fp = results["fp64"]
+    fp_step = fp["total_ms"] / fp["steps"]
+    ts = sorted(mixed["times"])
+    p50 = ts[len(ts) // 2]
+    p99 = ts[min(len(ts) - 1, int(math.ceil(0.99 * len(ts))) - 1)]
+    phase_mean = {k: statistics.mean(p[k] for p in mixed["phases"]) for k in mixed["phases"][0]}
+    dominant = max(phase_mean, key=phase_mean.get)
+
+    out = {
+        "metric": "assembled entries/s (assemble + rhs + solve per request, MIXED tier, <=1e-6 rel. error)",
+        "value": value,
+        "unit": "entries/s",
+        "n_gpus": world,
+        "steps": mixed["steps"],
+        "warmup": args.warmup,
+        "ms_per_step": step_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": f"star256 r=0.4(1+0.2cos5t), n={n}, p={d}, N_ref={nref}, u=log|x-(2,1)|, 1 rhs",
+                   "n": n, "degree": d, "n_ref": nref, "n_quad": nq, "parallelism": f"replicas x{world}",
+                   "l2": "256 MB flush between timed steps (outside the step events)"},
+        "solves_per_s": world * mixed["steps"] / (mixed["total_ms"] * 1e-3),
+        "p50_ms": p50,
+        "p99_ms": p99,
+        "phases_ms": phase_mean,
+        "dominant_phase": dominant,
+        "rel_err_vs_fp64": rel_err,
+        "rel_err_vs_fp64_by_band": bands,
+        "ir_iterations": mixed["ir"],
+        "final_residual": mixed["resid"],
+        "fp64": {"value": world * n * n * fp["steps"] / (fp["total_ms"] * 1e-3), "unit": "entries/s",
+                 "ms_per_step": fp_step, "solves_per_s": world * fp["steps"] / (fp["total_ms"] * 1e-3),
+                 "phases_ms": {k: statistics.mean(p[k] for p in fp["phases"]) for k in fp["phases"][0]},
+                 "steps": fp["steps"]},
+        "speedup_mixed_vs_fp64": fp_step / step_ms,
+        "roofline": {"kernel": "k_assemble_tile<float>", "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "work": f"{flops_per_pair} flop per node pair x n_quad^2 + stage-2 contraction",
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+        "gpu_launches": int(sum(mixed["launches"])),
+        "clocks": mixed["clocks"],
+    }
+
+    # ------------------------------------------------------------------ e2e through host buffers
+    if not args.no_e2e:
+        prob = mixed["prob"]
+        e2e_times, h2d, d2h = [], 0, 0
+        for it in range(args.warmup + mixed["steps"]):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g2 = igs.igs_create_geometry(ctx, curve.degree, curve.knots, curve.ctrl, curve.weights, curve.closed)
+            igs.igs_set_geometry(prob, g2)
+            igs.igs_assemble(prob)
+            xy = igs.igs_rhs_points(prob)
+            u = data.value(xy[:, 0], xy[:, 1])[None, :]
+            igs.igs_build_rhs(prob, u, return_beta=False)
+            alpha, res = igs.igs_solve(prob)
+            t1 = time.perf_counter()
+            igs.igs_set_geometry(prob, geom)
+            igs.igs_destroy_geometry(g2)
+            if it >= args.warmup:
+                e2e_times.append(t1 - t0)
+            h2d = 8 * (len(curve.knots) + curve.ctrl.size + (len(curve.ctrl) if curve.weights is not None else 0)) + 8 * u.size
+            d2h = 8 * xy.size + 8 * alpha.size
+        e2e_total = sum(e2e_times)
+        out["e2e"] = {"value": world * n * n * len(e2e_times) / e2e_total, "unit": "entries/s",
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                      "ms_per_step": 1e3 * e2e_total / len(e2e_times),
+                      "includes": "new geometry upload, assemble, rhs points D2H, host u_D, rhs upload, solve, alpha D2H"}
+
+    # ------------------------------------------------------------------ CPU oracle baseline
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(n, d, nref)
+
+    for name in ("mixed", "fp64"):
+        igs.igs_destroy_problem(results[name]["prob"])
+    igs.igs_destroy_geometry(geom)
+    igs.igs_destroy(ctx)
+    return out
+
+
+ORACLE_SAMPLE = """
+import sys, time, json
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle.assembly as oa
+from paper_1703_10016_gb300 import workloads as wl
+rows = np.array({rows!r})
+t0 = time.perf_counter()
+oa.assemble_rows(wl.star_curve(), {n}, {d}, {nref}, rows)
+print(json.dumps({{"seconds": time.perf_counter() - t0}}))
+"""
+
+
+def cpu_baseline(n, d, nref, rows=(0, 511, 1024, 2047)):
+    """The oracle (plain FP64 numpy, single thread) on a bounded sample: full
+    rows of A at the benchmark size."""
+    rows = [r for r in rows if r < n]
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SAMPLE.format(root=ROOT, rows=list(rows), n=n, d=d, nref=nref)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": "entries/s", "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-200:]}
+    sec = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+    return {"value": len(rows) * n / sec, "unit": "entries/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(rows)} full rows of A (star, n={n}, p={d}, N_ref={nref}) with the singular-rule rows, "
+                      f"kernel rows and regular rules they need; {sec:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle, timed on the host cores, bounded sample per step."""
+    if rank != 0:
+        return None
+    n, d, nref = args.n, args.degree, args.nref
+    times = []
+    rows_per_step = 1
+    for it in range(args.warmup + args.steps):
+        base = cpu_baseline(n, d, nref, rows=(it * 97 % n,))
+        if base["value"] is None:
+            return {"impl": "reference", "unavailable": base["sample"]}
+        if it >= args.warmup:
+            times.append(rows_per_step * n / base["value"])
+    total = sum(times)
+    value = args.steps * rows_per_step * n / total
+    return {"metric": "assembled entries/s (assemble + rhs + solve per request, MIXED tier, <=1e-6 rel. error)",
+            "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"star256 r=0.4(1+0.2cos5t), n={n}, p={d}, N_ref={nref}, u=log|x-(2,1)|, 1 rhs",
+                       "parallelism": "single CPU thread"},
+            "cpu_baseline": {"value": value, "unit": "entries/s", "cores": 1, "kind": "oracle",
+                             "sample": "one full row of A per step (FP64 numpy oracle)"},
+            "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

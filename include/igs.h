@@ -130,6 +130,13 @@ int igs_destroy_geometry(igs_geom geom);
  * n_ref * n_elems >= 3.  Errors: INVALID_ARG. */
 int igs_create_problem(igs_geom geom, igs_prob* out, int degree, int n_elems, int n_ref, int precision);
 int igs_destroy_problem(igs_prob prob);
+
+/* Attach another boundary curve to an existing problem, keeping its rules
+ * (the rules of Algorithms 1 and 2 depend only on the discretisation, not on
+ * the geometry, Sect. 4).  The new curve must be closed iff the old one was
+ * and have the same parameter interval I.  Invalidates the assembled matrix,
+ * the factor and the right-hand sides.  Errors: INVALID_ARG. */
+int igs_set_geometry(igs_prob prob, igs_geom geom);
 int igs_problem_info(igs_prob prob, igs_info* out);
 int igs_problem_timing(igs_prob prob, igs_timing* out);
 
@@ -158,13 +165,14 @@ int igs_assemble(igs_prob prob, void* A_out, int64_t ld, int mem, int dtype);
  * Requires the rules (built on demand).  Errors: INVALID_ARG, CUDA. */
 int igs_rhs_points(igs_prob prob, double* xy_out, int64_t capacity, int64_t* count);
 
-/* Right-hand side of Sect. 5 for `nrhs` data sets.  uD (HOST) holds, for each
- * data set k, n_rhs_pts values u_D at the points of igs_rhs_points, data set k
- * at uD[k * n_rhs_pts].  Interior (closed) problem: beta = b1/2 - b2/(2pi)
- * (eq. seconda_BIE); open arc: beta = b1 (eq. prima_BIE).  beta is kept in the
- * problem for igs_solve; if beta_out != NULL it is also written (HOST, n x nrhs,
- * data set k at beta_out[k * n]).  Errors: INVALID_ARG, NO_MEMORY, CUDA. */
-int igs_build_rhs(igs_prob prob, const double* uD, int nrhs, double* beta_out);
+/* Right-hand side of Sect. 5 for `nrhs` (1..8) data sets.  uD (`mem` memory)
+ * holds, for each data set k, n_rhs_pts values u_D at the points of
+ * igs_rhs_points, data set k at uD[k * n_rhs_pts].  Interior (closed) problem:
+ * beta = b1/2 - b2/(2pi) (eq. seconda_BIE); open arc: beta = b1 (eq.
+ * prima_BIE).  beta is kept in the problem for igs_solve; if beta_out != NULL
+ * it is also written (`mem` memory, n x nrhs, data set k at beta_out[k * n]).
+ * Errors: INVALID_ARG, NO_MEMORY, CUDA. */
+int igs_build_rhs(igs_prob prob, const double* uD, int nrhs, double* beta_out, int mem);
 
 /* Solve (A + A^T)/2 alpha = beta (eq. sistlin) by Cholesky.  FP64 tier: FP64
  * factorisation.  MIXED tier: FP32 factorisation and FP64 iterative refinement

@@ -250,6 +250,25 @@ int igs_destroy_problem(igs_prob p) {
     API_END
 }
 
+int igs_set_geometry(igs_prob p, igs_geom g) {
+    API_BEGIN
+    REQUIRE(p && g, IGS_E_INVALID_ARG, "NULL argument");
+    REQUIRE(g->ctx == p->geom->ctx, IGS_E_INVALID_ARG, "geometry belongs to another context");
+    REQUIRE(g->closed == p->plan.closed, IGS_E_INVALID_ARG, "closed/open mismatch");
+    REQUIRE(g->a == p->plan.a && g->b == p->plan.b, IGS_E_INVALID_ARG, "parameter interval differs");
+    if (g != p->geom) {
+        p->geom->live_probs--;
+        g->live_probs++;
+        p->geom = g;
+        p->geometry_ready = 0;
+        p->assembled = 0;
+        p->factored = 0;
+        p->rhs_n = 0;
+        if (p->d_rhs_geo) geometry_eval(g, p->d_rhs_t, p->Ng, p->d_rhs_geo, g->ctx->stream);
+    }
+    API_END
+}
+
 int igs_problem_info(igs_prob p, igs_info* out) {
     API_BEGIN
     REQUIRE(p && out, IGS_E_INVALID_ARG, "NULL argument");
@@ -356,10 +375,11 @@ int igs_rhs_points(igs_prob p, double* xy_out, int64_t capacity, int64_t* count)
     API_END
 }
 
-int igs_build_rhs(igs_prob p, const double* uD, int nrhs, double* beta_out) {
+int igs_build_rhs(igs_prob p, const double* uD, int nrhs, double* beta_out, int mem) {
     API_BEGIN
     REQUIRE(p && uD, IGS_E_INVALID_ARG, "NULL argument");
     REQUIRE(nrhs >= 1 && nrhs <= 8, IGS_E_INVALID_ARG, "nrhs must be in [1, 8]");
+    REQUIRE(mem == IGS_MEM_HOST || mem == IGS_MEM_DEVICE, IGS_E_INVALID_ARG, "bad mem kind");
     IGS_CUDA(cudaSetDevice(p->geom->ctx->device));
     cudaStream_t s = p->geom->ctx->stream;
     p->launches = 0;
@@ -370,14 +390,18 @@ int igs_build_rhs(igs_prob p, const double* uD, int nrhs, double* beta_out) {
     cudaEvent_t e0, e1;
     IGS_CUDA(cudaEventCreate(&e0)); IGS_CUDA(cudaEventCreate(&e1));
     IGS_CUDA(cudaEventRecord(e0, s));
-    double* d_u = (double*)dev_alloc(p, sizeof(double) * cnt);
-    IGS_CUDA(cudaMemcpyAsync(d_u, uD, sizeof(double) * cnt, cudaMemcpyHostToDevice, s));
-    rhs_build(p, d_u, nrhs);
+    double* d_u = nullptr;
+    if (mem == IGS_MEM_HOST) {
+        d_u = (double*)dev_alloc(p, sizeof(double) * cnt);
+        IGS_CUDA(cudaMemcpyAsync(d_u, uD, sizeof(double) * cnt, cudaMemcpyHostToDevice, s));
+    }
+    rhs_build(p, d_u ? d_u : uD, nrhs);
     if (beta_out)
-        IGS_CUDA(cudaMemcpyAsync(beta_out, p->d_beta, sizeof(double) * (size_t)P.n * nrhs, cudaMemcpyDeviceToHost, s));
+        IGS_CUDA(cudaMemcpyAsync(beta_out, p->d_beta, sizeof(double) * (size_t)P.n * nrhs,
+                                 mem == IGS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
     IGS_CUDA(cudaEventRecord(e1, s));
     IGS_CUDA(cudaStreamSynchronize(s));
-    dev_free(p, d_u);
+    if (d_u) dev_free(p, d_u);
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     p->timing.rhs_ms = ms;

@@ -30,7 +30,7 @@ IGS_F64, IGS_F32 = 0, 1
 
 EXPORTED = [
     "igs_create", "igs_destroy", "igs_last_error", "igs_create_geometry", "igs_destroy_geometry",
-    "igs_create_problem", "igs_destroy_problem", "igs_problem_info", "igs_problem_timing",
+    "igs_create_problem", "igs_destroy_problem", "igs_set_geometry", "igs_problem_info", "igs_problem_timing",
     "igs_build_weighted_rules", "igs_assemble", "igs_rhs_points", "igs_build_rhs", "igs_solve",
     "igs_get_rules", "igs_get_node_geometry",
 ]
@@ -68,12 +68,13 @@ def _load() -> C.CDLL:
         "igs_destroy_geometry": [vp],
         "igs_create_problem": [vp, C.POINTER(vp), i32, i32, i32, i32],
         "igs_destroy_problem": [vp],
+        "igs_set_geometry": [vp, vp],
         "igs_problem_info": [vp, C.POINTER(igs_info)],
         "igs_problem_timing": [vp, C.POINTER(igs_timing)],
         "igs_build_weighted_rules": [vp],
         "igs_assemble": [vp, vp, i64, i32, i32],
         "igs_rhs_points": [vp, vp, i64, C.POINTER(i64)],
-        "igs_build_rhs": [vp, vp, i32, vp],
+        "igs_build_rhs": [vp, vp, i32, vp, i32],
         "igs_solve": [vp, vp, i32, vp, vp, i32],
         "igs_get_rules": [vp, vp, vp, vp, vp],
         "igs_get_node_geometry": [vp, vp, vp],
@@ -151,6 +152,10 @@ def igs_destroy_problem(prob) -> None:
     _check(_lib.igs_destroy_problem(prob), "igs_destroy_problem")
 
 
+def igs_set_geometry(prob, geom) -> None:
+    _check(_lib.igs_set_geometry(prob, geom), "igs_set_geometry")
+
+
 def igs_problem_info(prob) -> igs_info:
     out = igs_info()
     _check(_lib.igs_problem_info(prob, C.byref(out)), "igs_problem_info")
@@ -189,14 +194,23 @@ def igs_rhs_points(prob) -> np.ndarray:
     return xy
 
 
-def igs_build_rhs(prob, uD, return_beta: bool = True) -> np.ndarray | None:
-    """uD: (nrhs, n_rhs_pts) values at igs_rhs_points (HOST)."""
+def igs_build_rhs(prob, uD, return_beta: bool = True):
+    """uD: (nrhs, n_rhs_pts) values at igs_rhs_points: a host array, or a CUDA
+    tensor (device memory; beta is then returned as a CUDA tensor)."""
+    if hasattr(uD, "is_cuda") and uD.is_cuda:
+        u = uD if uD.dim() == 2 else uD[None, :]
+        beta = None
+        if return_beta:
+            import torch
+            beta = torch.empty((u.shape[0], igs_problem_info(prob).n), dtype=torch.float64, device=u.device)
+        _check(_lib.igs_build_rhs(prob, _ptr(u), u.shape[0], _ptr(beta), IGS_MEM_DEVICE), "igs_build_rhs")
+        return beta
     u = _f64(uD)
     if u.ndim == 1:
         u = u[None, :]
     nrhs = u.shape[0]
     beta = np.empty((nrhs, igs_problem_info(prob).n), dtype=np.float64) if return_beta else None
-    _check(_lib.igs_build_rhs(prob, _ptr(u), nrhs, _ptr(beta)), "igs_build_rhs")
+    _check(_lib.igs_build_rhs(prob, _ptr(u), nrhs, _ptr(beta), IGS_MEM_HOST), "igs_build_rhs")
     return beta
 
 
