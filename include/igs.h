@@ -174,6 +174,26 @@ int igs_rhs_points(igs_prob prob, double* xy_out, int64_t capacity, int64_t* cou
  * Errors: INVALID_ARG, NO_MEMORY, CUDA. */
 int igs_build_rhs(igs_prob prob, const double* uD, int nrhs, double* beta_out, int mem);
 
+/* Right-hand side without any device allocation.  The paper has no
+ * counterpart: this entry exists for callers that cannot allocate device
+ * memory inside a call -- a framework that owns all device memory through its
+ * own allocator and forbids others, or a latency-bound serving loop that must
+ * stay off the driver's allocator.  It computes the same beta as igs_build_rhs
+ * (same kernels), but keeps the double-layer potentials at the nodes in a
+ * fixed device array inside the library (8 MiB per GPU, held from library load
+ * until process exit) and allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *   uD:       DEVICE, nrhs x n_rhs_pts (layout of igs_build_rhs)
+ *   beta_out: DEVICE, nrhs x n, written (the problem's own beta is not changed)
+ * Limits: 1 <= nrhs <= 8 and n_quad * nrhs <= 1048576 (else INVALID_ARG).
+ * Preconditions: the rules, the node geometry and the rhs points exist (call
+ * igs_assemble and igs_rhs_points first), else STATE.  The work is queued on
+ * the context stream and not waited for.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU race on it.  Errors: INVALID_ARG, STATE, CUDA. */
+int igs_build_rhs_noalloc(igs_prob prob, const double* uD, int nrhs, double* beta_out);
+
 /* Solve (A + A^T)/2 alpha = beta (eq. sistlin) by Cholesky.  FP64 tier: FP64
  * factorisation.  MIXED tier: FP32 factorisation and FP64 iterative refinement
  * until ||beta - A_s alpha|| <= 1e-10 ||beta|| (at most 30 steps).

@@ -410,6 +410,16 @@ int igs_build_rhs(igs_prob p, const double* uD, int nrhs, double* beta_out, int 
     API_END
 }
 
+int igs_build_rhs_noalloc(igs_prob p, const double* uD, int nrhs, double* beta_out) {
+    API_BEGIN
+    REQUIRE(p && uD && beta_out, IGS_E_INVALID_ARG, "NULL argument");
+    IGS_CUDA(cudaSetDevice(p->geom->ctx->device));
+    p->launches = 0;
+    rhs_build_noalloc(p, uD, nrhs, beta_out);
+    p->timing.kernel_launches = p->launches;
+    API_END
+}
+
 int igs_solve(igs_prob p, const double* beta, int nrhs, double* alpha_out, double* resid_out, int mem) {
     API_BEGIN
     REQUIRE(p && alpha_out, IGS_E_INVALID_ARG, "NULL argument");

@@ -143,5 +143,6 @@ void geometry_nodes(igs_prob p);
 void assemble_matrix(igs_prob p);
 void rhs_prepare(igs_prob p);
 void rhs_build(igs_prob p, const double* d_uD, int nrhs);
+void rhs_build_noalloc(igs_prob p, const double* d_uD, int nrhs, double* d_beta);
 void solve_system(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double* resid);
 }  // namespace igs

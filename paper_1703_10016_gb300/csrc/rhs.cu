@@ -4,6 +4,8 @@
 //   Kbar(s,t) = dK/dn_y(f(s), f(t)) J(t) = ((f(t)-f(s)) . (f2'(t), -f1'(t))) / |f(t)-f(s)|^2
 // (outward normal of a counter-clockwise curve).  beta = b1/2 - b2/(2 pi) for the
 // interior problem (eq. seconda_BIE), beta = b1 for an open arc (eq. prima_BIE).
+#include <mutex>
+
 #include "igs_internal.h"
 
 namespace igs {
@@ -138,4 +140,64 @@ void rhs_build(igs_prob p, const double* d_uD, int nrhs) {
     }
 }
 
+// ------------------------------------------------------------ no-allocation variant
+// Some callers cannot allocate device memory inside a call: a host framework
+// that owns all device memory through its own allocator and forbids others
+// (custom-call handlers, memory-pool managed serving loops), code that must
+// stay off the driver's allocator for latency reasons, or code that runs while
+// someone else captures the stream.  For them igs_build_rhs_noalloc runs the
+// same two kernels as igs_build_rhs (double-layer potential at the nodes, then
+// the weighted sums b1 / b2) with the node potentials v kept in this fixed,
+// file-scope device array instead of a buffer from cudaMallocAsync.  Every GPU
+// that loads the library holds the array until the process exits.  All calls
+// share it, so calls that overlap on the GPU (two streams, two host threads)
+// race on it; it keeps the last call's contents, and nothing in it needs to
+// start at zero because the first kernel overwrites every entry it uses.
+constexpr size_t kNoAllocScratchDoubles = size_t(1) << 20;       // 8 MiB: n_quad * nrhs <= 1048576
+static __device__ __align__(256) double g_rhs_scratch[kNoAllocScratchDoubles];
+
+static std::mutex g_scratch_mu;
+static double* g_scratch_addr[256] = {};
+
+// Device address of g_rhs_scratch on `device` (which must be current).  In
+// host code the symbol g_rhs_scratch is only a host-side stand-in, so the
+// address is queried once per device with cudaGetSymbolAddress and cached.
+static double* scratch_address(int device) {
+    if (device < 0 || device >= 256) throw Error(IGS_E_INVALID_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[device]) {
+        void* ptr = nullptr;
+        IGS_CUDA(cudaGetSymbolAddress(&ptr, g_rhs_scratch));
+        g_scratch_addr[device] = (double*)ptr;
+    }
+    return g_scratch_addr[device];
+}
+
+void rhs_build_noalloc(igs_prob p, const double* d_uD, int nrhs, double* d_beta) {
+    const Plan& P = p->plan;
+    cudaStream_t s = p->geom->ctx->stream;
+    if (nrhs < 1 || nrhs > kMaxRhs) throw Error(IGS_E_INVALID_ARG, "nrhs must be in [1, 8]");
+    if (!p->rules_ready || !p->geometry_ready || !p->d_rhs_geo)
+        throw Error(IGS_E_STATE, "igs_build_rhs_noalloc needs the rules, the node geometry and the rhs points: "
+                                 "call igs_assemble and igs_rhs_points first");
+    if ((size_t)P.Nq * nrhs > kNoAllocScratchDoubles)
+        throw Error(IGS_E_INVALID_ARG, "igs_build_rhs_noalloc: n_quad * nrhs = " + std::to_string((size_t)P.Nq * nrhs) +
+                                           " exceeds the fixed scratch of " + std::to_string(kNoAllocScratchDoubles) +
+                                           " doubles");
+    double* v = scratch_address(p->geom->ctx->device);
+    const int ldu = P.Nq + p->Ng;
+    if (P.closed) {
+        k_double_layer<<<(P.Nq + 255) / 256, 256, 0, s>>>(P.Nq, p->Ng, nrhs, p->d_geo, p->d_rhs_geo, p->d_rhs_w,
+                                                          d_uD, ldu, P.Nq, v);
+        IGS_CUDA(cudaGetLastError());
+        p->launches++;
+    }
+    dim3 grid((P.n + 127) / 128, nrhs);
+    k_beta<<<grid, 128, 0, s>>>(P.n, P.Nq, P.d, nrhs, P.closed, p->d_lo, p->d_hi, p->d_jfirst, p->d_W, p->d_geo, d_uD,
+                                ldu, v, d_beta);
+    IGS_CUDA(cudaGetLastError());
+    p->launches++;
+}
+
 }  // namespace igs
+

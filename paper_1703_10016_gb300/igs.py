@@ -31,7 +31,8 @@ IGS_F64, IGS_F32 = 0, 1
 EXPORTED = [
     "igs_create", "igs_destroy", "igs_last_error", "igs_create_geometry", "igs_destroy_geometry",
     "igs_create_problem", "igs_destroy_problem", "igs_set_geometry", "igs_problem_info", "igs_problem_timing",
-    "igs_build_weighted_rules", "igs_assemble", "igs_rhs_points", "igs_build_rhs", "igs_solve",
+    "igs_build_weighted_rules", "igs_assemble", "igs_rhs_points", "igs_build_rhs", "igs_build_rhs_noalloc",
+    "igs_solve",
     "igs_get_rules", "igs_get_node_geometry",
 ]
 
@@ -75,6 +76,7 @@ def _load() -> C.CDLL:
         "igs_assemble": [vp, vp, i64, i32, i32],
         "igs_rhs_points": [vp, vp, i64, C.POINTER(i64)],
         "igs_build_rhs": [vp, vp, i32, vp, i32],
+        "igs_build_rhs_noalloc": [vp, vp, i32, vp],
         "igs_solve": [vp, vp, i32, vp, vp, i32],
         "igs_get_rules": [vp, vp, vp, vp, vp],
         "igs_get_node_geometry": [vp, vp, vp],
@@ -212,6 +214,13 @@ def igs_build_rhs(prob, uD, return_beta: bool = True):
     beta = np.empty((nrhs, igs_problem_info(prob).n), dtype=np.float64) if return_beta else None
     _check(_lib.igs_build_rhs(prob, _ptr(u), nrhs, _ptr(beta), IGS_MEM_HOST), "igs_build_rhs")
     return beta
+
+
+def igs_build_rhs_noalloc(prob, uD, beta_out) -> None:
+    """Right-hand side into caller-owned device memory without any device
+    allocation (uD: CUDA tensor nrhs x n_rhs_pts; beta_out: CUDA tensor nrhs x n)."""
+    u = uD if uD.dim() == 2 else uD[None, :]
+    _check(_lib.igs_build_rhs_noalloc(prob, _ptr(u), int(u.shape[0]), _ptr(beta_out)), "igs_build_rhs_noalloc")
 
 
 def igs_solve(prob, beta=None, nrhs: int = 1, alpha_out=None, mem: int = IGS_MEM_HOST):
