@@ -180,12 +180,12 @@ int igs_build_rhs(igs_prob prob, const double* uD, int nrhs, double* beta_out, i
  * own allocator and forbids others, or a latency-bound serving loop that must
  * stay off the driver's allocator.  It computes the same beta as igs_build_rhs
  * (same kernels), but keeps the double-layer potentials at the nodes in a
- * fixed device array inside the library (8 MiB per GPU, held from library load
+ * fixed device array inside the library (16 MiB per GPU, held from library load
  * until process exit) and allocates nothing: no cudaMalloc, cudaFree or
  * allocating library routine.
  *   uD:       DEVICE, nrhs x n_rhs_pts (layout of igs_build_rhs)
  *   beta_out: DEVICE, nrhs x n, written (the problem's own beta is not changed)
- * Limits: 1 <= nrhs <= 8 and n_quad * nrhs <= 1048576 (else INVALID_ARG).
+ * Limits: 1 <= nrhs <= 8 and 9 * n_quad * nrhs <= 2097152 (else INVALID_ARG).
  * Preconditions: the rules, the node geometry and the rhs points exist (call
  * igs_assemble and igs_rhs_points first), else STATE.  The work is queued on
  * the context stream and not waited for.  The first call on a device looks up

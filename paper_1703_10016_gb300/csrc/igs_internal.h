@@ -116,7 +116,10 @@ struct igs_prob_s {
 
     // matrix and solve
     void* d_A = nullptr;          // [n][n] tier type (row-major)
-    void* d_F = nullptr;          // [n][n] Cholesky factor (tier type)
+    void* d_F = nullptr;          // [n][n] Cholesky factor (tier type): lower = L, upper = L^T
+    void* d_diagL = nullptr;      // [n][64] factored diagonal blocks of L (tier type)
+    void* d_diagLinv = nullptr;   // [n][64] inverses of the diagonal blocks of L (tier type)
+    cudaGraphExec_t factor_exec = nullptr;   // captured factorisation (fixed pointers and sizes)
     double* d_As64 = nullptr;     // (A+A^T)/2 in FP64 for residuals (MIXED)
     int rhs_n = 0;
     double* d_beta = nullptr;     // [nrhs][n]

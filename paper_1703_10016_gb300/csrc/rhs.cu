@@ -4,6 +4,15 @@
 //   Kbar(s,t) = dK/dn_y(f(s), f(t)) J(t) = ((f(t)-f(s)) . (f2'(t), -f1'(t))) / |f(t)-f(s)|^2
 // (outward normal of a counter-clockwise curve).  beta = b1/2 - b2/(2 pi) for the
 // interior problem (eq. seconda_BIE), beta = b1 for an open arc (eq. prima_BIE).
+//
+// The double-layer potentials v_k(eta_m) = sum_g w_g Kbar(eta_m, t_g) u_k(t_g) are
+// an N_quad x N_GQ kernel sum.  The Gauss range is split in kSplit slices, one
+// grid row each, so that every node has kSplit partial sums (reduced in a fixed
+// order by k_beta: results do not depend on scheduling).  MIXED tier: FP32 with
+// float-float coordinate differences for every pair except the Gauss points of
+// the node's refined element and its two neighbours, where the numerator
+// (f(t)-f(s)).n(t) is second-order small; those are summed in FP64 by
+// k_double_layer_near into one more partial slot.  FP64 tier: every pair in FP64.
 #include <mutex>
 
 #include "igs_internal.h"
@@ -12,6 +21,7 @@ namespace igs {
 
 constexpr int kMaxRhs = 8;
 constexpr int kRhsChunk = 256;
+constexpr int kSplit = 8;
 
 __global__ void k_rhs_points(int M, int G, double a, double hf, const double* __restrict__ gx,
                              const double* __restrict__ gw, double* __restrict__ t, double* __restrict__ w) {
@@ -22,43 +32,151 @@ __global__ void k_rhs_points(int M, int G, double a, double hf, const double* __
     w[q] = hf * gw[g];
 }
 
-// v[k][m] = sum_g w_g Kbar(eta_m, t_g) u_D^k(t_g)   (FP64)
-__global__ void __launch_bounds__(256) k_double_layer(int Nq, int Ng, int nrhs, const double* __restrict__ geo,
-                                                      const double* __restrict__ rgeo, const double* __restrict__ rw,
-                                                      const double* __restrict__ uD, int ldu, int off,
-                                                      double* __restrict__ v) {
-    __shared__ double sx[kRhsChunk], sy[kRhsChunk], sx1[kRhsChunk], sy1[kRhsChunk];
-    __shared__ double su[kMaxRhs][kRhsChunk];
+__device__ __forceinline__ void split2(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+__device__ __forceinline__ bool near_elem(int eg, int em, int M) {
+    int dd = eg - em;
+    if (dd < 0) dd = -dd;
+    if (dd > M / 2) dd = M - dd;              // closed curve: cyclic distance
+    return dd <= 1;
+}
+
+// MIXED far field: partial sums over Gauss slice blockIdx.y, FP32, near pairs masked.
+template <int NR>
+__global__ void __launch_bounds__(256) k_double_layer_f(int Nq, int Ng, int M, const double* __restrict__ geo,
+                                                        const int* __restrict__ fspan, const double* __restrict__ rgeo,
+                                                        const double* __restrict__ rw, const double* __restrict__ uD,
+                                                        int ldu, int off, double* __restrict__ part) {
+    __shared__ float sxh[kRhsChunk], sxl[kRhsChunk], syh[kRhsChunk], syl[kRhsChunk];
+    __shared__ float sa[kRhsChunk], sb[kRhsChunk];
+    __shared__ int se[kRhsChunk];
+    __shared__ float su[NR][kRhsChunk];
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = m < Nq;
-    const double xm = live ? geo[m] : 0.0, ym = live ? geo[Nq + m] : 0.0;
-    double acc[kMaxRhs];
-    for (int k = 0; k < kMaxRhs; ++k) acc[k] = 0.0;
-    for (int g0 = 0; g0 < Ng; g0 += kRhsChunk) {
-        const int cn = min(kRhsChunk, Ng - g0);
+    float xh = 0, xl = 0, yh = 0, yl = 0;
+    int em = 0;
+    if (live) {
+        split2(geo[m], xh, xl);
+        split2(geo[Nq + m], yh, yl);
+        em = fspan[m];
+    }
+    float acc[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) acc[k] = 0.f;
+    const int per = (Ng + kSplit - 1) / kSplit;
+    const int g_lo = blockIdx.y * per, g_hi = min(Ng, g_lo + per);
+    for (int g0 = g_lo; g0 < g_hi; g0 += kRhsChunk) {
+        const int cn = min(kRhsChunk, g_hi - g0);
         __syncthreads();
         for (int q = threadIdx.x; q < cn; q += blockDim.x) {
             const int g = g0 + q;
-            sx[q] = rgeo[g]; sy[q] = rgeo[Ng + g]; sx1[q] = rgeo[2 * Ng + g]; sy1[q] = rgeo[3 * Ng + g];
-            for (int k = 0; k < nrhs; ++k) su[k][q] = rw[g] * uD[(size_t)k * ldu + off + g];
+            split2(rgeo[g], sxh[q], sxl[q]);
+            split2(rgeo[Ng + g], syh[q], syl[q]);
+            sa[q] = (float)rgeo[3 * Ng + g];          //  f2'(t)
+            sb[q] = (float)(-rgeo[2 * Ng + g]);       // -f1'(t)
+            se[q] = g / kGaussRhs;
+            const double w = rw[g];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) su[k][q] = (float)(w * uD[(size_t)k * ldu + off + g]);
+        }
+        __syncthreads();
+        if (live) {
+#pragma unroll 4
+            for (int q = 0; q < cn; ++q) {
+                const float dx = (sxh[q] - xh) + (sxl[q] - xl);
+                const float dy = (syh[q] - yh) + (syl[q] - yl);
+                const float num = dx * sa[q] + dy * sb[q];
+                const float r2 = dx * dx + dy * dy;
+                float kb = num * __frcp_rn(r2);
+                kb = near_elem(se[q], em, M) ? 0.f : kb;
+#pragma unroll
+                for (int k = 0; k < NR; ++k) acc[k] = fmaf(kb, su[k][q], acc[k]);
+            }
+        }
+    }
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) part[((size_t)blockIdx.y * NR + k) * Nq + m] = (double)acc[k];
+    }
+}
+
+// FP64 tier: every pair in FP64, partial sums over Gauss slice blockIdx.y.
+template <int NR>
+__global__ void __launch_bounds__(256) k_double_layer_d(int Nq, int Ng, const double* __restrict__ geo,
+                                                        const double* __restrict__ rgeo, const double* __restrict__ rw,
+                                                        const double* __restrict__ uD, int ldu, int off,
+                                                        double* __restrict__ part) {
+    __shared__ double sx[kRhsChunk], sy[kRhsChunk], sa[kRhsChunk], sb[kRhsChunk];
+    __shared__ double su[NR][kRhsChunk];
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = m < Nq;
+    const double xm = live ? geo[m] : 0.0, ym = live ? geo[Nq + m] : 0.0;
+    double acc[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) acc[k] = 0.0;
+    const int per = (Ng + kSplit - 1) / kSplit;
+    const int g_lo = blockIdx.y * per, g_hi = min(Ng, g_lo + per);
+    for (int g0 = g_lo; g0 < g_hi; g0 += kRhsChunk) {
+        const int cn = min(kRhsChunk, g_hi - g0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < cn; q += blockDim.x) {
+            const int g = g0 + q;
+            sx[q] = rgeo[g]; sy[q] = rgeo[Ng + g]; sa[q] = rgeo[3 * Ng + g]; sb[q] = -rgeo[2 * Ng + g];
+            const double w = rw[g];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) su[k][q] = w * uD[(size_t)k * ldu + off + g];
         }
         __syncthreads();
         if (live) {
             for (int q = 0; q < cn; ++q) {
                 const double dx = sx[q] - xm, dy = sy[q] - ym;
-                const double kb = (dx * sy1[q] - dy * sx1[q]) / (dx * dx + dy * dy);
-                for (int k = 0; k < nrhs; ++k) acc[k] += kb * su[k][q];
+                const double kb = (dx * sa[q] + dy * sb[q]) / (dx * dx + dy * dy);
+#pragma unroll
+                for (int k = 0; k < NR; ++k) acc[k] += kb * su[k][q];
             }
         }
     }
-    if (live)
-        for (int k = 0; k < nrhs; ++k) v[(size_t)k * Nq + m] = acc[k];
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) part[((size_t)blockIdx.y * NR + k) * Nq + m] = acc[k];
+    }
 }
 
-// beta[k][i] from the row weights P[m][r] = J_m w^(jfirst+r)_m over N^(i).
+// MIXED near field: Gauss points of the node's element and its two neighbours, FP64.
+__global__ void k_double_layer_near(int Nq, int Ng, int M, int nrhs, const double* __restrict__ geo,
+                                    const int* __restrict__ fspan, const double* __restrict__ rgeo,
+                                    const double* __restrict__ rw, const double* __restrict__ uD, int ldu, int off,
+                                    double* __restrict__ part) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nq) return;
+    const double xm = geo[m], ym = geo[Nq + m];
+    const int em = fspan[m];
+    double acc[kMaxRhs];
+    for (int k = 0; k < nrhs; ++k) acc[k] = 0.0;
+    for (int de = -1; de <= 1; ++de) {
+        int e = em + de;
+        if (e < 0) e += M;
+        if (e >= M) e -= M;
+        for (int q = 0; q < kGaussRhs; ++q) {
+            const int g = e * kGaussRhs + q;
+            const double dx = rgeo[g] - xm, dy = rgeo[Ng + g] - ym;
+            const double kb = (dx * rgeo[3 * Ng + g] - dy * rgeo[2 * Ng + g]) / (dx * dx + dy * dy);
+            const double w = rw[g];
+            for (int k = 0; k < nrhs; ++k) acc[k] += kb * w * uD[(size_t)k * ldu + off + g];
+        }
+    }
+    for (int k = 0; k < nrhs; ++k) part[(size_t)k * Nq + m] = acc[k];
+}
+
+// beta[k][i] from the row weights P[m][r] = J_m w^(jfirst+r)_m over N^(i);
+// v_k(eta_m) is the sum of the np partial slots (fixed order).
 __global__ void k_beta(int n, int Nq, int d, int nrhs, int closed, const int* __restrict__ lo, const int* __restrict__ hi,
                        const int* __restrict__ jfirst, const double* __restrict__ W, const double* __restrict__ geo,
-                       const double* __restrict__ uD, int ldu, const double* __restrict__ v, double* __restrict__ beta) {
+                       const double* __restrict__ uD, int ldu, const double* __restrict__ part, int np,
+                       double* __restrict__ beta) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
     if (i >= n || k >= nrhs) return;
@@ -71,7 +189,11 @@ __global__ void k_beta(int n, int Nq, int d, int nrhs, int closed, const int* __
         if (r < 0 || r > d) continue;
         const double p = geo[4 * Nq + m] * W[m * (d + 1) + r];
         b1 += p * uD[(size_t)k * ldu + m];
-        if (closed) b2 += p * v[(size_t)k * Nq + m];
+        if (closed) {
+            double v = 0.0;
+            for (int s = 0; s < np; ++s) v += part[((size_t)s * nrhs + k) * Nq + m];
+            b2 += p * v;
+        }
     }
     beta[(size_t)k * n + i] = closed ? 0.5 * b1 - b2 / (2.0 * kPi) : b1;
 }
@@ -114,29 +236,73 @@ void rhs_prepare(igs_prob p) {
     dev_free(p, d_g);
 }
 
+// Number of partial-sum slots (each nrhs x N_quad doubles) the kernels need.
+static int rhs_slots(const igs_prob p) {
+    if (!p->plan.closed) return 0;
+    return kSplit + (p->precision == IGS_MIXED ? 1 : 0);
+}
+
+template <int NR>
+static void launch_far(igs_prob p, const double* d_uD, int ldu, double* part) {
+    const Plan& P = p->plan;
+    cudaStream_t s = p->geom->ctx->stream;
+    dim3 grid((P.Nq + 255) / 256, kSplit);
+    if (p->precision == IGS_MIXED)
+        k_double_layer_f<NR><<<grid, 256, 0, s>>>(P.Nq, p->Ng, P.M, p->d_geo, p->d_fspan, p->d_rhs_geo, p->d_rhs_w,
+                                                  d_uD, ldu, P.Nq, part);
+    else
+        k_double_layer_d<NR><<<grid, 256, 0, s>>>(P.Nq, p->Ng, p->d_geo, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq,
+                                                  part);
+    IGS_CUDA(cudaGetLastError());
+}
+
+// beta for nrhs data sets into d_beta, partial sums in `scratch` (rhs_slots x nrhs x N_quad doubles).
+static void rhs_compute(igs_prob p, const double* d_uD, int nrhs, double* d_beta, double* scratch) {
+    const Plan& P = p->plan;
+    cudaStream_t s = p->geom->ctx->stream;
+    const int ldu = P.Nq + p->Ng;
+    const int np = rhs_slots(p);
+    if (P.closed) {
+        switch (nrhs) {
+            case 1: launch_far<1>(p, d_uD, ldu, scratch); break;
+            case 2: launch_far<2>(p, d_uD, ldu, scratch); break;
+            case 3: launch_far<3>(p, d_uD, ldu, scratch); break;
+            case 4: launch_far<4>(p, d_uD, ldu, scratch); break;
+            case 5: launch_far<5>(p, d_uD, ldu, scratch); break;
+            case 6: launch_far<6>(p, d_uD, ldu, scratch); break;
+            case 7: launch_far<7>(p, d_uD, ldu, scratch); break;
+            default: launch_far<8>(p, d_uD, ldu, scratch); break;
+        }
+        p->launches++;
+        if (p->precision == IGS_MIXED) {
+            k_double_layer_near<<<(P.Nq + 127) / 128, 128, 0, s>>>(P.Nq, p->Ng, P.M, nrhs, p->d_geo, p->d_fspan,
+                                                                   p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq,
+                                                                   scratch + (size_t)kSplit * nrhs * P.Nq);
+            IGS_CUDA(cudaGetLastError());
+            p->launches++;
+        }
+    }
+    dim3 grid((P.n + 127) / 128, nrhs);
+    k_beta<<<grid, 128, 0, s>>>(P.n, P.Nq, P.d, nrhs, P.closed, p->d_lo, p->d_hi, p->d_jfirst, p->d_W, p->d_geo, d_uD,
+                                ldu, scratch, np, d_beta);
+    IGS_CUDA(cudaGetLastError());
+    p->launches++;
+}
+
 void rhs_build(igs_prob p, const double* d_uD, int nrhs) {
     const Plan& P = p->plan;
     cudaStream_t s = p->geom->ctx->stream;
     if (nrhs < 1 || nrhs > kMaxRhs) throw Error(IGS_E_INVALID_ARG, "nrhs must be in [1, 8]");
-    const int ldu = P.Nq + p->Ng;
-    double* d_v = nullptr;
-    if (P.closed) {
-        d_v = (double*)dev_alloc(p, sizeof(double) * (size_t)nrhs * P.Nq);
-        k_double_layer<<<(P.Nq + 255) / 256, 256, 0, s>>>(P.Nq, p->Ng, nrhs, p->d_geo, p->d_rhs_geo, p->d_rhs_w,
-                                                          d_uD, ldu, P.Nq, d_v);
-        p->launches++;
-    }
+    double* scratch = nullptr;
+    const int np = rhs_slots(p);
+    if (np > 0) scratch = (double*)dev_alloc(p, sizeof(double) * (size_t)np * nrhs * P.Nq);
     if (p->d_beta && p->rhs_n < nrhs) dev_free(p, p->d_beta);
     if (!p->d_beta) p->d_beta = (double*)dev_alloc(p, sizeof(double) * (size_t)kMaxRhs * P.n);
     p->rhs_n = nrhs;
-    dim3 grid((P.n + 127) / 128, nrhs);
-    k_beta<<<grid, 128, 0, s>>>(P.n, P.Nq, P.d, nrhs, P.closed, p->d_lo, p->d_hi, p->d_jfirst, p->d_W, p->d_geo, d_uD,
-                                ldu, d_v, p->d_beta);
-    p->launches++;
-    IGS_CUDA(cudaGetLastError());
-    if (d_v) {
+    rhs_compute(p, d_uD, nrhs, p->d_beta, scratch);
+    if (scratch) {
         IGS_CUDA(cudaStreamSynchronize(s));
-        dev_free(p, d_v);
+        dev_free(p, scratch);
     }
 }
 
@@ -146,14 +312,14 @@ void rhs_build(igs_prob p, const double* d_uD, int nrhs) {
 // (custom-call handlers, memory-pool managed serving loops), code that must
 // stay off the driver's allocator for latency reasons, or code that runs while
 // someone else captures the stream.  For them igs_build_rhs_noalloc runs the
-// same two kernels as igs_build_rhs (double-layer potential at the nodes, then
-// the weighted sums b1 / b2) with the node potentials v kept in this fixed,
-// file-scope device array instead of a buffer from cudaMallocAsync.  Every GPU
-// that loads the library holds the array until the process exits.  All calls
-// share it, so calls that overlap on the GPU (two streams, two host threads)
-// race on it; it keeps the last call's contents, and nothing in it needs to
-// start at zero because the first kernel overwrites every entry it uses.
-constexpr size_t kNoAllocScratchDoubles = size_t(1) << 20;       // 8 MiB: n_quad * nrhs <= 1048576
+// same kernels as igs_build_rhs (double-layer potentials at the nodes, then
+// the weighted sums b1 / b2) with the partial sums of the potentials kept in
+// this fixed, file-scope device array instead of a buffer from cudaMallocAsync.
+// Every GPU that loads the library holds the array until the process exits.
+// All calls share it, so calls that overlap on the GPU (two streams, two host
+// threads) race on it; it keeps the last call's contents, and nothing in it
+// needs to start at zero because the kernels overwrite every entry they read.
+constexpr size_t kNoAllocScratchDoubles = size_t(1) << 21;       // 16 MiB
 static __device__ __align__(256) double g_rhs_scratch[kNoAllocScratchDoubles];
 
 static std::mutex g_scratch_mu;
@@ -175,29 +341,17 @@ static double* scratch_address(int device) {
 
 void rhs_build_noalloc(igs_prob p, const double* d_uD, int nrhs, double* d_beta) {
     const Plan& P = p->plan;
-    cudaStream_t s = p->geom->ctx->stream;
     if (nrhs < 1 || nrhs > kMaxRhs) throw Error(IGS_E_INVALID_ARG, "nrhs must be in [1, 8]");
     if (!p->rules_ready || !p->geometry_ready || !p->d_rhs_geo)
         throw Error(IGS_E_STATE, "igs_build_rhs_noalloc needs the rules, the node geometry and the rhs points: "
                                  "call igs_assemble and igs_rhs_points first");
-    if ((size_t)P.Nq * nrhs > kNoAllocScratchDoubles)
-        throw Error(IGS_E_INVALID_ARG, "igs_build_rhs_noalloc: n_quad * nrhs = " + std::to_string((size_t)P.Nq * nrhs) +
-                                           " exceeds the fixed scratch of " + std::to_string(kNoAllocScratchDoubles) +
-                                           " doubles");
-    double* v = scratch_address(p->geom->ctx->device);
-    const int ldu = P.Nq + p->Ng;
-    if (P.closed) {
-        k_double_layer<<<(P.Nq + 255) / 256, 256, 0, s>>>(P.Nq, p->Ng, nrhs, p->d_geo, p->d_rhs_geo, p->d_rhs_w,
-                                                          d_uD, ldu, P.Nq, v);
-        IGS_CUDA(cudaGetLastError());
-        p->launches++;
-    }
-    dim3 grid((P.n + 127) / 128, nrhs);
-    k_beta<<<grid, 128, 0, s>>>(P.n, P.Nq, P.d, nrhs, P.closed, p->d_lo, p->d_hi, p->d_jfirst, p->d_W, p->d_geo, d_uD,
-                                ldu, v, d_beta);
-    IGS_CUDA(cudaGetLastError());
-    p->launches++;
+    const size_t need = (size_t)rhs_slots(p) * nrhs * P.Nq;
+    if (need > kNoAllocScratchDoubles)
+        throw Error(IGS_E_INVALID_ARG, "igs_build_rhs_noalloc: needs " + std::to_string(need) +
+                                           " scratch doubles (9 x n_quad x nrhs), more than the fixed " +
+                                           std::to_string(kNoAllocScratchDoubles));
+    double* scratch = scratch_address(p->geom->ctx->device);
+    rhs_compute(p, d_uD, nrhs, d_beta, scratch);
 }
 
 }  // namespace igs
-

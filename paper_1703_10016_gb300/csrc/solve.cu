@@ -1,19 +1,25 @@
 // Solve (A + A^T)/2 alpha = beta (eq. sistlin; A is SPD in the continuous
 // setting, symmetric only up to quadrature error in the discrete one).
 //
-// FP64 tier: blocked right-looking Cholesky in FP64 and two triangular solves.
-// MIXED tier: the same factorisation in FP32, then iterative refinement with
-// FP64 residuals r = beta - A_s alpha until ||r|| <= 1e-10 ||beta||.
-// The factor L is stored in the lower triangle of F and mirrored to the upper
-// triangle (U = L^T) so that both substitutions read contiguous rows.
+// Blocked right-looking Cholesky with 64-wide panels, one graph-captured
+// launch sequence per problem:
+//   k_panel  every CTA factors the 64 x 64 diagonal block (one warp, rows in
+//            registers, columns broadcast by shuffles); CTA 0 stores L11, the
+//            other CTAs turn their 64-row slice of the panel into
+//            L21 = A21 L11^{-T} (a thread per row, right-looking);
+//   k_syrk   trailing update of the lower triangle, 128 x 128 tiles.
+// FP64 tier: all in FP64, then one substitution pair.  MIXED tier: the same in
+// FP32, then iterative refinement with FP64 residuals r = beta - A_s alpha until
+// ||r|| <= 1e-10 ||beta||.  The triangular solves go by 64-row blocks in solve
+// order: the inverted diagonal block (computed once per factorisation, in
+// parallel), then a rank-64 update of the rows not yet solved.
 #include <cmath>
 
 #include "igs_internal.h"
 
 namespace igs {
 
-constexpr int kNB = 64;      // Cholesky panel width
-constexpr int kTB = 32;      // triangular-solve block
+constexpr int kNB = 64;      // Cholesky panel width / triangular-solve block
 
 template <typename T>
 __global__ void k_symmetrize(int n, const T* __restrict__ A, T* __restrict__ F, double* __restrict__ As64) {
@@ -24,154 +30,344 @@ __global__ void k_symmetrize(int n, const T* __restrict__ A, T* __restrict__ F, 
     if (As64) As64[(size_t)i * n + j] = v;
 }
 
-// Unblocked Cholesky of the kb x kb diagonal block at (k0, k0), one CTA.
+// Cholesky of a 32 x 32 SPD block held one row per lane in registers (lane
+// owns row `lane`, entries r[0..31]); column j is broadcast with shuffles.
+// A non-positive pivot sets *flag and is replaced by 1.
 template <typename T>
-__global__ void __launch_bounds__(256) k_potrf(int n, T* __restrict__ F, int k0, int kb, int* __restrict__ flag) {
-    __shared__ T a[kNB][kNB + 1];
-    for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
-        const int i = idx / kb, l = idx % kb;
-        a[i][l] = (l <= i) ? F[(size_t)(k0 + i) * n + k0 + l] : (T)0;
-    }
-    __syncthreads();
-    for (int j = 0; j < kb; ++j) {
-        if (threadIdx.x == 0) {
-            const T dj = a[j][j];
-            if (!(dj > (T)0)) { atomicOr(flag, 1); a[j][j] = (T)1; }
-            else a[j][j] = sqrt(dj);
+__device__ __forceinline__ void potrf32_reg(T (&r)[32], int lane, int* flag) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        T ajj = __shfl_sync(0xffffffffu, r[j], j);
+        if (!(ajj > (T)0)) {
+            if (lane == 0) atomicOr(flag, 1);
+            ajj = (T)1;
         }
-        __syncthreads();
-        const T dj = a[j][j];
-        for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) a[i][j] /= dj;
-        __syncthreads();
-        const int rem = kb - j - 1;
-        for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
-            const int i = j + 1 + idx / rem, l = j + 1 + idx % rem;
-            if (l <= i) a[i][l] -= a[i][j] * a[l][j];
+        const T d = sqrt(ajj);
+        const T rinv = (T)1 / d;
+        if (lane == j) r[j] = d;
+        else if (lane > j) r[j] *= rinv;
+        const T lj = r[j];
+#pragma unroll
+        for (int l = j + 1; l < 32; ++l) {
+            const T c = __shfl_sync(0xffffffffu, lj, l);     // L[l][j]
+            if (lane >= l) r[l] -= lj * c;
         }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
-        const int i = idx / kb, l = idx % kb;
-        if (l <= i) F[(size_t)(k0 + i) * n + k0 + l] = a[i][l];
     }
 }
 
-// Panel: F[i, k0:k0+kb] <- F[i, k0:k0+kb] L11^{-T} for rows i >= k0+kb (64 rows per CTA).
+// Factor the 64 x 64 diagonal block a (shared, lower, padded with identity
+// beyond kb) as 2 x 2 blocks of 32, by warp 0:  L11 = chol(A11),
+// L21 = A21 L11^{-T}, A22 -= L21 L21^T, L22 = chol(A22).  Also writes the
+// reciprocal diagonal rd[i] = 1 / L[i][i].
 template <typename T>
-__global__ void __launch_bounds__(64) k_trsm(int n, T* __restrict__ F, int k0, int kb) {
-    __shared__ T L11[kNB][kNB + 1];
-    __shared__ T X[64][kNB + 1];
-    const int r0 = k0 + kb + blockIdx.x * 64;
-    for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
-        const int i = idx / kb, l = idx % kb;
-        L11[i][l] = (l <= i) ? F[(size_t)(k0 + i) * n + k0 + l] : (T)0;
+__device__ void potrf64_warp(T (*a)[kNB + 1], T* rd, int* flag) {
+    const int lane = threadIdx.x % 32;
+    T r[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) r[l] = a[lane][l];
+    potrf32_reg<T>(r, lane, flag);
+#pragma unroll
+    for (int l = 0; l < 32; ++l) a[lane][l] = (l <= lane) ? r[l] : (T)0;
+    rd[lane] = (T)1 / r[lane];
+    __syncwarp();
+    // L21 row (32 + lane): x L11^T = a21, right-looking in registers
+    T x[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) x[l] = a[32 + lane][l];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        x[c] *= rd[c];
+#pragma unroll
+        for (int l = c + 1; l < 32; ++l) x[l] -= x[c] * a[l][c];
     }
-    for (int idx = threadIdx.x; idx < 64 * kb; idx += blockDim.x) {
-        const int rr = idx / kb, c = idx % kb;
-        X[rr][c] = (r0 + rr < n) ? F[(size_t)(r0 + rr) * n + k0 + c] : (T)0;
+#pragma unroll
+    for (int l = 0; l < 32; ++l) a[32 + lane][l] = x[l];
+    __syncwarp();
+    // A22 row (32 + lane) -= L21 row . L21 rows
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+        T s = (T)0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) s += x[k] * a[32 + l][k];
+        r[l] = a[32 + lane][32 + l] - s;
+    }
+    potrf32_reg<T>(r, lane, flag);
+#pragma unroll
+    for (int l = 0; l < 32; ++l) a[32 + lane][32 + l] = (l <= lane) ? r[l] : (T)0;
+    rd[32 + lane] = (T)1 / r[lane];
+    __syncwarp();
+}
+
+// Panel step at column k0 (width kb): CTA b handles rows k0 + 64 b .. + 63.
+// Every CTA factors the diagonal block (warp 0, registers and shuffles); CTA 0
+// stores L11, the others solve L21 L11^T = A21 with one thread per row, the
+// row held in registers, right-looking (no division in the chain).
+template <typename T>
+__global__ void __launch_bounds__(256) k_panel(int n, T* __restrict__ F, int k0, int kb, T* __restrict__ diagL,
+                                               int* __restrict__ flag) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T (*a)[kNB + 1] = (T (*)[kNB + 1])smem_raw;
+    T* rd = (T*)(a + kNB);
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
+        const int i = idx / kNB, l = idx % kNB;
+        T v;
+        if (i < kb && l < kb) v = (l <= i) ? F[(size_t)(k0 + i) * n + k0 + l] : (T)0;
+        else v = (i == l) ? (T)1 : (T)0;                 // identity padding beyond kb
+        a[i][l] = v;
     }
     __syncthreads();
-    const int rr = threadIdx.x;
-    if (r0 + rr < n) {
-        for (int c = 0; c < kb; ++c) {
-            T s = X[rr][c];
-            for (int l = 0; l < c; ++l) s -= X[rr][l] * L11[c][l];
-            X[rr][c] = s / L11[c][c];
+    if (tid < 32) potrf64_warp<T>(a, rd, flag);
+    __syncthreads();
+    if (blockIdx.x == 0) {
+        for (int idx = tid; idx < kb * kNB; idx += blockDim.x) {
+            const int i = idx / kNB, l = idx % kNB;
+            diagL[(size_t)(k0 + i) * kNB + l] = (l <= i) ? a[i][l] : (T)0;
         }
+        return;
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < 64 * kb; idx += blockDim.x) {
-        const int r = idx / kb, c = idx % kb;
-        if (r0 + r < n) F[(size_t)(r0 + r) * n + k0 + c] = X[r][c];
+    const int r0 = k0 + blockIdx.x * kNB;
+    if (tid < kNB && r0 + tid < n) {
+        T* row = F + (size_t)(r0 + tid) * n + k0;
+        T x[kNB];
+#pragma unroll
+        for (int l = 0; l < kNB; ++l) x[l] = row[l];
+#pragma unroll
+        for (int c = 0; c < kNB; ++c) {
+            x[c] *= rd[c];
+#pragma unroll
+            for (int l = c + 1; l < kNB; ++l) x[l] -= x[c] * a[l][c];
+        }
+#pragma unroll
+        for (int l = 0; l < kNB; ++l) row[l] = x[l];
     }
 }
 
-// Trailing update of the lower triangle: F[i][j] -= sum_l F[i][k0+l] F[j][k0+l],
-// 64 x 64 tiles, 256 threads with 4 x 4 outputs each.
+// Trailing update of the lower triangle: F[i][j] -= sum_l F[i][k0+l] F[j][k0+l]
+// for i >= j >= k0 + kb, 128 x 128 tiles.  The panel rows are staged row-major
+// (coalesced 16-byte loads, conflict-free stores); thread (tx, ty) owns rows
+// ty + 16q and columns tx + 16q (q = 0..7) and reads 16-byte vectors along l,
+// which keeps each quarter-warp's shared reads in distinct banks.
+constexpr int kST = 128;
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
+template <typename T> __host__ __device__ constexpr int syrk_ld() { return kNB + 16 / (int)sizeof(T); }   // row stride: odd in 16-byte units
+
+template <typename T>
+__device__ __forceinline__ T vget(const typename Vec16<T>::type& v, int q);
+template <> __device__ __forceinline__ float vget<float>(const float4& v, int q) {
+    return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+}
+template <> __device__ __forceinline__ double vget<double>(const double2& v, int q) { return q == 0 ? v.x : v.y; }
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_syrk(int n, T* __restrict__ F, int k0, int kb) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N;
+    constexpr int LD = syrk_ld<T>();
     const int ti = blockIdx.y, tj = blockIdx.x;
     if (tj > ti) return;
     const int base = k0 + kb;
-    const int i0 = base + ti * 64, j0 = base + tj * 64;
-    __shared__ T As[64][kNB + 1], Bs[64][kNB + 1];
-    for (int idx = threadIdx.x; idx < 64 * kb; idx += blockDim.x) {
-        const int r = idx / kb, l = idx % kb;
-        As[r][l] = (i0 + r < n) ? F[(size_t)(i0 + r) * n + k0 + l] : (T)0;
-        Bs[r][l] = (j0 + r < n) ? F[(size_t)(j0 + r) * n + k0 + l] : (T)0;
+    const int i0 = base + ti * kST, j0 = base + tj * kST;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T (*As)[LD] = (T (*)[LD])smem_raw;
+    T (*Bs)[LD] = As + kST;
+    const bool vec_ok = (n % VN) == 0 && kb == kNB;
+    if (vec_ok) {
+        constexpr int per_row = kNB / VN;
+        for (int idx = threadIdx.x; idx < kST * per_row; idx += blockDim.x) {
+            const int rr = idx / per_row, q = idx % per_row;
+            V va, vb;
+            if (i0 + rr < n) va = *(const V*)(F + (size_t)(i0 + rr) * n + k0 + q * VN);
+            else va = V{};
+            if (j0 + rr < n) vb = *(const V*)(F + (size_t)(j0 + rr) * n + k0 + q * VN);
+            else vb = V{};
+            *(V*)&As[rr][q * VN] = va;
+            *(V*)&Bs[rr][q * VN] = vb;
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < kST * kNB; idx += blockDim.x) {
+            const int rr = idx / kNB, l = idx % kNB;
+            As[rr][l] = (i0 + rr < n && l < kb) ? F[(size_t)(i0 + rr) * n + k0 + l] : (T)0;
+            Bs[rr][l] = (j0 + rr < n && l < kb) ? F[(size_t)(j0 + rr) * n + k0 + l] : (T)0;
+        }
     }
     __syncthreads();
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    T acc[4][4] = {};
-    for (int l = 0; l < kb; ++l) {
-        T av[4], bv[4];
+    T acc[8][8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { av[q] = As[ty + 16 * q][l]; bv[q] = Bs[tx + 16 * q][l]; }
+    for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 8; ++c) acc[r][c] = (T)0;
+    for (int l = 0; l < kNB; l += VN) {
+        V av[8], bv[8];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[r][c] += av[r] * bv[c];
+        for (int q = 0; q < 8; ++q) {
+            av[q] = *(const V*)&As[ty + 16 * q][l];
+            bv[q] = *(const V*)&Bs[tx + 16 * q][l];
+        }
+#pragma unroll
+        for (int u = 0; u < VN; ++u)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const T ar = vget<T>(av[r], u);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] += ar * vget<T>(bv[c], u);
+            }
+    }
+    // epilogue: read every C entry before writing any (all loads in flight at once)
+    T cv[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int i = i0 + ty + 16 * r;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int j = j0 + tx + 16 * c;
+            cv[r][c] = (i < n && j <= i) ? F[(size_t)i * n + j] : (T)0;
+        }
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 8; ++r) {
+        const int i = i0 + ty + 16 * r;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
-            if (i < n && j < n && j <= i) F[(size_t)i * n + j] -= acc[r][c];
+        for (int c = 0; c < 8; ++c) {
+            const int j = j0 + tx + 16 * c;
+            if (i < n && j <= i) F[(size_t)i * n + j] = cv[r][c] - acc[r][c];
         }
+    }
 }
 
+// Diagonal blocks back into F, and U = L^T into the upper triangle.
 template <typename T>
-__global__ void k_mirror(int n, T* __restrict__ F) {
+__global__ void k_finalize(int n, T* __restrict__ F, const T* __restrict__ diagL) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
-    if (j < i) F[(size_t)j * n + i] = F[(size_t)i * n + j];
+    if (j > i) return;
+    T v;
+    if (i / kNB == j / kNB) v = diagL[(size_t)i * kNB + (j % kNB)];
+    else v = F[(size_t)i * n + j];
+    F[(size_t)i * n + j] = v;
+    if (j < i) F[(size_t)j * n + i] = v;
 }
 
-// Forward (lower=1: L y = b) or backward (lower=0: U x = y, U = L^T in the upper
-// triangle) substitution for nrhs vectors, one CTA of 1024 threads; X holds b
-// on entry and the solution on exit (X[k*n + i]).
+// Inverses of the 64 x 64 diagonal blocks of L (one CTA per block, after the
+// factorisation, off the panel critical path): li[i][c] = -(sum_{l=c}^{i-1}
+// L[i][l] li[l][c]) / L[i][i], row by row, all columns of a row at once.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_trsv(int n, const T* __restrict__ F, T* __restrict__ X, int nrhs, int lower) {
-    __shared__ T xb[8][kTB];
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int nblk = (n + kTB - 1) / kTB;
+__global__ void __launch_bounds__(256) k_diag_inverse(int n, const T* __restrict__ diagL, T* __restrict__ diagLinv) {
+    __shared__ T a[kNB][kNB + 1], li[kNB][kNB + 1];
+    const int b0 = blockIdx.x * kNB, bn = min(kNB, n - b0);
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
+        const int i = idx / kNB, l = idx % kNB;
+        const T v = (i < bn && l < bn) ? diagL[(size_t)(b0 + i) * kNB + l] : (T)(i == l ? 1 : 0);
+        a[i][l] = v;
+        li[i][l] = (i == l) ? (T)1 / v : (T)0;
+    }
+    __syncthreads();
+    const int c = tid / 4, part = tid % 4;
+    for (int i = 1; i < kNB; ++i) {
+        T s = (T)0;
+        if (c < i)
+            for (int l = c + part; l < i; l += 4) s += a[i][l] * li[l][c];
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        if (c < i && part == 0) li[i][c] = -s * li[i][i];
+        __syncthreads();
+    }
+    for (int idx = tid; idx < bn * kNB; idx += blockDim.x) {
+        const int i = idx / kNB, l = idx % kNB;
+        diagLinv[(size_t)(b0 + i) * kNB + l] = li[i][l];
+    }
+}
+
+// Forward (lower=1: L y = b) or backward (lower=0: L^T x = y, U = L^T in the
+// upper triangle) substitution for NR vectors, one CTA of 1024 threads, by
+// 64-row blocks in solve order ("right-looking"): the block is solved with the
+// inverted diagonal block (a 64 x 64 matrix-vector product), then every row
+// not yet solved subtracts its 64-column slice times the new block of the
+// solution -- each thread streams its row slice as 16-byte vectors.  X holds b
+// on entry and the solution on exit (X[k*n + i]).
+constexpr int kTrsvThreads = 1024;
+template <typename T, int NR>
+__global__ void __launch_bounds__(kTrsvThreads) k_trsv(int n, const T* __restrict__ F, const T* __restrict__ Linv,
+                                                       T* __restrict__ X, int lower) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N;
+    __shared__ T rb[NR][kNB];
+    __shared__ __align__(16) T yb[NR][kNB];
+    const int nblk = (n + kNB - 1) / kNB;
+    const bool vec_ok = (n % VN) == 0;
     for (int bb = 0; bb < nblk; ++bb) {
         const int blk = lower ? bb : nblk - 1 - bb;
-        const int b0 = blk * kTB, bn = min(kTB, n - b0);
-        // 1. update: X[b0+w] -= sum over solved columns (warp w owns row b0+w, lanes stride columns)
-        const int c_lo = lower ? 0 : b0 + bn, c_hi = lower ? b0 : n;
-        if (warp < bn) {
-            const int row = b0 + warp;
-            T part[8];
-            for (int k = 0; k < nrhs; ++k) part[k] = (T)0;
-            for (int c = c_lo + lane; c < c_hi; c += 32) {
-                const T f = F[(size_t)row * n + c];
-                for (int k = 0; k < nrhs; ++k) part[k] += f * X[(size_t)k * n + c];
+        const int b0 = blk * kNB, bn = min(kNB, n - b0);
+        for (int idx = threadIdx.x; idx < NR * kNB; idx += blockDim.x) {
+            const int k = idx / kNB, i = idx % kNB;
+            rb[k][i] = (i < bn) ? X[(size_t)k * n + b0 + i] : (T)0;
+        }
+        __syncthreads();
+        // y = Linv r (lower) or Linv^T r (upper); four threads per output
+        for (int o = threadIdx.x / 4; o < NR * kNB; o += blockDim.x / 4) {
+            const int part = threadIdx.x % 4;
+            const int k = o / kNB, i = o % kNB;
+            T s = (T)0;
+            if (i < bn) {
+                if (lower)
+                    for (int l = part; l <= i; l += 4) s += Linv[(size_t)(b0 + i) * kNB + l] * rb[k][l];
+                else
+                    for (int l = i + part; l < bn; l += 4) s += Linv[(size_t)(b0 + l) * kNB + i] * rb[k][l];
             }
-            for (int k = 0; k < nrhs; ++k) {
-                T v = part[k];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) xb[k][warp] = X[(size_t)k * n + row] - v;
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            if (part == 0) {
+                yb[k][i] = (i < bn) ? s : (T)0;
+                if (i < bn) X[(size_t)k * n + b0 + i] = s;
             }
         }
         __syncthreads();
-        // 2. triangular block solve (warp k handles right-hand side k)
-        if (warp < nrhs) {
-            const int k = warp;
-            T xv = (lane < bn) ? xb[k][lane] : (T)0;
-            for (int q = 0; q < bn; ++q) {
-                const int c = lower ? q : bn - 1 - q;
-                const int row = b0 + c;
-                const T diag = F[(size_t)row * n + row];
-                T xc = __shfl_sync(0xffffffffu, xv, c) / diag;
-                if (lane == c) xv = xc;
-                // eliminate from the not-yet-solved rows of the block
-                const bool pending = lower ? (lane > c && lane < bn) : (lane < c);
-                if (pending) xv -= F[(size_t)(b0 + lane) * n + row] * xc;
+        // update the rows still to solve with columns b0 .. b0+bn-1
+        const int u_lo = lower ? b0 + bn : 0, u_hi = lower ? n : b0;
+        for (int row = u_lo + threadIdx.x; row < u_hi; row += blockDim.x) {
+            const T* frow = F + (size_t)row * n + b0;
+            T acc[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) acc[k] = (T)0;
+            if (vec_ok && bn == kNB) {
+#pragma unroll 4
+                for (int q = 0; q < kNB / VN; ++q) {
+                    const V fv = *(const V*)(frow + q * VN);
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) {
+                        const V yv = *(const V*)&yb[k][q * VN];
+#pragma unroll
+                        for (int u = 0; u < VN; ++u) acc[k] += vget<T>(fv, u) * vget<T>(yv, u);
+                    }
+                }
+            } else {
+                for (int l = 0; l < bn; ++l) {
+                    const T f = frow[l];
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) acc[k] += f * yb[k][l];
+                }
             }
-            if (lane < bn) X[(size_t)k * n + b0 + lane] = xv;
+#pragma unroll
+            for (int k = 0; k < NR; ++k) X[(size_t)k * n + row] -= acc[k];
         }
         __syncthreads();
+    }
+}
+
+template <typename T>
+static void launch_trsv(int n, const T* F, const T* Linv, T* X, int nrhs, int lower, cudaStream_t s) {
+    switch (nrhs) {
+        case 1: k_trsv<T, 1><<<1, kTrsvThreads, 0, s>>>(n, F, Linv, X, lower); break;
+        case 2: k_trsv<T, 2><<<1, kTrsvThreads, 0, s>>>(n, F, Linv, X, lower); break;
+        case 3: k_trsv<T, 3><<<1, kTrsvThreads, 0, s>>>(n, F, Linv, X, lower); break;
+        case 4: k_trsv<T, 4><<<1, kTrsvThreads, 0, s>>>(n, F, Linv, X, lower); break;
+        case 5: k_trsv<T, 5><<<1, kTrsvThreads, 0, s>>>(n, F, Linv, X, lower); break;
+        case 6: k_trsv<T, 6><<<1, kTrsvThreads, 0, s>>>(n, F, Linv, X, lower); break;
+        case 7: k_trsv<T, 7><<<1, kTrsvThreads, 0, s>>>(n, F, Linv, X, lower); break;
+        default: k_trsv<T, 8><<<1, kTrsvThreads, 0, s>>>(n, F, Linv, X, lower); break;
     }
 }
 
@@ -221,25 +417,67 @@ __global__ void k_accum(int cnt, const T* __restrict__ dx, double* __restrict__ 
 }
 
 template <typename T>
-static void factor(igs_prob p, cudaStream_t s) {
+static size_t panel_smem() { return (kNB * (kNB + 1) + kNB) * sizeof(T); }
+template <typename T>
+static size_t syrk_smem() { return 2 * kST * syrk_ld<T>() * sizeof(T); }
+
+// Issue the whole factorisation on stream s (used under stream capture).
+template <typename T>
+static void issue_factor(igs_prob p, cudaStream_t s) {
     const int n = p->plan.n;
     T* F = (T*)p->d_F;
     IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s));
     for (int k0 = 0; k0 < n; k0 += kNB) {
         const int kb = std::min(kNB, n - k0);
-        k_potrf<T><<<1, 256, 0, s>>>(n, F, k0, kb, p->d_flag);
+        const int rows = n - k0;
+        k_panel<T><<<(rows + kNB - 1) / kNB, 256, panel_smem<T>(), s>>>(n, F, k0, kb, (T*)p->d_diagL, p->d_flag);
         const int rem = n - k0 - kb;
         if (rem > 0) {
-            k_trsm<T><<<(rem + 63) / 64, 64, 0, s>>>(n, F, k0, kb);
-            const int nt = (rem + 63) / 64;
-            k_syrk<T><<<dim3(nt, nt), 256, 0, s>>>(n, F, k0, kb);
-            p->launches += 2;
+            const int nt = (rem + kST - 1) / kST;
+            k_syrk<T><<<dim3(nt, nt), 256, syrk_smem<T>(), s>>>(n, F, k0, kb);
         }
-        p->launches++;
     }
-    k_mirror<T><<<dim3((n + 255) / 256, n), 256, 0, s>>>(n, F);
-    p->launches++;
+    k_finalize<T><<<dim3((n + 255) / 256, n), 256, 0, s>>>(n, F, (const T*)p->d_diagL);
+    k_diag_inverse<T><<<(n + kNB - 1) / kNB, 256, 0, s>>>(n, (const T*)p->d_diagL, (T*)p->d_diagLinv);
     IGS_CUDA(cudaGetLastError());
+}
+
+static int factor_launches(int n) {
+    int c = 2;
+    for (int k0 = 0; k0 < n; k0 += kNB) c += (n - k0 - kNB > 0) ? 2 : 1;
+    return c;
+}
+
+template <typename T>
+static void factor(igs_prob p, cudaStream_t s) {
+    const int n = p->plan.n;
+    IGS_CUDA(cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem<T>()));
+    IGS_CUDA(cudaFuncSetAttribute(k_syrk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syrk_smem<T>()));
+    if (!p->factor_exec) {
+        // capture the fixed launch sequence once on a private stream
+        cudaStream_t cs;
+        IGS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        IGS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        try {
+            issue_factor<T>(p, cs);
+        } catch (...) {
+            cudaStreamEndCapture(cs, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            cudaStreamDestroy(cs);
+            throw;
+        }
+        IGS_CUDA(cudaStreamEndCapture(cs, &graph));
+        cudaError_t e = cudaGraphInstantiate(&p->factor_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+            p->factor_exec = nullptr;
+            throw Error(IGS_E_CUDA, cuda_msg(e, "cudaGraphInstantiate", __FILE__, __LINE__));
+        }
+    }
+    IGS_CUDA(cudaGraphLaunch(p->factor_exec, s));
+    p->launches += factor_launches(n);
     int flag = 0;
     IGS_CUDA(cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     IGS_CUDA(cudaStreamSynchronize(s));
@@ -249,7 +487,13 @@ static void factor(igs_prob p, cudaStream_t s) {
 template <typename T>
 static void prepare_factor(igs_prob p, cudaStream_t s) {
     const int n = p->plan.n;
-    if (!p->d_F) p->d_F = dev_alloc(p, sizeof(T) * (size_t)n * n);
+    if (!p->d_F) {
+        p->d_F = dev_alloc(p, sizeof(T) * (size_t)n * n);
+        p->d_diagL = dev_alloc(p, sizeof(T) * (size_t)n * kNB);
+        p->d_diagLinv = dev_alloc(p, sizeof(T) * (size_t)n * kNB);
+        // the factor graph captures these pointers: allocate before capture, keep for the problem's life
+        IGS_CUDA(cudaStreamSynchronize(s));
+    }
     if (!p->d_As64) p->d_As64 = (double*)dev_alloc(p, sizeof(double) * (size_t)n * n);
     k_symmetrize<T><<<dim3((n + 255) / 256, n), 256, 0, s>>>(n, (const T*)p->d_A, (T*)p->d_F, p->d_As64);
     p->launches++;
@@ -272,8 +516,8 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
     const double* scale = nullptr;
     for (;;) {
         k_cast_in<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, src, d_x, scale, n);
-        k_trsv<T><<<1, 1024, 0, s>>>(n, (const T*)p->d_F, d_x, nrhs, 1);
-        k_trsv<T><<<1, 1024, 0, s>>>(n, (const T*)p->d_F, d_x, nrhs, 0);
+        launch_trsv<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 1, s);
+        launch_trsv<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 0, s);
         k_accum<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, d_x, d_alpha, scale, n, it == 0);
         IGS_CUDA(cudaMemsetAsync(d_norm, 0, sizeof(double) * 2 * nrhs, s));
         k_resid<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, nrhs, p->d_As64, d_alpha, d_beta, d_r, d_norm);

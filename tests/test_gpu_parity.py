@@ -125,7 +125,9 @@ def test_rhs_and_solve(ctx, oracle_cache, name, n, d, nref, data):
             xy = lib().igs_rhs_points(p.prob)
             np.testing.assert_allclose(xy[:len(un), 0], bspline.curve_eval(curve, ref["disc"].eta, 0)[0][0], atol=1e-14)
             beta = lib().igs_build_rhs(p.prob, np.concatenate([un, ug])[None, :])[0]
-            assert np.max(np.abs(beta - beta_ref)) <= 1e-12 * np.max(np.abs(beta_ref))
+            # FP64 tier: FP64 bar; MIXED tier: FP32 double-layer far field, 1e-6 bar
+            tol_b = 1e-12 if tol_a is not None else 1e-6
+            assert np.max(np.abs(beta - beta_ref)) <= tol_b * np.max(np.abs(beta_ref))
             p.assemble()
             alpha, res = lib().igs_solve(p.prob)
             assert res[0] <= 1e-10
