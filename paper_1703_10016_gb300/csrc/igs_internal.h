@@ -120,6 +120,9 @@ struct igs_prob_s {
     void* d_diagL = nullptr;      // [n][64] factored diagonal blocks of L (tier type)
     void* d_diagLinv = nullptr;   // [n][64] inverses of the diagonal blocks of L (tier type)
     cudaGraphExec_t factor_exec = nullptr;   // captured factorisation (fixed pointers and sizes)
+    int* d_tflags = nullptr;      // [n/64] per-block completion flags of the triangular solves
+    int tepoch = 0;               // flag value of the current triangular solve
+    bool coop_ok = false;         // cooperative launch available
     double* d_As64 = nullptr;     // (A+A^T)/2 in FP64 for residuals (MIXED)
     int rhs_n = 0;
     double* d_beta = nullptr;     // [nrhs][n]

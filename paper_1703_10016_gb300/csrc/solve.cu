@@ -371,6 +371,140 @@ static void launch_trsv(int n, const T* F, const T* Linv, T* X, int nrhs, int lo
     }
 }
 
+// Multi-CTA substitution in one cooperative launch (all CTAs co-resident).
+// CTA c handles the 64-row blocks blk(c), blk(c + grid), ... in solve order.
+// A block waits for each block it depends on (bounded spin on a flag that the
+// producer sets after writing its piece of the solution), subtracts that
+// block's contribution as soon as it arrives, then applies the inverted
+// diagonal block and publishes its own piece.  The L traffic is spread over
+// the CTAs; the critical path is one 64 x 64 matrix-vector product per block.
+// A wait that exceeds its budget (one second, or 2^22 polls) sets *err and
+// ends the kernel; the blocks waiting on it then run out of budget too.
+constexpr long long kSpinLimit = 1LL << 22;
+constexpr unsigned long long kSpinNs = 1000000000ull;
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+template <typename T, int NR>
+__global__ void __launch_bounds__(256) k_trsv_coop(int n, const T* __restrict__ F, const T* __restrict__ Linv,
+                                                   T* __restrict__ X, int lower, int* __restrict__ flags, int epoch,
+                                                   int* __restrict__ err) {
+    __shared__ T acc[NR][kNB];
+    __shared__ T yin[NR][kNB];
+    __shared__ int s_abort;
+    const int tid = threadIdx.x;
+    const int nblk = (n + kNB - 1) / kNB;
+    if (tid == 0) s_abort = 0;
+    for (int J = blockIdx.x; J < nblk; J += gridDim.x) {
+        const int blk = lower ? J : nblk - 1 - J;
+        const int b0 = blk * kNB, bn = min(kNB, n - b0);
+        for (int idx = tid; idx < NR * kNB; idx += blockDim.x) {
+            const int k = idx / kNB, i = idx % kNB;
+            acc[k][i] = (i < bn) ? X[(size_t)k * n + b0 + i] : (T)0;
+        }
+        __syncthreads();
+        const int ndep = lower ? blk : nblk - 1 - blk;
+        for (int q = 0; q < ndep; ++q) {
+            const int D = lower ? q : nblk - 1 - q;
+            const int d0 = D * kNB, dn = min(kNB, n - d0);
+            if (tid == 0) {
+                long long it = 0;
+                const unsigned long long t0 = global_ns();
+                while (atomicAdd(&flags[D], 0) != epoch) {
+                    if (++it > kSpinLimit || global_ns() - t0 > kSpinNs) {
+                        atomicOr(err, 1);
+                        s_abort = 1;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                __threadfence();
+            }
+            __syncthreads();
+            if (s_abort) return;
+            for (int idx = tid; idx < NR * kNB; idx += blockDim.x) {
+                const int k = idx / kNB, c = idx % kNB;
+                yin[k][c] = (c < dn) ? __ldcg(X + (size_t)k * n + d0 + c) : (T)0;
+            }
+            __syncthreads();
+            // acc[k][i] -= sum_c F[b0+i][d0+c] yin[k][c]  (four threads per row)
+            const int i = tid / 4, part = tid % 4;
+            T sk[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) sk[k] = (T)0;
+            if (i < bn) {
+                const T* frow = F + (size_t)(b0 + i) * n + d0;
+                for (int c = part; c < dn; c += 4) {
+                    const T f = frow[c];
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) sk[k] += f * yin[k][c];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                T v = sk[k];
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                if (part == 0 && i < bn) acc[k][i] -= v;
+            }
+            __syncthreads();
+        }
+        // own block: y = Linv acc (lower) or Linv^T acc (upper)
+        for (int o = tid / 4; o < NR * kNB; o += blockDim.x / 4) {
+            const int part = tid % 4;
+            const int k = o / kNB, i = o % kNB;
+            T v = (T)0;
+            if (i < bn) {
+                if (lower)
+                    for (int l = part; l <= i; l += 4) v += Linv[(size_t)(b0 + i) * kNB + l] * acc[k][l];
+                else
+                    for (int l = i + part; l < bn; l += 4) v += Linv[(size_t)(b0 + l) * kNB + i] * acc[k][l];
+            }
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            if (part == 0 && i < bn) X[(size_t)k * n + b0 + i] = v;
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicExch(&flags[blk], epoch);
+    }
+}
+
+template <typename T, int NR>
+static void coop_launch(int n, const T* F, const T* Linv, T* X, int lower, int* flags, int epoch, int* err,
+                        cudaStream_t s) {
+    static int max_blocks = -1;                   // co-resident CTAs of this instantiation
+    if (max_blocks < 0) {
+        int dev = 0, sms = 0, per = 0;
+        IGS_CUDA(cudaGetDevice(&dev));
+        IGS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        IGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trsv_coop<T, NR>, 256, 0));
+        max_blocks = sms * per;
+    }
+    const int nblk = (n + kNB - 1) / kNB;
+    const int grid = std::max(1, std::min(nblk, max_blocks));
+    void* args[] = {(void*)&n, (void*)&F, (void*)&Linv, (void*)&X, (void*)&lower, (void*)&flags, (void*)&epoch,
+                    (void*)&err};
+    IGS_CUDA(cudaLaunchCooperativeKernel((void*)k_trsv_coop<T, NR>, dim3(grid), dim3(256), args, 0, s));
+}
+
+template <typename T>
+static void launch_trsv_coop(int n, const T* F, const T* Linv, T* X, int nrhs, int lower, int* flags, int epoch,
+                             int* err, cudaStream_t s) {
+    switch (nrhs) {
+        case 1: coop_launch<T, 1>(n, F, Linv, X, lower, flags, epoch, err, s); break;
+        case 2: coop_launch<T, 2>(n, F, Linv, X, lower, flags, epoch, err, s); break;
+        case 3: coop_launch<T, 3>(n, F, Linv, X, lower, flags, epoch, err, s); break;
+        case 4: coop_launch<T, 4>(n, F, Linv, X, lower, flags, epoch, err, s); break;
+        case 5: coop_launch<T, 5>(n, F, Linv, X, lower, flags, epoch, err, s); break;
+        case 6: coop_launch<T, 6>(n, F, Linv, X, lower, flags, epoch, err, s); break;
+        case 7: coop_launch<T, 7>(n, F, Linv, X, lower, flags, epoch, err, s); break;
+        default: coop_launch<T, 8>(n, F, Linv, X, lower, flags, epoch, err, s); break;
+    }
+}
+
 // r = beta - As alpha (FP64), one warp per row; also |r|^2 and |beta|^2 per rhs.
 __global__ void k_resid(int n, int nrhs, const double* __restrict__ As, const double* __restrict__ alpha,
                         const double* __restrict__ beta, double* __restrict__ r, double* __restrict__ norms) {
@@ -491,6 +625,13 @@ static void prepare_factor(igs_prob p, cudaStream_t s) {
         p->d_F = dev_alloc(p, sizeof(T) * (size_t)n * n);
         p->d_diagL = dev_alloc(p, sizeof(T) * (size_t)n * kNB);
         p->d_diagLinv = dev_alloc(p, sizeof(T) * (size_t)n * kNB);
+        p->d_tflags = (int*)dev_alloc(p, sizeof(int) * ((n + kNB - 1) / kNB));
+        IGS_CUDA(cudaMemsetAsync(p->d_tflags, 0, sizeof(int) * ((n + kNB - 1) / kNB), s));
+        p->tepoch = 0;
+        int dev = 0, coop = 0;
+        IGS_CUDA(cudaGetDevice(&dev));
+        IGS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        p->coop_ok = coop != 0;
         // the factor graph captures these pointers: allocate before capture, keep for the problem's life
         IGS_CUDA(cudaStreamSynchronize(s));
     }
@@ -514,17 +655,33 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
     int it = 0;
     const double* src = d_beta;
     const double* scale = nullptr;
+    IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s));
     for (;;) {
         k_cast_in<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, src, d_x, scale, n);
-        launch_trsv<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 1, s);
-        launch_trsv<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 0, s);
+        if (p->coop_ok) {
+            launch_trsv_coop<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 1, p->d_tflags,
+                                ++p->tepoch, p->d_flag, s);
+            launch_trsv_coop<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 0, p->d_tflags,
+                                ++p->tepoch, p->d_flag, s);
+        } else {
+            launch_trsv<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 1, s);
+            launch_trsv<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 0, s);
+        }
         k_accum<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, d_x, d_alpha, scale, n, it == 0);
         IGS_CUDA(cudaMemsetAsync(d_norm, 0, sizeof(double) * 2 * nrhs, s));
         k_resid<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, nrhs, p->d_As64, d_alpha, d_beta, d_r, d_norm);
         p->launches += 5;
         IGS_CUDA(cudaGetLastError());
         IGS_CUDA(cudaMemcpyAsync(hn.data(), d_norm, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, s));
+        int tflag = 0;
+        IGS_CUDA(cudaMemcpyAsync(&tflag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
         IGS_CUDA(cudaStreamSynchronize(s));
+        if (tflag) {
+            dev_free(p, d_x);
+            dev_free(p, d_r);
+            dev_free(p, d_norm);
+            throw Error(IGS_E_TIMEOUT, "triangular solve: a block waited past its budget");
+        }
         ++it;
         double worst = 0;
         for (int k = 0; k < nrhs; ++k) {
