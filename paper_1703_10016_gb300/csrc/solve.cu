@@ -3,10 +3,9 @@
 //
 // Blocked right-looking Cholesky with 64-wide panels, one graph-captured
 // launch sequence per problem:
-//   k_panel  every CTA factors the 64 x 64 diagonal block (one warp, rows in
-//            registers, columns broadcast by shuffles); CTA 0 stores L11, the
-//            other CTAs turn their 64-row slice of the panel into
-//            L21 = A21 L11^{-T} (a thread per row, right-looking);
+//   k_panel  CTA 0 factors the 64 x 64 diagonal block and stores L11; every
+//            other CTA factors the diagonal block stacked on its 64-row slice
+//            of the panel, which yields L21 = A21 L11^{-T} for that slice;
 //   k_syrk   trailing update of the lower triangle, 128 x 128 tiles.
 // FP64 tier: all in FP64, then one substitution pair.  MIXED tier: the same in
 // FP32, then iterative refinement with FP64 residuals r = beta - A_s alpha until
@@ -30,116 +29,155 @@ __global__ void k_symmetrize(int n, const T* __restrict__ A, T* __restrict__ F, 
     if (As64) As64[(size_t)i * n + j] = v;
 }
 
-// Cholesky of a 32 x 32 SPD block held one row per lane in registers (lane
-// owns row `lane`, entries r[0..31]); column j is broadcast with shuffles.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
+
+template <typename T>
+__device__ __forceinline__ T vget(const typename Vec16<T>::type& v, int q);
+template <> __device__ __forceinline__ float vget<float>(const float4& v, int q) {
+    return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+}
+template <> __device__ __forceinline__ double vget<double>(const double2& v, int q) { return q == 0 ? v.x : v.y; }
+
+// Panel step at column k0 (width kb).  CTA 0 factors the 64 x 64 diagonal
+// block and stores L11; CTA b >= 1 factors the tall block made of the
+// diagonal block and rows k0 + 64 b .. + 63 below it (the diagonal part
+// redundantly, so that no CTA waits for another), which turns its rows into
+// L21 = A21 L11^{-T}.  Right-looking by 8-column blocks, two barriers per
+// block: (1) each row's thread factors the 8 x 8 diagonal sub-block itself
+// (every thread the same, in registers: no communication) and solves its own
+// row against it; (2) rank-8 update of the columns to the right.
 // A non-positive pivot sets *flag and is replaced by 1.
-template <typename T>
-__device__ __forceinline__ void potrf32_reg(T (&r)[32], int lane, int* flag) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        T ajj = __shfl_sync(0xffffffffu, r[j], j);
-        if (!(ajj > (T)0)) {
-            if (lane == 0) atomicOr(flag, 1);
-            ajj = (T)1;
-        }
-        const T d = sqrt(ajj);
-        const T rinv = (T)1 / d;
-        if (lane == j) r[j] = d;
-        else if (lane > j) r[j] *= rinv;
-        const T lj = r[j];
-#pragma unroll
-        for (int l = j + 1; l < 32; ++l) {
-            const T c = __shfl_sync(0xffffffffu, lj, l);     // L[l][j]
-            if (lane >= l) r[l] -= lj * c;
-        }
-    }
-}
+constexpr int kPanelThreads = 512;
+constexpr int kPanelRows = 2 * kNB;                        // diagonal block + 64 rows below
+constexpr int kPanelParts = kPanelThreads / kPanelRows;   // threads per row in the update
+constexpr int kPB = 8;                                     // inner block width
 
-// Factor the 64 x 64 diagonal block a (shared, lower, padded with identity
-// beyond kb) as 2 x 2 blocks of 32, by warp 0:  L11 = chol(A11),
-// L21 = A21 L11^{-T}, A22 -= L21 L21^T, L22 = chol(A22).  Also writes the
-// reciprocal diagonal rd[i] = 1 / L[i][i].
-template <typename T>
-__device__ void potrf64_warp(T (*a)[kNB + 1], T* rd, int* flag) {
-    const int lane = threadIdx.x % 32;
-    T r[32];
-#pragma unroll
-    for (int l = 0; l < 32; ++l) r[l] = a[lane][l];
-    potrf32_reg<T>(r, lane, flag);
-#pragma unroll
-    for (int l = 0; l < 32; ++l) a[lane][l] = (l <= lane) ? r[l] : (T)0;
-    rd[lane] = (T)1 / r[lane];
-    __syncwarp();
-    // L21 row (32 + lane): x L11^T = a21, right-looking in registers
-    T x[32];
-#pragma unroll
-    for (int l = 0; l < 32; ++l) x[l] = a[32 + lane][l];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-        x[c] *= rd[c];
-#pragma unroll
-        for (int l = c + 1; l < 32; ++l) x[l] -= x[c] * a[l][c];
-    }
-#pragma unroll
-    for (int l = 0; l < 32; ++l) a[32 + lane][l] = x[l];
-    __syncwarp();
-    // A22 row (32 + lane) -= L21 row . L21 rows
-#pragma unroll
-    for (int l = 0; l < 32; ++l) {
-        T s = (T)0;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) s += x[k] * a[32 + l][k];
-        r[l] = a[32 + lane][32 + l] - s;
-    }
-    potrf32_reg<T>(r, lane, flag);
-#pragma unroll
-    for (int l = 0; l < 32; ++l) a[32 + lane][32 + l] = (l <= lane) ? r[l] : (T)0;
-    rd[32 + lane] = (T)1 / r[lane];
-    __syncwarp();
-}
+template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 
-// Panel step at column k0 (width kb): CTA b handles rows k0 + 64 b .. + 63.
-// Every CTA factors the diagonal block (warp 0, registers and shuffles); CTA 0
-// stores L11, the others solve L21 L11^T = A21 with one thread per row, the
-// row held in registers, right-looking (no division in the chain).
 template <typename T>
-__global__ void __launch_bounds__(256) k_panel(int n, T* __restrict__ F, int k0, int kb, T* __restrict__ diagL,
-                                               int* __restrict__ flag) {
+__global__ void __launch_bounds__(kPanelThreads) k_panel(int n, T* __restrict__ F, int k0, int kb,
+                                                         T* __restrict__ diagL, int* __restrict__ flag) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T (*a)[kNB + 1] = (T (*)[kNB + 1])smem_raw;
-    T* rd = (T*)(a + kNB);
+    T (*P)[kPB] = (T (*)[kPB])smem_raw;                     // current 8 columns of L, one row of 8 per row
+    T (*a)[kNB + 1] = (T (*)[kNB + 1])(P + kPanelRows);    // rows 0..63 diagonal block, 64..127 rows below
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
-        const int i = idx / kNB, l = idx % kNB;
-        T v;
-        if (i < kb && l < kb) v = (l <= i) ? F[(size_t)(k0 + i) * n + k0 + l] : (T)0;
-        else v = (i == l) ? (T)1 : (T)0;                 // identity padding beyond kb
-        a[i][l] = v;
+    const int r0 = k0 + blockIdx.x * kNB;
+    const int nb = blockIdx.x == 0 ? 0 : min(kNB, n - r0);
+    const int rows = kNB + nb;
+    // all loads in flight before the first store
+    constexpr int kPer = kPanelRows * kNB / kPanelThreads;
+    T v[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int idx = tid + q * kPanelThreads, i = idx / kNB, l = idx % kNB;
+        if (i < kNB) {
+            if (i < kb && l < kb) v[q] = (l <= i) ? F[(size_t)(k0 + i) * n + k0 + l] : (T)0;
+            else v[q] = (i == l) ? (T)1 : (T)0;       // identity padding beyond kb
+        } else {
+            v[q] = (i < rows) ? F[(size_t)(r0 + i - kNB) * n + k0 + l] : (T)0;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int idx = tid + q * kPanelThreads;
+        a[idx / kNB][idx % kNB] = v[q];
     }
     __syncthreads();
-    if (tid < 32) potrf64_warp<T>(a, rd, flag);
-    __syncthreads();
+    const int i = tid % kPanelRows, part = tid / kPanelRows;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kNB; c0 += kPB) {
+        // (1) rows i >= c0: L of the 8 x 8 diagonal sub-block, then this row's 8 entries
+        if (part == 0 && i >= c0 && i < rows) {
+            T d[kPB][kPB];
+#pragma unroll
+            for (int u = 0; u < kPB; ++u)
+#pragma unroll
+                for (int w = 0; w < kPB; ++w) d[u][w] = (w <= u) ? a[c0 + u][c0 + w] : (T)0;
+            T x[kPB];
+#pragma unroll
+            for (int w = 0; w < kPB; ++w) x[w] = a[i][c0 + w];
+#pragma unroll
+            for (int w = 0; w < kPB; ++w) {
+                T pv = d[w][w];
+                if (!(pv > (T)0)) {
+                    if (i == c0) atomicOr(flag, 1);
+                    pv = (T)1;
+                }
+                const T r = rsqrt_t<T>(pv);
+                d[w][w] = pv * r;
+#pragma unroll
+                for (int u = 0; u < kPB; ++u)
+                    if (u > w) d[u][w] *= r;
+#pragma unroll
+                for (int u = 0; u < kPB; ++u)
+#pragma unroll
+                    for (int z = 0; z < kPB; ++z)
+                        if (z > w && z <= u) d[u][z] -= d[u][w] * d[z][w];
+                // own row (rows below the sub-block): forward substitution step w
+                x[w] *= r;
+#pragma unroll
+                for (int z = 0; z < kPB; ++z)
+                    if (z > w) x[z] -= x[w] * d[z][w];
+            }
+            // a row inside the sub-block comes out of the same substitution as its
+            // row of L (its entries right of the diagonal start at zero): clear those
+#pragma unroll
+            for (int w = 0; w < kPB; ++w)
+                if (i < kNB && c0 + w > i) x[w] = (T)0;
+#pragma unroll
+            for (int w = 0; w < kPB; ++w) {
+                a[i][c0 + w] = x[w];
+                P[i][w] = x[w];
+            }
+        }
+        __syncthreads();
+        // (2) a[i][l] -= sum_w L[i][c0+w] L[l][c0+w] for c0 + 8 <= l (<= i on the diagonal block)
+        if (c0 + kPB < kNB && i >= c0 + kPB && i < rows) {
+            V xi[kPB / VN];
+#pragma unroll
+            for (int q = 0; q < kPB / VN; ++q) xi[q] = *(const V*)&P[i][q * VN];
+            const int lmax = i < kNB ? i : kNB - 1;
+            // two columns per trip, both loaded before either store
+#pragma unroll 1
+            for (int l = c0 + kPB + part; l <= lmax; l += 2 * kPanelParts) {
+                const int l2 = l + kPanelParts;
+                const bool two = l2 <= lmax;
+                V p1[kPB / VN], p2[kPB / VN];
+#pragma unroll
+                for (int q = 0; q < kPB / VN; ++q) {
+                    p1[q] = *(const V*)&P[l][q * VN];
+                    p2[q] = *(const V*)&P[two ? l2 : l][q * VN];
+                }
+                T s1 = a[i][l], s2 = a[i][two ? l2 : l];
+#pragma unroll
+                for (int q = 0; q < kPB / VN; ++q)
+#pragma unroll
+                    for (int u = 0; u < VN; ++u) {
+                        s1 -= vget<T>(xi[q], u) * vget<T>(p1[q], u);
+                        s2 -= vget<T>(xi[q], u) * vget<T>(p2[q], u);
+                    }
+                a[i][l] = s1;
+                if (two) a[i][l2] = s2;
+            }
+        }
+        __syncthreads();
+    }
     if (blockIdx.x == 0) {
-        for (int idx = tid; idx < kb * kNB; idx += blockDim.x) {
-            const int i = idx / kNB, l = idx % kNB;
-            diagL[(size_t)(k0 + i) * kNB + l] = (l <= i) ? a[i][l] : (T)0;
+        for (int idx = tid; idx < kb * kNB; idx += kPanelThreads) {
+            const int r = idx / kNB, l = idx % kNB;
+            diagL[(size_t)(k0 + r) * kNB + l] = (l <= r) ? a[r][l] : (T)0;
         }
         return;
     }
-    const int r0 = k0 + blockIdx.x * kNB;
-    if (tid < kNB && r0 + tid < n) {
-        T* row = F + (size_t)(r0 + tid) * n + k0;
-        T x[kNB];
-#pragma unroll
-        for (int l = 0; l < kNB; ++l) x[l] = row[l];
-#pragma unroll
-        for (int c = 0; c < kNB; ++c) {
-            x[c] *= rd[c];
-#pragma unroll
-            for (int l = c + 1; l < kNB; ++l) x[l] -= x[c] * a[l][c];
-        }
-#pragma unroll
-        for (int l = 0; l < kNB; ++l) row[l] = x[l];
+    for (int idx = tid; idx < nb * kNB; idx += kPanelThreads) {
+        const int r = idx / kNB, l = idx % kNB;
+        F[(size_t)(r0 + r) * n + k0 + l] = a[kNB + r][l];
     }
 }
 
@@ -149,17 +187,8 @@ __global__ void __launch_bounds__(256) k_panel(int n, T* __restrict__ F, int k0,
 // ty + 16q and columns tx + 16q (q = 0..7) and reads 16-byte vectors along l,
 // which keeps each quarter-warp's shared reads in distinct banks.
 constexpr int kST = 128;
-template <typename T> struct Vec16;
-template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
-template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
 template <typename T> __host__ __device__ constexpr int syrk_ld() { return kNB + 16 / (int)sizeof(T); }   // row stride: odd in 16-byte units
 
-template <typename T>
-__device__ __forceinline__ T vget(const typename Vec16<T>::type& v, int q);
-template <> __device__ __forceinline__ float vget<float>(const float4& v, int q) {
-    return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
-}
-template <> __device__ __forceinline__ double vget<double>(const double2& v, int q) { return q == 0 ? v.x : v.y; }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_syrk(int n, T* __restrict__ F, int k0, int kb) {
@@ -396,16 +425,37 @@ __global__ void __launch_bounds__(256) k_trsv_coop(int n, const T* __restrict__ 
     __shared__ int s_abort;
     const int tid = threadIdx.x;
     const int nblk = (n + kNB - 1) / kNB;
+    const int i = tid / 4, part = tid % 4;          // row of the block, column phase
     if (tid == 0) s_abort = 0;
     for (int J = blockIdx.x; J < nblk; J += gridDim.x) {
         const int blk = lower ? J : nblk - 1 - J;
         const int b0 = blk * kNB, bn = min(kNB, n - b0);
-        for (int idx = tid; idx < NR * kNB; idx += blockDim.x) {
-            const int k = idx / kNB, i = idx % kNB;
-            acc[k][i] = (i < bn) ? X[(size_t)k * n + b0 + i] : (T)0;
+        // this thread's slice of the inverted diagonal block, fetched before any wait:
+        // row i (lower) or column i (upper), entries l = part + 4 m
+        T lv[kNB / 4];
+#pragma unroll
+        for (int m = 0; m < kNB / 4; ++m) {
+            const int l = part + 4 * m;
+            if (lower) lv[m] = (i < bn) ? Linv[(size_t)(b0 + i) * kNB + l] : (T)0;
+            else lv[m] = (l < bn && i < bn) ? Linv[(size_t)(b0 + l) * kNB + i] : (T)0;
         }
-        __syncthreads();
+        for (int idx = tid; idx < NR * kNB; idx += blockDim.x) {
+            const int k = idx / kNB, r = idx % kNB;
+            acc[k][r] = (r < bn) ? X[(size_t)k * n + b0 + r] : (T)0;
+        }
         const int ndep = lower ? blk : nblk - 1 - blk;
+        T fr[kNB / 4];                              // F[b0 + i][d0 + part + 4 m] of the next dependency
+        auto fetch = [&](int q) {
+            const int D = lower ? q : nblk - 1 - q;
+            const int d0 = D * kNB, dn = min(kNB, n - d0);
+#pragma unroll
+            for (int m = 0; m < kNB / 4; ++m) {
+                const int c = part + 4 * m;
+                fr[m] = (i < bn && c < dn) ? F[(size_t)(b0 + i) * n + d0 + c] : (T)0;
+            }
+        };
+        if (ndep > 0) fetch(0);
+        __syncthreads();
         for (int q = 0; q < ndep; ++q) {
             const int D = lower ? q : nblk - 1 - q;
             const int d0 = D * kNB, dn = min(kNB, n - d0);
@@ -430,18 +480,15 @@ __global__ void __launch_bounds__(256) k_trsv_coop(int n, const T* __restrict__ 
             }
             __syncthreads();
             // acc[k][i] -= sum_c F[b0+i][d0+c] yin[k][c]  (four threads per row)
-            const int i = tid / 4, part = tid % 4;
             T sk[NR];
 #pragma unroll
-            for (int k = 0; k < NR; ++k) sk[k] = (T)0;
-            if (i < bn) {
-                const T* frow = F + (size_t)(b0 + i) * n + d0;
-                for (int c = part; c < dn; c += 4) {
-                    const T f = frow[c];
+            for (int k = 0; k < NR; ++k) {
+                T v = (T)0;
 #pragma unroll
-                    for (int k = 0; k < NR; ++k) sk[k] += f * yin[k][c];
-                }
+                for (int m = 0; m < kNB / 4; ++m) v += fr[m] * yin[k][part + 4 * m];
+                sk[k] = v;
             }
+            if (q + 1 < ndep) fetch(q + 1);
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
                 T v = sk[k];
@@ -452,16 +499,11 @@ __global__ void __launch_bounds__(256) k_trsv_coop(int n, const T* __restrict__ 
             __syncthreads();
         }
         // own block: y = Linv acc (lower) or Linv^T acc (upper)
-        for (int o = tid / 4; o < NR * kNB; o += blockDim.x / 4) {
-            const int part = tid % 4;
-            const int k = o / kNB, i = o % kNB;
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
             T v = (T)0;
-            if (i < bn) {
-                if (lower)
-                    for (int l = part; l <= i; l += 4) v += Linv[(size_t)(b0 + i) * kNB + l] * acc[k][l];
-                else
-                    for (int l = i + part; l < bn; l += 4) v += Linv[(size_t)(b0 + l) * kNB + i] * acc[k][l];
-            }
+#pragma unroll
+            for (int m = 0; m < kNB / 4; ++m) v += lv[m] * acc[k][part + 4 * m];
             v += __shfl_xor_sync(0xffffffffu, v, 1);
             v += __shfl_xor_sync(0xffffffffu, v, 2);
             if (part == 0 && i < bn) X[(size_t)k * n + b0 + i] = v;
@@ -551,7 +593,7 @@ __global__ void k_accum(int cnt, const T* __restrict__ dx, double* __restrict__ 
 }
 
 template <typename T>
-static size_t panel_smem() { return (kNB * (kNB + 1) + kNB) * sizeof(T); }
+static size_t panel_smem() { return (kPanelRows * kPB + kPanelRows * (kNB + 1)) * sizeof(T); }
 template <typename T>
 static size_t syrk_smem() { return 2 * kST * syrk_ld<T>() * sizeof(T); }
 
@@ -564,7 +606,7 @@ static void issue_factor(igs_prob p, cudaStream_t s) {
     for (int k0 = 0; k0 < n; k0 += kNB) {
         const int kb = std::min(kNB, n - k0);
         const int rows = n - k0;
-        k_panel<T><<<(rows + kNB - 1) / kNB, 256, panel_smem<T>(), s>>>(n, F, k0, kb, (T*)p->d_diagL, p->d_flag);
+        k_panel<T><<<(rows + kNB - 1) / kNB, kPanelThreads, panel_smem<T>(), s>>>(n, F, k0, kb, (T*)p->d_diagL, p->d_flag);
         const int rem = n - k0 - kb;
         if (rem > 0) {
             const int nt = (rem + kST - 1) / kST;
