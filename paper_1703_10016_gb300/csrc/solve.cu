@@ -6,7 +6,9 @@
 //   k_panel  CTA 0 factors the 64 x 64 diagonal block and stores L11; every
 //            other CTA factors the diagonal block stacked on its 64-row slice
 //            of the panel, which yields L21 = A21 L11^{-T} for that slice;
-//   k_syrk   trailing update of the lower triangle, 128 x 128 tiles.
+//   k_syrk   trailing update of the lower triangle, 64 x 64 tiles; the tile
+//            column that holds the next panel goes first, the rest runs on a
+//            second captured stream beside the next panel (look-ahead).
 // FP64 tier: all in FP64, then one substitution pair.  MIXED tier: the same in
 // FP32, then iterative refinement with FP64 residuals r = beta - A_s alpha until
 // ||r|| <= 1e-10 ||beta||.  The triangular solves go by 64-row blocks in solve
@@ -181,86 +183,106 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel(int n, T* __restrict__ 
     }
 }
 
-// Trailing update of the lower triangle: F[i][j] -= sum_l F[i][k0+l] F[j][k0+l]
-// for i >= j >= k0 + kb, 128 x 128 tiles.  The panel rows are staged row-major
-// (coalesced 16-byte loads, conflict-free stores); thread (tx, ty) owns rows
-// ty + 16q and columns tx + 16q (q = 0..7) and reads 16-byte vectors along l,
-// which keeps each quarter-warp's shared reads in distinct banks.
-constexpr int kST = 128;
-template <typename T> __host__ __device__ constexpr int syrk_ld() { return kNB + 16 / (int)sizeof(T); }   // row stride: odd in 16-byte units
+// Trailing update of the lower triangle after panel k0:
+// F[i][j] -= sum_l F[i][k0+l] F[j][k0+l] for i >= j >= k0 + kb, 64 x 64 tiles.
+// `mode` picks the tiles: 0 all, 1 the first tile column only (the next
+// panel's columns, updated first so that the next panel can start), 2 all
+// but the first tile column.  CTAs are numbered over the lower triangle of
+// tiles only.  The panel rows are staged row-major (coalesced 16-byte loads);
+// thread (tx, ty) owns rows ty + 16 r and columns tx + 16 c (r, c < 4) and
+// reads 16-byte vectors along l (odd row stride in 16-byte units: the
+// quarter-warps hit distinct banks).
+constexpr int kST = 64;
+constexpr int kSTM = kST / 16;       // rows / columns per thread
+template <typename T> __host__ __device__ constexpr int syrk_ld() { return kNB + 16 / (int)sizeof(T); }
 
+__device__ __forceinline__ void tri_decode(int t, int& ti, int& tj) {
+    int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    while (r * (r + 1) / 2 > t) --r;
+    ti = r;
+    tj = t - r * (r + 1) / 2;
+}
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_syrk(int n, T* __restrict__ F, int k0, int kb) {
+__global__ void __launch_bounds__(256) k_syrk(int n, T* __restrict__ F, int k0, int kb, int mode) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
     constexpr int LD = syrk_ld<T>();
-    const int ti = blockIdx.y, tj = blockIdx.x;
-    if (tj > ti) return;
+    int ti, tj;
+    if (mode == 1) {
+        ti = blockIdx.x;
+        tj = 0;
+    } else if (mode == 2) {
+        tri_decode(blockIdx.x, ti, tj);
+        ++ti;
+        ++tj;
+    } else {
+        tri_decode(blockIdx.x, ti, tj);
+    }
     const int base = k0 + kb;
     const int i0 = base + ti * kST, j0 = base + tj * kST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T (*As)[LD] = (T (*)[LD])smem_raw;
-    T (*Bs)[LD] = As + kST;
+    T (*Bs)[LD] = (ti == tj) ? As : As + kST;
     const bool vec_ok = (n % VN) == 0 && kb == kNB;
     if (vec_ok) {
         constexpr int per_row = kNB / VN;
         for (int idx = threadIdx.x; idx < kST * per_row; idx += blockDim.x) {
             const int rr = idx / per_row, q = idx % per_row;
-            V va, vb;
+            V va = V{}, vb = V{};
             if (i0 + rr < n) va = *(const V*)(F + (size_t)(i0 + rr) * n + k0 + q * VN);
-            else va = V{};
-            if (j0 + rr < n) vb = *(const V*)(F + (size_t)(j0 + rr) * n + k0 + q * VN);
-            else vb = V{};
+            if (ti != tj && j0 + rr < n) vb = *(const V*)(F + (size_t)(j0 + rr) * n + k0 + q * VN);
             *(V*)&As[rr][q * VN] = va;
-            *(V*)&Bs[rr][q * VN] = vb;
+            if (ti != tj) *(V*)&Bs[rr][q * VN] = vb;
         }
     } else {
         for (int idx = threadIdx.x; idx < kST * kNB; idx += blockDim.x) {
             const int rr = idx / kNB, l = idx % kNB;
             As[rr][l] = (i0 + rr < n && l < kb) ? F[(size_t)(i0 + rr) * n + k0 + l] : (T)0;
-            Bs[rr][l] = (j0 + rr < n && l < kb) ? F[(size_t)(j0 + rr) * n + k0 + l] : (T)0;
+            if (ti != tj) Bs[rr][l] = (j0 + rr < n && l < kb) ? F[(size_t)(j0 + rr) * n + k0 + l] : (T)0;
         }
     }
     __syncthreads();
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    T acc[8][8];
+    T acc[kSTM][kSTM];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+    for (int r = 0; r < kSTM; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = (T)0;
+        for (int c = 0; c < kSTM; ++c) acc[r][c] = (T)0;
+#pragma unroll 4
     for (int l = 0; l < kNB; l += VN) {
-        V av[8], bv[8];
+        V av[kSTM], bv[kSTM];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < kSTM; ++q) {
             av[q] = *(const V*)&As[ty + 16 * q][l];
             bv[q] = *(const V*)&Bs[tx + 16 * q][l];
         }
 #pragma unroll
         for (int u = 0; u < VN; ++u)
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < kSTM; ++r) {
                 const T ar = vget<T>(av[r], u);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) acc[r][c] += ar * vget<T>(bv[c], u);
+                for (int c = 0; c < kSTM; ++c) acc[r][c] += ar * vget<T>(bv[c], u);
             }
     }
     // epilogue: read every C entry before writing any (all loads in flight at once)
-    T cv[8][8];
+    T cv[kSTM][kSTM];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < kSTM; ++r) {
         const int i = i0 + ty + 16 * r;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < kSTM; ++c) {
             const int j = j0 + tx + 16 * c;
             cv[r][c] = (i < n && j <= i) ? F[(size_t)i * n + j] : (T)0;
         }
     }
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < kSTM; ++r) {
         const int i = i0 + ty + 16 * r;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < kSTM; ++c) {
             const int j = j0 + tx + 16 * c;
             if (i < n && j <= i) F[(size_t)i * n + j] = cv[r][c] - acc[r][c];
         }
@@ -598,29 +620,56 @@ template <typename T>
 static size_t syrk_smem() { return 2 * kST * syrk_ld<T>() * sizeof(T); }
 
 // Issue the whole factorisation on stream s (used under stream capture).
+// One factorisation as a two-stream launch sequence (captured into a graph):
+// s0 carries panel k, the update of column block k+1 and panel k+1; s1 the
+// rest of the update of step k, concurrent with panel k+1.  Ordering: the
+// first-column update of step k waits for the rest-update of step k-1 (both
+// touch column block k+1); the rest-update of step k waits for panel k.
 template <typename T>
-static void issue_factor(igs_prob p, cudaStream_t s) {
+static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evP, cudaEvent_t evB,
+                         cudaEvent_t evJ) {
     const int n = p->plan.n;
     T* F = (T*)p->d_F;
-    IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s));
+    IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s0));
+    bool pending = false, forked = false;
     for (int k0 = 0; k0 < n; k0 += kNB) {
         const int kb = std::min(kNB, n - k0);
         const int rows = n - k0;
-        k_panel<T><<<(rows + kNB - 1) / kNB, kPanelThreads, panel_smem<T>(), s>>>(n, F, k0, kb, (T*)p->d_diagL, p->d_flag);
+        k_panel<T><<<(rows + kNB - 1) / kNB, kPanelThreads, panel_smem<T>(), s0>>>(n, F, k0, kb, (T*)p->d_diagL,
+                                                                                 p->d_flag);
         const int rem = n - k0 - kb;
-        if (rem > 0) {
-            const int nt = (rem + kST - 1) / kST;
-            k_syrk<T><<<dim3(nt, nt), 256, syrk_smem<T>(), s>>>(n, F, k0, kb);
+        if (rem <= 0) continue;
+        const int nt = (rem + kST - 1) / kST;
+        if (nt > 1) IGS_CUDA(cudaEventRecord(evP, s0));
+        if (pending) {
+            IGS_CUDA(cudaStreamWaitEvent(s0, evB, 0));
+            pending = false;
+        }
+        k_syrk<T><<<nt, 256, syrk_smem<T>(), s0>>>(n, F, k0, kb, 1);
+        if (nt > 1) {
+            IGS_CUDA(cudaStreamWaitEvent(s1, evP, 0));
+            forked = true;
+            k_syrk<T><<<(nt - 1) * nt / 2, 256, syrk_smem<T>(), s1>>>(n, F, k0, kb, 2);
+            IGS_CUDA(cudaEventRecord(evB, s1));
+            pending = true;
         }
     }
-    k_finalize<T><<<dim3((n + 255) / 256, n), 256, 0, s>>>(n, F, (const T*)p->d_diagL);
-    k_diag_inverse<T><<<(n + kNB - 1) / kNB, 256, 0, s>>>(n, (const T*)p->d_diagL, (T*)p->d_diagLinv);
+    if (forked) {
+        IGS_CUDA(cudaEventRecord(evJ, s1));
+        IGS_CUDA(cudaStreamWaitEvent(s0, evJ, 0));
+    }
+    k_finalize<T><<<dim3((n + 255) / 256, n), 256, 0, s0>>>(n, F, (const T*)p->d_diagL);
+    k_diag_inverse<T><<<(n + kNB - 1) / kNB, 256, 0, s0>>>(n, (const T*)p->d_diagL, (T*)p->d_diagLinv);
     IGS_CUDA(cudaGetLastError());
 }
 
 static int factor_launches(int n) {
     int c = 2;
-    for (int k0 = 0; k0 < n; k0 += kNB) c += (n - k0 - kNB > 0) ? 2 : 1;
+    for (int k0 = 0; k0 < n; k0 += kNB) {
+        ++c;
+        const int rem = n - k0 - kNB;
+        if (rem > 0) c += (rem > kST) ? 2 : 1;
+    }
     return c;
 }
 
@@ -630,23 +679,36 @@ static void factor(igs_prob p, cudaStream_t s) {
     IGS_CUDA(cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem<T>()));
     IGS_CUDA(cudaFuncSetAttribute(k_syrk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syrk_smem<T>()));
     if (!p->factor_exec) {
-        // capture the fixed launch sequence once on a private stream
-        cudaStream_t cs;
-        IGS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        // capture the fixed launch sequence once, on two private streams
+        cudaStream_t cs = nullptr, cs1 = nullptr;
+        cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+        auto release = [&]() {
+            for (cudaEvent_t& e : ev)
+                if (e) cudaEventDestroy(e);
+            if (cs1) cudaStreamDestroy(cs1);
+            if (cs) cudaStreamDestroy(cs);
+        };
         cudaGraph_t graph = nullptr;
-        IGS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         try {
-            issue_factor<T>(p, cs);
+            IGS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            IGS_CUDA(cudaStreamCreateWithFlags(&cs1, cudaStreamNonBlocking));
+            for (cudaEvent_t& e : ev) IGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            IGS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            try {
+                issue_factor<T>(p, cs, cs1, ev[0], ev[1], ev[2]);
+            } catch (...) {
+                cudaStreamEndCapture(cs, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                throw;
+            }
+            IGS_CUDA(cudaStreamEndCapture(cs, &graph));
         } catch (...) {
-            cudaStreamEndCapture(cs, &graph);
-            if (graph) cudaGraphDestroy(graph);
-            cudaStreamDestroy(cs);
+            release();
             throw;
         }
-        IGS_CUDA(cudaStreamEndCapture(cs, &graph));
         cudaError_t e = cudaGraphInstantiate(&p->factor_exec, graph, 0);
         cudaGraphDestroy(graph);
-        cudaStreamDestroy(cs);
+        release();
         if (e != cudaSuccess) {
             p->factor_exec = nullptr;
             throw Error(IGS_E_CUDA, cuda_msg(e, "cudaGraphInstantiate", __FILE__, __LINE__));
