@@ -184,6 +184,156 @@ __global__ void __launch_bounds__(256) k_assemble_tile(
     }
 }
 
+// Natural logarithm for the FP32 tier, x > 0 and normal.  x = 2^e m with m in
+// [sqrt(1/2), sqrt(2)); ln m = 2 atanh(t) = 2 (t + t^3/3 + t^5/5 + ...), with
+// t = (m - 1)/(m + 1), |t| <= 0.1716 (Abramowitz & Stegun 4.1.27).  Five terms
+// leave a truncation error below 2e-9 relative; with the rounding of the
+// division and the sums the result is within a few FP32 ulps.
+__device__ __forceinline__ float ln_pos(float x) {
+    const int ix = __float_as_int(x);
+    const int e = (ix - 0x3f3504f3) >> 23;            // 0x3f3504f3 = sqrt(1/2)
+    const float m = __int_as_float(ix - (e << 23));
+    const float t = __fdividef(m - 1.0f, m + 1.0f);
+    const float t2 = t * t;
+    float q = fmaf(t2, 1.0f / 9.0f, 1.0f / 7.0f);
+    q = fmaf(t2, q, 1.0f / 5.0f);
+    q = fmaf(t2, q, 1.0f / 3.0f);
+    q = fmaf(t2, q, 1.0f);
+    return fmaf((float)e, 0.693147180559945309f, 2.0f * t * q);
+}
+
+// FP32 tier, one thread per A-range node: the block is as wide as the largest
+// node range (rounded up to a warp), so that no thread idles in stage 1.  The
+// B-range nodes are kept in shared memory as 16-byte records read by
+// broadcast; the singular weight for the next pair is fetched one step ahead.
+template <int D>
+__global__ void __launch_bounds__(1024) k_assemble_f(
+    int n, int Nq, int closed, float invL2, const int* __restrict__ lo, const int* __restrict__ hi,
+    const int* __restrict__ jfirst, const NodeF* __restrict__ nodes, const float* __restrict__ P,
+    const float* __restrict__ Q, const float* __restrict__ WsT, float* __restrict__ A, int64_t ld, int maxr) {
+    constexpr int D1 = D + 1;
+    constexpr int NV = (D1 + 3) / 4;                   // float4s per weight row
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int i0 = blockIdx.y * kTile, j0 = blockIdx.x * kTile;
+    const int ni = min(kTile, n - i0), nj = min(kTile, n - j0);
+    const int uA0 = lo[i0], Na = hi[i0 + ni - 1] - uA0 + 1;
+    const int uB0 = lo[j0], Nb = hi[j0 + nj - 1] - uB0 + 1;
+    float4* sBg = (float4*)smem;                       // [maxr][2]: (xh, xl, yh, yl), (eh, el, ebh, ebl)
+    float4* sBw = sBg + 2 * maxr;                      // [maxr][2 NV]: P row, Q row (zero padded)
+    float* sPA = (float*)(sBw + 2 * NV * maxr);        // [maxr][D1]
+    float* sS1 = sPA + maxr * D1;                      // [maxr][kTile + 1]
+    int2* sBm = (int2*)(sS1 + maxr * (kTile + 1));     // [maxr]: (m, first column - j0)
+    int* sJA = (int*)(sBm + maxr);                     // [maxr]
+
+    for (int v = threadIdx.x; v < Nb; v += blockDim.x) {
+        const int u = uB0 + v, m = pmod(u, Nq), per = pdiv(u, Nq);
+        const NodeF b = nodes[m];
+        sBg[2 * v] = make_float4(b.xh, b.xl, b.yh, b.yl);
+        sBg[2 * v + 1] = make_float4(b.eh, b.el, b.ebh, b.ebl);
+        float w[2][4 * NV];
+#pragma unroll
+        for (int r = 0; r < 4 * NV; ++r) {
+            w[0][r] = r < D1 ? P[m * D1 + r] : 0.0f;
+            w[1][r] = r < D1 ? Q[m * D1 + r] : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int q = 0; q < NV; ++q)
+                sBw[(2 * v + k) * NV + q] = make_float4(w[k][4 * q], w[k][4 * q + 1], w[k][4 * q + 2], w[k][4 * q + 3]);
+        sBm[v] = make_int2(m, jfirst[m] + n * per - j0);
+    }
+    for (int v = threadIdx.x; v < Na; v += blockDim.x) {
+        const int u = uA0 + v, m = pmod(u, Nq), per = pdiv(u, Nq);
+        sJA[v] = jfirst[m] + n * per - i0;
+        for (int r = 0; r < D1; ++r) sPA[v * D1 + r] = P[m * D1 + r];
+    }
+    __syncthreads();
+
+    const int a = threadIdx.x;
+    if (a < Na) {
+        const int ma = pmod(uA0 + a, Nq);
+        const NodeF na = nodes[ma];
+        const float lnJ = na.lnJ;
+        float acc[D1];
+#pragma unroll
+        for (int r = 0; r < D1; ++r) acc[r] = 0.0f;
+        int jcur = sBm[0].y;
+        float* row = sS1 + a * (kTile + 1);
+        const float* wcol = WsT + ma;
+        float ws_next = __ldg(wcol + (size_t)sBm[0].x * Nq);
+        for (int v = 0; v < Nb; ++v) {
+            const int2 bm = sBm[v];
+            const float ws = ws_next;
+            if (v + 1 < Nb) ws_next = __ldg(wcol + (size_t)sBm[v + 1].x * Nq);
+            while (jcur < bm.y) {
+                if (jcur >= 0 && jcur < nj) row[jcur] = acc[0];
+#pragma unroll
+                for (int r = 0; r < D; ++r) acc[r] = acc[r + 1];
+                acc[D] = 0.0f;
+                ++jcur;
+            }
+            const float4 g0 = sBg[2 * v], g1 = sBg[2 * v + 1];
+            const float dx = (g0.x - na.xh) + (g0.y - na.xl);
+            const float dy = (g0.z - na.yh) + (g0.w - na.yl);
+            float Dd = fabsf((g1.x - na.eh) + (g1.y - na.el));
+            if (closed) Dd *= ((g1.x + na.ebh) + (g1.y + na.ebl)) * ((g1.z + na.eh) + (g1.w + na.el)) * invL2;
+            float c0 = 0.5f * ln_pos(__fdividef(dx * dx + dy * dy, Dd * Dd));
+            const int mb = bm.x;
+            c0 = (mb == ma) ? lnJ : c0;
+            c0 = (closed && ma + mb == Nq - 1 && (ma == 0 || mb == 0)) ? lnJ - 0.693147180559945309f : c0;
+            float w[2][4 * NV];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    const float4 t4 = sBw[(2 * v + k) * NV + q];
+                    w[k][4 * q] = t4.x; w[k][4 * q + 1] = t4.y; w[k][4 * q + 2] = t4.z; w[k][4 * q + 3] = t4.w;
+                }
+#pragma unroll
+            for (int r = 0; r < D1; ++r) acc[r] = fmaf(w[0][r], c0, fmaf(w[1][r], ws, acc[r]));
+        }
+#pragma unroll
+        for (int r = 0; r < D1; ++r)
+            if (jcur + r >= 0 && jcur + r < nj) row[jcur + r] = acc[r];
+    }
+    __syncthreads();
+
+    const float scale = (float)(-1.0 / (2.0 * kPi));
+    for (int idx = threadIdx.x; idx < ni * nj; idx += blockDim.x) {
+        const int il = idx / nj, jl = idx % nj;
+        const int i = i0 + il;
+        const int a0 = lo[i] - uA0, a1 = hi[i] - uA0;
+        float s = 0.0f;
+        for (int b = a0; b <= a1; ++b) {
+            const int r = il - sJA[b];
+            if (r >= 0 && r <= D) s += sPA[b * D1 + r] * sS1[b * (kTile + 1) + jl];
+        }
+        A[(size_t)i * ld + j0 + jl] = scale * s;
+    }
+}
+
+static size_t tile_smem_f(int maxr, int d) {
+    const int NV = (d + 1 + 3) / 4;
+    return (size_t)maxr * (2 + 2 * NV) * 16 + (size_t)maxr * (d + 1) * 4 + (size_t)maxr * (kTile + 1) * 4 +
+           (size_t)maxr * 8 + (size_t)maxr * 4 + 64;
+}
+
+template <int D>
+static void launch_tile_f(igs_prob p, int maxr, cudaStream_t s) {
+    const Plan& P = p->plan;
+    const size_t sm = tile_smem_f(maxr, D);
+    auto kern = k_assemble_f<D>;
+    IGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int nt = (P.n + kTile - 1) / kTile;
+    const int threads = std::min(1024, (maxr + 31) / 32 * 32);
+    kern<<<dim3(nt, nt), threads, sm, s>>>(P.n, P.Nq, P.closed, (float)(1.0 / (P.L * P.L)), p->d_lo, p->d_hi,
+                                           p->d_jfirst, (const NodeF*)p->d_nodes, (const float*)p->d_P,
+                                           (const float*)p->d_Q, (const float*)p->d_WsT32, (float*)p->d_A,
+                                           (int64_t)P.n, maxr);
+    IGS_CUDA(cudaGetLastError());
+}
+
 template <typename T>
 static size_t tile_smem(int maxr, int d) {
     using Node = typename NodeOf<T>::type;
@@ -208,6 +358,15 @@ static void launch_tile(igs_prob p, int maxr, cudaStream_t s) {
 
 template <typename T>
 static void launch_tile_deg(igs_prob p, int maxr, cudaStream_t s) {
+    if (std::is_same<T, float>::value && maxr <= 1024) {
+        switch (p->plan.d) {
+            case 2: launch_tile_f<2>(p, maxr, s); return;
+            case 3: launch_tile_f<3>(p, maxr, s); return;
+            case 4: launch_tile_f<4>(p, maxr, s); return;
+            case 5: launch_tile_f<5>(p, maxr, s); return;
+            default: throw Error(IGS_E_INVALID_ARG, "unsupported degree");
+        }
+    }
     switch (p->plan.d) {
         case 2: launch_tile<T, 2>(p, maxr, s); break;
         case 3: launch_tile<T, 3>(p, maxr, s); break;
