@@ -184,31 +184,25 @@ __global__ void __launch_bounds__(256) k_assemble_tile(
     }
 }
 
-// Natural logarithm for the FP32 tier, x > 0 and normal.  x = 2^e m with m in
-// [sqrt(1/2), sqrt(2)); ln m = 2 atanh(t) = 2 (t + t^3/3 + t^5/5 + ...), with
-// t = (m - 1)/(m + 1), |t| <= 0.1716 (Abramowitz & Stegun 4.1.27).  Five terms
-// leave a truncation error below 2e-9 relative; with the rounding of the
-// division and the sums the result is within a few FP32 ulps.
+// Natural logarithm for the FP32 tier, x > 0 and normal: x = 2^e m with m in
+// [sqrt(1/2), sqrt(2)) by exponent arithmetic, ln x = (e + log2 m) ln 2.  On
+// [0.5, 2] the hardware base-2 logarithm (__log2f) has an absolute error of
+// at most 2^-22, so ln x carries an absolute error of about 2^-22 ln 2 plus
+// the rounding of the result.
 __device__ __forceinline__ float ln_pos(float x) {
     const int ix = __float_as_int(x);
     const int e = (ix - 0x3f3504f3) >> 23;            // 0x3f3504f3 = sqrt(1/2)
     const float m = __int_as_float(ix - (e << 23));
-    const float t = __fdividef(m - 1.0f, m + 1.0f);
-    const float t2 = t * t;
-    float q = fmaf(t2, 1.0f / 9.0f, 1.0f / 7.0f);
-    q = fmaf(t2, q, 1.0f / 5.0f);
-    q = fmaf(t2, q, 1.0f / 3.0f);
-    q = fmaf(t2, q, 1.0f);
-    return fmaf((float)e, 0.693147180559945309f, 2.0f * t * q);
+    return ((float)e + __log2f(m)) * 0.693147180559945309f;
 }
 
 // FP32 tier, one thread per A-range node: the block is as wide as the largest
 // node range (rounded up to a warp), so that no thread idles in stage 1.  The
 // B-range nodes are kept in shared memory as 16-byte records read by
 // broadcast; the singular weight for the next pair is fetched one step ahead.
-template <int D>
+template <int D, bool CLOSED>
 __global__ void __launch_bounds__(1024) k_assemble_f(
-    int n, int Nq, int closed, float invL2, const int* __restrict__ lo, const int* __restrict__ hi,
+    int n, int Nq, float invL2, const int* __restrict__ lo, const int* __restrict__ hi,
     const int* __restrict__ jfirst, const NodeF* __restrict__ nodes, const float* __restrict__ P,
     const float* __restrict__ Q, const float* __restrict__ WsT, float* __restrict__ A, int64_t ld, int maxr) {
     constexpr int D1 = D + 1;
@@ -261,11 +255,17 @@ __global__ void __launch_bounds__(1024) k_assemble_f(
         int jcur = sBm[0].y;
         float* row = sS1 + a * (kTile + 1);
         const float* wcol = WsT + ma;
-        float ws_next = __ldg(wcol + (size_t)sBm[0].x * Nq);
+        // singular weights of the next kPre pairs in flight (ring in registers)
+        constexpr int kPre = 4;
+        float wq[kPre];
+#pragma unroll
+        for (int q = 0; q < kPre; ++q) wq[q] = (q < Nb) ? __ldg(wcol + (size_t)sBm[q].x * Nq) : 0.0f;
         for (int v = 0; v < Nb; ++v) {
             const int2 bm = sBm[v];
-            const float ws = ws_next;
-            if (v + 1 < Nb) ws_next = __ldg(wcol + (size_t)sBm[v + 1].x * Nq);
+            const float ws = wq[0];
+#pragma unroll
+            for (int q = 0; q < kPre - 1; ++q) wq[q] = wq[q + 1];
+            wq[kPre - 1] = (v + kPre < Nb) ? __ldg(wcol + (size_t)sBm[v + kPre].x * Nq) : 0.0f;
             while (jcur < bm.y) {
                 if (jcur >= 0 && jcur < nj) row[jcur] = acc[0];
 #pragma unroll
@@ -277,11 +277,11 @@ __global__ void __launch_bounds__(1024) k_assemble_f(
             const float dx = (g0.x - na.xh) + (g0.y - na.xl);
             const float dy = (g0.z - na.yh) + (g0.w - na.yl);
             float Dd = fabsf((g1.x - na.eh) + (g1.y - na.el));
-            if (closed) Dd *= ((g1.x + na.ebh) + (g1.y + na.ebl)) * ((g1.z + na.eh) + (g1.w + na.el)) * invL2;
+            if (CLOSED) Dd *= ((g1.x + na.ebh) + (g1.y + na.ebl)) * ((g1.z + na.eh) + (g1.w + na.el)) * invL2;
             float c0 = 0.5f * ln_pos(__fdividef(dx * dx + dy * dy, Dd * Dd));
             const int mb = bm.x;
             c0 = (mb == ma) ? lnJ : c0;
-            c0 = (closed && ma + mb == Nq - 1 && (ma == 0 || mb == 0)) ? lnJ - 0.693147180559945309f : c0;
+            if (CLOSED) c0 = (ma + mb == Nq - 1 && (ma == 0 || mb == 0)) ? lnJ - 0.693147180559945309f : c0;
             float w[2][4 * NV];
 #pragma unroll
             for (int k = 0; k < 2; ++k)
@@ -319,19 +319,24 @@ static size_t tile_smem_f(int maxr, int d) {
            (size_t)maxr * 8 + (size_t)maxr * 4 + 64;
 }
 
-template <int D>
+template <int D, bool CLOSED>
 static void launch_tile_f(igs_prob p, int maxr, cudaStream_t s) {
     const Plan& P = p->plan;
     const size_t sm = tile_smem_f(maxr, D);
-    auto kern = k_assemble_f<D>;
+    auto kern = k_assemble_f<D, CLOSED>;
     IGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int nt = (P.n + kTile - 1) / kTile;
     const int threads = std::min(1024, (maxr + 31) / 32 * 32);
-    kern<<<dim3(nt, nt), threads, sm, s>>>(P.n, P.Nq, P.closed, (float)(1.0 / (P.L * P.L)), p->d_lo, p->d_hi,
-                                           p->d_jfirst, (const NodeF*)p->d_nodes, (const float*)p->d_P,
-                                           (const float*)p->d_Q, (const float*)p->d_WsT32, (float*)p->d_A,
-                                           (int64_t)P.n, maxr);
+    kern<<<dim3(nt, nt), threads, sm, s>>>(P.n, P.Nq, (float)(1.0 / (P.L * P.L)), p->d_lo, p->d_hi, p->d_jfirst,
+                                           (const NodeF*)p->d_nodes, (const float*)p->d_P, (const float*)p->d_Q,
+                                           (const float*)p->d_WsT32, (float*)p->d_A, (int64_t)P.n, maxr);
     IGS_CUDA(cudaGetLastError());
+}
+
+template <int D>
+static void launch_tile_f(igs_prob p, int maxr, cudaStream_t s) {
+    if (p->plan.closed) launch_tile_f<D, true>(p, maxr, s);
+    else launch_tile_f<D, false>(p, maxr, s);
 }
 
 template <typename T>
