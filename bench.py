@@ -241,7 +241,7 @@ def run_ours(args, rank, world, local_rank):
                  "phases_ms": {k: statistics.mean(p[k] for p in fp["phases"]) for k in fp["phases"][0]},
                  "steps": fp["steps"]},
         "speedup_mixed_vs_fp64": fp_step / step_ms,
-        "roofline": {"kernel": "k_assemble_tile<float>", "bound": "alu", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": f"k_assemble_f<{d},{'true' if curve.closed else 'false'}>", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "work": f"{flops_per_pair} flop per node pair x n_quad^2 + stage-2 contraction",
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
