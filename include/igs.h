@@ -127,7 +127,13 @@ int igs_destroy_geometry(igs_geom geom);
  * (periodic for a closed curve, clamped for an open arc), exactness space
  * refined `n_ref` times (Sect. 4), precision IGS_FP64 or IGS_MIXED.
  * Limits: 2 <= degree <= 5, 1 <= n_ref <= 4, closed: n_elems >= 2(degree+1),
- * n_ref * n_elems >= 3.  Errors: INVALID_ARG. */
+ * n_ref * n_elems >= 3, n <= 65535.  Errors: INVALID_ARG.
+ * Storage of the singular rules: on uniform knots the weight of node m' in
+ * the rule at node m depends, away from the ends of I, only on m - m' and on
+ * the parity of m' (Algorithm 2 is translation invariant there), so beyond
+ * small n_quad the library keeps 24(d+1)+16 explicit columns and d+2 explicit
+ * rows at each end plus two sequences of length 2 n_quad - 1: O(n_quad)
+ * memory instead of n_quad^2. */
 int igs_create_problem(igs_geom geom, igs_prob* out, int degree, int n_elems, int n_ref, int precision);
 int igs_destroy_problem(igs_prob prob);
 
@@ -208,8 +214,9 @@ int igs_solve(igs_prob prob, const double* beta, int nrhs, double* alpha_out, do
  *   eta[n_quad]; W_band[n_quad * (degree+1)]: W_band[m*(d+1)+r] = w^(i)_m for
  *   the test function i = (first(m) + r) mod n containing eta_m (0 if none),
  *   first[n_quad]: first(m) (may be >= n for the seam node eta = b);
- *   Ws[n_quad * n_quad] (row m = w^{eta_m}, NULL to skip).
- * Any output pointer may be NULL.  Errors: STATE, CUDA. */
+ *   Ws[n_quad * n_quad] (row m = w^{eta_m}, NULL to skip; expanded from the
+ *   stored form, n_quad <= 65535).
+ * Any output pointer may be NULL.  Errors: STATE, INVALID_ARG, NO_MEMORY, CUDA. */
 int igs_get_rules(igs_prob prob, double* eta, double* W_band, int32_t* first, double* Ws);
 
 /* Diagnostic download of the geometry at the nodes (HOST, FP64): xy[n_quad*2]

@@ -200,7 +200,7 @@ int igs_create_problem(igs_geom g, igs_prob* out, int degree, int n_elems, int n
     if (rc != IGS_OK) { delete p; throw Error(rc, err); }
     const Plan& P = p->plan;
     if (P.max_nodes_i > 64 || P.max_fine_i > 40) { delete p; throw Error(IGS_E_INVALID_ARG, "local rule system too large"); }
-    if (P.Nq > 65535) { delete p; throw Error(IGS_E_INVALID_ARG, "n_quad > 65535 is not supported by the dense singular-rule store"); }
+    if (P.n > 65535) { delete p; throw Error(IGS_E_INVALID_ARG, "n > 65535 is not supported"); }
     try {
         upload(p, p->d_pos, P.pos_num);
         upload(p, p->d_jfirst, P.jfirst);
@@ -239,7 +239,8 @@ int igs_destroy_problem(igs_prob p) {
                      p->d_lo, p->d_hi, p->d_jr, p->d_gfirst, p->d_glast,
                      p->d_piece, p->d_series, p->d_eta, p->d_Bf,
                      p->d_Bt, p->d_W, p->d_G, p->d_Z, p->d_WsT,
-                     p->d_WsT32, p->d_flag, p->d_geo, p->d_nodes,
+                     p->d_WsT32, p->d_WsRow, p->d_WsRow32, p->d_WsToe, p->d_WsToe32,
+                     p->d_flag, p->d_geo, p->d_nodes,
                      p->d_P, p->d_Q, p->d_A, p->d_F, p->d_As64, p->d_diagL, p->d_diagLinv, p->d_tflags,
                      p->d_beta, p->d_rhs_geo, p->d_rhs_w, p->d_rhs_t};
     for (void* q : ptrs) dev_free_raw(p, q);
@@ -473,15 +474,16 @@ int igs_get_rules(igs_prob p, double* eta, double* W_band, int32_t* first, doubl
     if (eta) IGS_CUDA(cudaMemcpyAsync(eta, p->d_eta, sizeof(double) * P.Nq, cudaMemcpyDeviceToHost, s));
     if (W_band) IGS_CUDA(cudaMemcpyAsync(W_band, p->d_W, sizeof(double) * P.Nq * (P.d + 1), cudaMemcpyDeviceToHost, s));
     if (first) std::copy(P.jfirst.begin(), P.jfirst.end(), first);
-    std::vector<double> wt;
     if (Ws) {
-        wt.resize((size_t)P.Nq * P.Nq);
-        IGS_CUDA(cudaMemcpyAsync(wt.data(), p->d_WsT, sizeof(double) * wt.size(), cudaMemcpyDeviceToHost, s));
+        REQUIRE(P.Nq <= 65535, IGS_E_INVALID_ARG, "dense W^s download is limited to n_quad <= 65535");
+        double* d_ws = (double*)dev_alloc(p, sizeof(double) * (size_t)P.Nq * P.Nq);
+        ws_expand(p, d_ws);
+        cudaError_t e = cudaMemcpyAsync(Ws, d_ws, sizeof(double) * (size_t)P.Nq * P.Nq, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        dev_free(p, d_ws);
+        if (e != cudaSuccess) throw Error(IGS_E_CUDA, cuda_msg(e, "cudaMemcpyAsync", __FILE__, __LINE__));
     }
     IGS_CUDA(cudaStreamSynchronize(s));
-    if (Ws)
-        for (int m = 0; m < P.Nq; ++m)
-            for (int nn = 0; nn < P.Nq; ++nn) Ws[(size_t)m * P.Nq + nn] = wt[(size_t)nn * P.Nq + m];
     API_END
 }
 

@@ -105,7 +105,7 @@ template <typename T, int D>
 __global__ void __launch_bounds__(256) k_assemble_tile(
     int n, int Nq, int closed, T invL2, const int* __restrict__ lo, const int* __restrict__ hi,
     const int* __restrict__ jfirst, const typename NodeOf<T>::type* __restrict__ nodes, const T* __restrict__ P,
-    const T* __restrict__ Q, const T* __restrict__ WsT, T* __restrict__ A, int64_t ld, int maxr) {
+    const T* __restrict__ Q, const WsView<T> wsv, T* __restrict__ A, int64_t ld, int maxr) {
     using Node = typename NodeOf<T>::type;
     constexpr int D1 = D + 1;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) k_assemble_tile(
             if (mb == ma) c0 = na.lnJ;
             else if (closed && (ma + mb == Nq - 1) && (ma == 0 || mb == 0)) c0 = na.lnJ - ln2;
             else c0 = k1_pair(na, sB[v], closed, invL2);
-            const T ws = WsT[(size_t)mb * Nq + ma];
+            const T ws = ws_at(wsv, ma, mb);
 #pragma unroll
             for (int r = 0; r < D1; ++r) acc[r] += sPB[v * D1 + r] * c0 + sQB[v * D1 + r] * ws;
         }
@@ -204,7 +204,7 @@ template <int D, bool CLOSED>
 __global__ void __launch_bounds__(1024) k_assemble_f(
     int n, int Nq, float invL2, const int* __restrict__ lo, const int* __restrict__ hi,
     const int* __restrict__ jfirst, const NodeF* __restrict__ nodes, const float* __restrict__ P,
-    const float* __restrict__ Q, const float* __restrict__ WsT, float* __restrict__ A, int64_t ld, int maxr) {
+    const float* __restrict__ Q, const WsView<float> wsv, float* __restrict__ A, int64_t ld, int maxr) {
     constexpr int D1 = D + 1;
     constexpr int NV = (D1 + 3) / 4;                   // float4s per weight row
     extern __shared__ __align__(16) unsigned char smem[];
@@ -254,18 +254,17 @@ __global__ void __launch_bounds__(1024) k_assemble_f(
         for (int r = 0; r < D1; ++r) acc[r] = 0.0f;
         int jcur = sBm[0].y;
         float* row = sS1 + a * (kTile + 1);
-        const float* wcol = WsT + ma;
         // singular weights of the next kPre pairs in flight (ring in registers)
         constexpr int kPre = 4;
         float wq[kPre];
 #pragma unroll
-        for (int q = 0; q < kPre; ++q) wq[q] = (q < Nb) ? __ldg(wcol + (size_t)sBm[q].x * Nq) : 0.0f;
+        for (int q = 0; q < kPre; ++q) wq[q] = (q < Nb) ? ws_at(wsv, ma, sBm[q].x) : 0.0f;
         for (int v = 0; v < Nb; ++v) {
             const int2 bm = sBm[v];
             const float ws = wq[0];
 #pragma unroll
             for (int q = 0; q < kPre - 1; ++q) wq[q] = wq[q + 1];
-            wq[kPre - 1] = (v + kPre < Nb) ? __ldg(wcol + (size_t)sBm[v + kPre].x * Nq) : 0.0f;
+            wq[kPre - 1] = (v + kPre < Nb) ? ws_at(wsv, ma, sBm[v + kPre].x) : 0.0f;
             while (jcur < bm.y) {
                 if (jcur >= 0 && jcur < nj) row[jcur] = acc[0];
 #pragma unroll
@@ -329,7 +328,8 @@ static void launch_tile_f(igs_prob p, int maxr, cudaStream_t s) {
     const int threads = std::min(1024, (maxr + 31) / 32 * 32);
     kern<<<dim3(nt, nt), threads, sm, s>>>(P.n, P.Nq, (float)(1.0 / (P.L * P.L)), p->d_lo, p->d_hi, p->d_jfirst,
                                            (const NodeF*)p->d_nodes, (const float*)p->d_P, (const float*)p->d_Q,
-                                           (const float*)p->d_WsT32, (float*)p->d_A, (int64_t)P.n, maxr);
+                                           WsView<float>{p->d_WsT32, p->d_WsRow32, p->d_WsToe32, P.Nq, p->ws_B, p->ws_R},
+                                           (float*)p->d_A, (int64_t)P.n, maxr);
     IGS_CUDA(cudaGetLastError());
 }
 
@@ -354,7 +354,9 @@ static void launch_tile(igs_prob p, int maxr, cudaStream_t s) {
     IGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int nt = (P.n + kTile - 1) / kTile;
     dim3 grid(nt, nt);
-    const T* ws = std::is_same<T, float>::value ? (const T*)p->d_WsT32 : (const T*)p->d_WsT;
+    const bool f32 = std::is_same<T, float>::value;
+    const WsView<T> ws{f32 ? (const T*)p->d_WsT32 : (const T*)p->d_WsT, f32 ? (const T*)p->d_WsRow32 : (const T*)p->d_WsRow,
+                       f32 ? (const T*)p->d_WsToe32 : (const T*)p->d_WsToe, P.Nq, p->ws_B, p->ws_R};
     kern<<<grid, 256, sm, s>>>(P.n, P.Nq, P.closed, (T)(1.0 / (P.L * P.L)), p->d_lo, p->d_hi, p->d_jfirst,
                                (const typename NodeOf<T>::type*)p->d_nodes, (const T*)p->d_P, (const T*)p->d_Q, ws,
                                (T*)p->d_A, (int64_t)P.n, maxr);

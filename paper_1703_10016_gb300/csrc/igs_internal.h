@@ -104,8 +104,17 @@ struct igs_prob_s {
     double* d_W = nullptr;        // [Nq][d+1] regular weights w^(jfirst+r)_m
     double* d_G = nullptr;        // [NE][d+1] Cholesky factor of G (row j: L(j, j-r))
     double* d_Z = nullptr;        // [NE][Nq] G^{-1} mu(eta_m) (work)
-    double* d_WsT = nullptr;      // [Nq][Nq] transposed singular rules: WsT[n][m] = w^{eta_m}_n
+    // Singular rules W^s[m][m'] (row m = w^{eta_m}).  Column m' is stored
+    // explicitly for the ws_B columns at each end (ws_B = n_quad: dense); the
+    // interior is 2-periodic Toeplitz (ws_T[p][m - m' + n_quad - 1], p =
+    // (m' - ws_B) & 1) except for the ws_R rows at each end (ws_row).
+    int ws_B = 0, ws_R = 0;
+    double* d_WsT = nullptr;      // [2 ws_B][Nq] boundary columns: d_WsT[c][m] = W^s[m][m'(c)]
     float* d_WsT32 = nullptr;     // FP32 copy (MIXED tier)
+    double* d_WsRow = nullptr;    // [2 ws_R][Nq] boundary rows: d_WsRow[r][m'] = W^s[m(r)][m']
+    float* d_WsRow32 = nullptr;
+    double* d_WsToe = nullptr;    // [2][2 Nq - 1] interior Toeplitz sequences
+    float* d_WsToe32 = nullptr;
     int* d_flag = nullptr;        // device status word
 
     // geometry at nodes
@@ -133,6 +142,26 @@ struct igs_prob_s {
 };
 
 namespace igs {
+// Read access to the singular rules in either layout (see igs_prob_s).
+template <typename T>
+struct WsView {
+    const T* col;
+    const T* row;
+    const T* toe;
+    int Nq, B, R;
+};
+// W^s[ma][mb]: weight of node mb in the singular rule at node ma.
+template <typename T>
+__host__ __device__ __forceinline__ T ws_at(const WsView<T>& v, int ma, int mb) {
+    if (mb < v.B) return v.col[(size_t)mb * v.Nq + ma];
+    if (mb >= v.Nq - v.B) return v.col[(size_t)(mb - v.Nq + 2 * v.B) * v.Nq + ma];
+    if (ma < v.R) return v.row[(size_t)ma * v.Nq + mb];
+    if (ma >= v.Nq - v.R) return v.row[(size_t)(ma - v.Nq + 2 * v.R) * v.Nq + mb];
+    return v.toe[(size_t)((mb - v.B) & 1) * (2 * (size_t)v.Nq - 1) + (ma - mb + v.Nq - 1)];
+}
+}  // namespace igs
+
+namespace igs {
 // allocation helpers (stream-ordered, accounted on the problem)
 void* dev_alloc(igs_prob p, size_t bytes);
 void dev_free_raw(igs_prob p, void* ptr);
@@ -144,6 +173,7 @@ inline void dev_free(igs_prob p, T*& ptr) {
 
 // phases (implemented in the .cu files)
 void rules_build(igs_prob p);
+void ws_expand(igs_prob p, double* d_out);   // dense W^s[m][m'] into d_out[Nq][Nq]
 void geometry_eval(igs_geom g, const double* d_t, int count, double* d_out, cudaStream_t s);
 void geometry_nodes(igs_prob p);
 void assemble_matrix(igs_prob p);

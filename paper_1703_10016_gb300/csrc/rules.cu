@@ -241,44 +241,50 @@ __device__ void local_log_moments(double c, int d, const double* __restrict__ se
     }
 }
 
-// mu_j(eta_m) for j in a block of 128, m = blockIdx.y; output Z[j][m].
-__global__ void __launch_bounds__(128) k_moments(int Nq, int NE, int M, int d, int den, int closed, double hf, double L,
-                                                 const int* __restrict__ pos, const int* __restrict__ rows,
-                                                 const double* __restrict__ piece, const double* __restrict__ series,
-                                                 double* __restrict__ Z, int ldz) {
-    __shared__ double E[128 + kMaxDegree][kMaxDegree + 1];
-    const int m = rows ? rows[blockIdx.y] : blockIdx.y;
-    const int col = blockIdx.y;
-    const int j0 = blockIdx.x * 128;
-    const double s_units = double(pos[m]) / den;                  // (eta_m - a) / h_f
+// Element moments by relative position.  E_{m,e,k} = int_e ((t - tau_e)/h_f)^k
+// K2(t - eta_m) dt depends on eta_m and the element only through the offset
+// du = pos_m - e den (positions in units of h_f/den, all integers), so one
+// table over du in [-(M-1) den, M den] holds every moment the rules need:
+// Et[(du - dmin)(d+1) + k], all K2 images included.
+__global__ void k_etable(int ntab, int dmin, int d, int den, int M, int closed, double hf, double L,
+                         const double* __restrict__ series, double* __restrict__ Et) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntab) return;
+    const double c = double(dmin + t) / den;                  // (eta - tau_e) / h_f
     const double lhf = log(hf);
-    for (int t = threadIdx.x; t < 128 + d; t += blockDim.x) {
-        const int e = j0 - d + t;
-        double acc[kMaxDegree + 1];
-        for (int k = 0; k <= d; ++k) acc[k] = 0.0;
-        if (e >= 0 && e < M) {
-            const int nimg = closed ? 3 : 1;
-            for (int im = 0; im < nimg; ++im) {
-                const double shift = (im == 0) ? 0.0 : (im == 1 ? -double(M) : double(M));
-                double Lk[kMaxDegree + 1];
-                local_log_moments(s_units + shift - e, d, series, Lk);
-                for (int k = 0; k <= d; ++k) acc[k] += hf * (lhf / (k + 1) + Lk[k]);
-            }
-            if (closed) {
-                const double c2 = 2.0 * log(L) * hf;
-                for (int k = 0; k <= d; ++k) acc[k] -= c2 / (k + 1);
-            }
-        }
-        for (int k = 0; k <= d; ++k) E[t][k] = acc[k];
+    double acc[kMaxDegree + 1];
+    for (int k = 0; k <= d; ++k) acc[k] = 0.0;
+    const int nimg = closed ? 3 : 1;
+    for (int im = 0; im < nimg; ++im) {
+        const double shift = (im == 0) ? 0.0 : (im == 1 ? -double(M) : double(M));
+        double Lk[kMaxDegree + 1];
+        local_log_moments(c + shift, d, series, Lk);
+        for (int k = 0; k <= d; ++k) acc[k] += hf * (lhf / (k + 1) + Lk[k]);
     }
-    __syncthreads();
-    const int j = j0 + threadIdx.x;
+    if (closed) {
+        const double c2 = 2.0 * log(L) * hf;
+        for (int k = 0; k <= d; ++k) acc[k] -= c2 / (k + 1);
+    }
+    for (int k = 0; k <= d; ++k) Et[(size_t)t * (d + 1) + k] = acc[k];
+}
+
+// mu_j(eta_m) = sum over the elements e = j-d+l of B-bar_j's support of
+// sum_k piece[l][k] E_{m,e,k} (eq. mod_mom_gen), for j in a block of 128 and
+// the node rows[blockIdx.y] (or blockIdx.y); output Z[j][col].
+__global__ void __launch_bounds__(128) k_mu_tab(int NE, int M, int d, int den, int dmin, const int* __restrict__ pos,
+                                                const int* __restrict__ rows, const double* __restrict__ piece,
+                                                const double* __restrict__ Et, double* __restrict__ Z, int ldz) {
+    const int col = blockIdx.y;
+    const int m = rows ? rows[col] : col;
+    const int j = blockIdx.x * 128 + threadIdx.x;
     if (j >= NE) return;
+    const int P = pos[m];
     double mu = 0.0;
-    for (int l = 0; l <= d; ++l) {                                  // element e = j - d + l
+    for (int l = 0; l <= d; ++l) {
         const int e = j - d + l;
         if (e < 0 || e >= M) continue;
-        for (int k = 0; k <= d; ++k) mu += piece[l * (d + 1) + k] * E[threadIdx.x + l][k];
+        const double* E = Et + (size_t)(P - e * den - dmin) * (d + 1);
+        for (int k = 0; k <= d; ++k) mu += piece[l * (d + 1) + k] * E[k];
     }
     Z[(size_t)j * ldz + col] = mu;
 }
@@ -313,6 +319,157 @@ __global__ void k_ws(int Nq, int d, const int* __restrict__ fspan, const double*
     WsT[(size_t)nn * Nq + m] = s;
     if (WsT32) WsT32[(size_t)nn * Nq + m] = (float)s;
 }
+
+// --------------------------------------------------- compressed singular rules
+// Column m' of W^s is Mu y with y = G^{-1} (B)[:, m'] (G symmetric).  y decays
+// geometrically away from m', so only the elements where it is above 1e-20
+// of its maximum contribute.  Away from the ends of [a, b] the columns are
+// shifted copies of one another (uniform knots; period 2 in the node index),
+// which the Toeplitz sequences record.
+
+// y_c = G^{-1} (B)[:, cols[c]], one thread per column; Y[c][j].
+__global__ void k_ycols(int ncols, int NE, int d, const int* __restrict__ cols, const int* __restrict__ fspan,
+                        const double* __restrict__ Bf, const double* __restrict__ L, double* __restrict__ Y) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    const int mp = cols[c], e0 = fspan[mp];
+    double* y = Y + (size_t)c * NE;
+    for (int j = 0; j < e0; ++j) y[j] = 0.0;
+    for (int j = e0; j < NE; ++j) {
+        double s = (j - e0 <= d) ? Bf[mp * (d + 1) + (j - e0)] : 0.0;
+        const int p0 = (j - d > e0) ? j - d : e0;
+        for (int p = p0; p < j; ++p) s -= L[j * (d + 1) + (j - p)] * y[p];
+        y[j] = s / L[j * (d + 1)];
+    }
+    for (int j = NE - 1; j >= 0; --j) {
+        double s = y[j];
+        const int p1 = (j + d < NE - 1) ? j + d : NE - 1;
+        for (int p = j + 1; p <= p1; ++p) s -= L[p * (d + 1) + (p - j)] * y[p];
+        y[j] = s / L[j * (d + 1)];
+    }
+}
+
+// Element range of each column and its per-element coefficients
+// Yc[c][e - elo][k] = sum_l piece[l][k] y_c[e + d - l]; one block per column.
+__global__ void __launch_bounds__(128) k_yc(int NE, int M, int d, int cap, const double* __restrict__ Y,
+                                            const double* __restrict__ piece, int* __restrict__ erange,
+                                            double* __restrict__ Yc, int* __restrict__ flag) {
+    __shared__ double smax[128];
+    __shared__ int slo[128], shi[128];
+    const int c = blockIdx.x, tid = threadIdx.x;
+    const double* y = Y + (size_t)c * NE;
+    double mx = 0.0;
+    for (int j = tid; j < NE; j += blockDim.x) mx = fmax(mx, fabs(y[j]));
+    smax[tid] = mx;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (tid < w) smax[tid] = fmax(smax[tid], smax[tid + w]);
+        __syncthreads();
+    }
+    const double tol = 1e-20 * smax[0];
+    int lo = NE, hi = -1;
+    for (int j = tid; j < NE; j += blockDim.x)
+        if (fabs(y[j]) > tol) { lo = min(lo, j); hi = max(hi, j); }
+    slo[tid] = lo;
+    shi[tid] = hi;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (tid < w) { slo[tid] = min(slo[tid], slo[tid + w]); shi[tid] = max(shi[tid], shi[tid + w]); }
+        __syncthreads();
+    }
+    const int elo = max(0, slo[0] - d), ehi = min(M - 1, shi[0]);
+    if (ehi - elo + 1 > cap || shi[0] < 0) {
+        if (tid == 0) { atomicOr(flag, 16); erange[2 * c] = 0; erange[2 * c + 1] = -1; }
+        return;
+    }
+    if (tid == 0) { erange[2 * c] = elo; erange[2 * c + 1] = ehi; }
+    for (int e = elo + tid; e <= ehi; e += blockDim.x)
+        for (int k = 0; k <= d; ++k) {
+            double s = 0.0;
+            for (int l = 0; l <= d; ++l) {
+                const int j = e + d - l;
+                if (j >= 0 && j < NE) s += piece[l * (d + 1) + k] * y[j];
+            }
+            Yc[((size_t)c * cap + (e - elo)) * (d + 1) + k] = s;
+        }
+}
+
+// Wc[c][m] = W^s[m][cols[c]] = sum_{e in range(c)} sum_k E_{m,e,k} Yc[c][e][k].
+__global__ void __launch_bounds__(256) k_wcols(int Nq, int d, int den, int dmin, int cap, const int* __restrict__ pos,
+                                               const double* __restrict__ Et, const int* __restrict__ erange,
+                                               const double* __restrict__ Yc, double* __restrict__ Wc) {
+    extern __shared__ double sY[];
+    const int c = blockIdx.y;
+    const int elo = erange[2 * c], cnt = erange[2 * c + 1] - elo + 1;
+    const int D1 = d + 1;
+    for (int t = threadIdx.x; t < cnt * D1; t += blockDim.x) sY[t] = Yc[(size_t)c * cap * D1 + t];
+    __syncthreads();
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nq) return;
+    const double* E = Et + (size_t)(pos[m] - elo * den - dmin) * D1;
+    double acc = 0.0;
+    for (int q = 0; q < cnt; ++q, E -= (size_t)den * D1)
+        for (int k = 0; k < D1; ++k) acc += E[k] * sY[q * D1 + k];
+    Wc[(size_t)c * Nq + m] = acc;
+}
+
+// Boundary rows: WsRow[r][m'] = sum_r' B-bar_{e+r'}(eta_m') z_r[e+r'], e = fspan[m'].
+__global__ void k_wrows(int Nq, int d, int nrow, const int* __restrict__ fspan, const double* __restrict__ Bf,
+                        const double* __restrict__ Z, double* __restrict__ Wr) {
+    const int r = blockIdx.y;
+    const int mp = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mp >= Nq) return;
+    const int e = fspan[mp];
+    double s = 0.0;
+    for (int q = 0; q <= d; ++q) s += Bf[mp * (d + 1) + q] * Z[(size_t)(e + q) * nrow + r];
+    Wr[(size_t)r * Nq + mp] = s;
+}
+
+// Interior Toeplitz sequences from the anchor columns: T[p][delta + Nq - 1] =
+// W^s[m][m'] for interior m' of parity p and m - m' = delta; the left anchor
+// gives delta >= 0, the right one delta < 0.
+__global__ void k_toeplitz(int Nq, int R, int aL0, int aL1, int aR0, int aR1, const double* __restrict__ WcL0,
+                           const double* __restrict__ WcL1, const double* __restrict__ WcR0,
+                           const double* __restrict__ WcR1, double* __restrict__ T) {
+    const size_t len = 2 * (size_t)Nq - 1;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2 * len) return;
+    const int p = int(idx / len);
+    const int delta = int(idx % len) - (Nq - 1);
+    double v = 0.0;
+    if (delta >= 0) {
+        const int m = (p ? aL1 : aL0) + delta;
+        if (m <= Nq - R - 1) v = (p ? WcL1 : WcL0)[m];
+    } else {
+        const int m = (p ? aR1 : aR0) + delta;
+        if (m >= R) v = (p ? WcR1 : WcR0)[m];
+    }
+    T[idx] = v;
+}
+
+__global__ void k_to_f32(size_t count, const double* __restrict__ x, float* __restrict__ y) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) y[i] = (float)x[i];
+}
+
+// Dense expansion for diagnostics: Ws[m][m'] = W^s[m][m'].
+__global__ void k_ws_expand(WsView<double> v, double* __restrict__ Ws) {
+    const int mp = blockIdx.x * blockDim.x + threadIdx.x, m = blockIdx.y;
+    if (mp >= v.Nq) return;
+    Ws[(size_t)m * v.Nq + mp] = ws_at(v, m, mp);
+}
+
+void ws_expand(igs_prob p, double* d_out) {
+    const int Nq = p->plan.Nq;
+    WsView<double> v{p->d_WsT, p->d_WsRow, p->d_WsToe, Nq, p->ws_B, p->ws_R};
+    k_ws_expand<<<dim3((Nq + 255) / 256, Nq), 256, 0, p->geom->ctx->stream>>>(v, d_out);
+    IGS_CUDA(cudaGetLastError());
+}
+
+// Boundary columns kept explicitly at each end: the columns' departure from
+// the interior shift pattern falls below 3e-13 of max|W^s| within 66, 88, 114
+// and 134 nodes for d = 2..5 (independent of N_ref); 24(d+1)+16 leaves margin.
+static int ws_boundary_columns(int d) { return 24 * (d + 1) + 16; }
 
 // ------------------------------------------------------------------ driver
 static void upload_gauss() {
@@ -391,20 +548,103 @@ void rules_build(igs_prob p) {
     ++launches;
     IGS_CUDA(cudaGetLastError());
 
-    // singular rules, dense: Z = G^{-1} Mu^T, WsT = (B)^T Z
-    p->d_Z = (double*)dev_alloc(p, sizeof(double) * (size_t)NE * Nq);
-    dim3 gm((NE + 127) / 128, Nq);
-    k_moments<<<gm, 128, 0, s>>>(Nq, NE, P.M, d, P.den, P.closed, P.hf, P.L, p->d_pos, nullptr, p->d_piece,
-                                 p->d_series, p->d_Z, Nq);
+    // element-moment table over all node/element offsets
+    const int den = P.den, M = P.M;
+    const int dmin = -(M - 1) * den;
+    const int ntab = (2 * M - 1) * den + 1;
+    double* d_Et = (double*)dev_alloc(p, sizeof(double) * (size_t)ntab * D1);
+    k_etable<<<(ntab + 127) / 128, 128, 0, s>>>(ntab, dmin, d, den, M, P.closed, P.hf, P.L, p->d_series, d_Et);
     ++launches;
-    k_gsolve<<<(Nq + 127) / 128, 128, 0, s>>>(NE, d, Nq, d_L, p->d_Z, Nq);
-    ++launches;
-    p->d_WsT = (double*)dev_alloc(p, sizeof(double) * (size_t)Nq * Nq);
-    if (p->precision == IGS_MIXED) p->d_WsT32 = (float*)dev_alloc(p, sizeof(float) * (size_t)Nq * Nq);
-    dim3 gw((Nq + 255) / 256, Nq);
-    k_ws<<<gw, 256, 0, s>>>(Nq, d, p->d_fspan, p->d_Bf, p->d_Z, Nq, p->d_WsT, p->d_WsT32);
-    ++launches;
-    IGS_CUDA(cudaGetLastError());
+
+    const bool mixed = p->precision == IGS_MIXED;
+    const int B = ws_boundary_columns(d), R = d + 2;
+    if (Nq < 2 * B + 2 * R + 64) {
+        // dense: Z = G^{-1} Mu^T, column m' of W^s for every node
+        p->ws_B = Nq;
+        p->ws_R = 0;
+        p->d_Z = (double*)dev_alloc(p, sizeof(double) * (size_t)NE * Nq);
+        k_mu_tab<<<dim3((NE + 127) / 128, Nq), 128, 0, s>>>(NE, M, d, den, dmin, p->d_pos, nullptr, p->d_piece, d_Et,
+                                                           p->d_Z, Nq);
+        ++launches;
+        k_gsolve<<<(Nq + 127) / 128, 128, 0, s>>>(NE, d, Nq, d_L, p->d_Z, Nq);
+        ++launches;
+        p->d_WsT = (double*)dev_alloc(p, sizeof(double) * (size_t)Nq * Nq);
+        if (mixed) p->d_WsT32 = (float*)dev_alloc(p, sizeof(float) * (size_t)Nq * Nq);
+        k_ws<<<dim3((Nq + 255) / 256, Nq), 256, 0, s>>>(Nq, d, p->d_fspan, p->d_Bf, p->d_Z, Nq, p->d_WsT,
+                                                       p->d_WsT32);
+        ++launches;
+        IGS_CUDA(cudaGetLastError());
+    } else {
+        // compressed: B boundary columns at each end, four interior anchor
+        // columns (two per node parity, one near each end), R boundary rows
+        p->ws_B = B;
+        p->ws_R = R;
+        const int ncols = 2 * B + 4;
+        std::vector<int> cols(ncols);
+        for (int c = 0; c < B; ++c) { cols[c] = c; cols[B + c] = Nq - B + c; }
+        int aR[2];
+        for (int q = 0; q < 2; ++q) aR[q] = Nq - B - 1 - ((Nq - B - 1 - B - q) & 1);
+        cols[2 * B] = B;
+        cols[2 * B + 1] = B + 1;
+        cols[2 * B + 2] = aR[0];
+        cols[2 * B + 3] = aR[1];
+        int* d_cols = (int*)dev_alloc(p, sizeof(int) * ncols);
+        IGS_CUDA(cudaMemcpyAsync(d_cols, cols.data(), sizeof(int) * ncols, cudaMemcpyHostToDevice, s));
+        double* d_Y = (double*)dev_alloc(p, sizeof(double) * (size_t)ncols * NE);
+        k_ycols<<<(ncols + 63) / 64, 64, 0, s>>>(ncols, NE, d, d_cols, p->d_fspan, p->d_Bf, d_L, d_Y);
+        ++launches;
+        const int cap = std::min(M, 1024);
+        int* d_er = (int*)dev_alloc(p, sizeof(int) * 2 * ncols);
+        double* d_Yc = (double*)dev_alloc(p, sizeof(double) * (size_t)ncols * cap * D1);
+        k_yc<<<ncols, 128, 0, s>>>(NE, M, d, cap, d_Y, p->d_piece, d_er, d_Yc, p->d_flag);
+        ++launches;
+        double* d_Wc = (double*)dev_alloc(p, sizeof(double) * (size_t)ncols * Nq);
+        const size_t ysm = sizeof(double) * (size_t)cap * D1;
+        IGS_CUDA(cudaFuncSetAttribute(k_wcols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm));
+        k_wcols<<<dim3((Nq + 255) / 256, ncols), 256, ysm, s>>>(Nq, d, den, dmin, cap, p->d_pos, d_Et, d_er, d_Yc,
+                                                               d_Wc);
+        ++launches;
+        // boundary rows: full rules at the first and last R nodes
+        std::vector<int> rows(2 * R);
+        for (int r = 0; r < R; ++r) { rows[r] = r; rows[R + r] = Nq - R + r; }
+        int* d_rows = (int*)dev_alloc(p, sizeof(int) * 2 * R);
+        IGS_CUDA(cudaMemcpyAsync(d_rows, rows.data(), sizeof(int) * 2 * R, cudaMemcpyHostToDevice, s));
+        double* d_Zr = (double*)dev_alloc(p, sizeof(double) * (size_t)NE * 2 * R);
+        k_mu_tab<<<dim3((NE + 127) / 128, 2 * R), 128, 0, s>>>(NE, M, d, den, dmin, p->d_pos, d_rows, p->d_piece,
+                                                              d_Et, d_Zr, 2 * R);
+        k_gsolve<<<1, 2 * R, 0, s>>>(NE, d, 2 * R, d_L, d_Zr, 2 * R);
+        p->d_WsRow = (double*)dev_alloc(p, sizeof(double) * (size_t)2 * R * Nq);
+        k_wrows<<<dim3((Nq + 255) / 256, 2 * R), 256, 0, s>>>(Nq, d, 2 * R, p->d_fspan, p->d_Bf, d_Zr, p->d_WsRow);
+        launches += 3;
+        // boundary columns (first 2B rows of Wc) and Toeplitz sequences
+        p->d_WsT = (double*)dev_alloc(p, sizeof(double) * (size_t)2 * B * Nq);
+        IGS_CUDA(cudaMemcpyAsync(p->d_WsT, d_Wc, sizeof(double) * (size_t)2 * B * Nq, cudaMemcpyDeviceToDevice, s));
+        const size_t tlen = 2 * (2 * (size_t)Nq - 1);
+        p->d_WsToe = (double*)dev_alloc(p, sizeof(double) * tlen);
+        k_toeplitz<<<(unsigned)((tlen + 255) / 256), 256, 0, s>>>(
+            Nq, R, B, B + 1, aR[0], aR[1], d_Wc + (size_t)(2 * B) * Nq, d_Wc + (size_t)(2 * B + 1) * Nq,
+            d_Wc + (size_t)(2 * B + 2) * Nq, d_Wc + (size_t)(2 * B + 3) * Nq, p->d_WsToe);
+        launches += 1;
+        if (mixed) {
+            const size_t nc = (size_t)2 * B * Nq, nr = (size_t)2 * R * Nq;
+            p->d_WsT32 = (float*)dev_alloc(p, sizeof(float) * nc);
+            p->d_WsRow32 = (float*)dev_alloc(p, sizeof(float) * nr);
+            p->d_WsToe32 = (float*)dev_alloc(p, sizeof(float) * tlen);
+            k_to_f32<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(nc, p->d_WsT, p->d_WsT32);
+            k_to_f32<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(nr, p->d_WsRow, p->d_WsRow32);
+            k_to_f32<<<(unsigned)((tlen + 255) / 256), 256, 0, s>>>(tlen, p->d_WsToe, p->d_WsToe32);
+            launches += 3;
+        }
+        IGS_CUDA(cudaGetLastError());
+        dev_free(p, d_cols);
+        dev_free(p, d_Y);
+        dev_free(p, d_er);
+        dev_free(p, d_Yc);
+        dev_free(p, d_Wc);
+        dev_free(p, d_rows);
+        dev_free(p, d_Zr);
+    }
+    dev_free(p, d_Et);
 
     int flag = 0;
     IGS_CUDA(cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -414,7 +654,7 @@ void rules_build(igs_prob p) {
     IGS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    dev_free(p, p->d_Z);
+    if (p->d_Z) dev_free(p, p->d_Z);
     dev_free(p, d_L);
     dev_free(p, d_tk);
     p->timing.rules_ms = ms;

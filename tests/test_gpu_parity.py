@@ -27,6 +27,11 @@ CASES = [
     ("star", 8, 3, 4),
     ("arc", 20, 2, 1),
     ("arc", 37, 3, 2),
+    # large enough for the stored form of the singular rules (explicit end
+    # columns and rows plus the interior shift pattern)
+    ("star", 200, 2, 1),
+    ("star", 160, 5, 2),
+    ("arc", 150, 4, 2),
 ]
 
 
