@@ -185,22 +185,68 @@ __global__ void k_gram(int NE, int d, const int* __restrict__ gfirst, const int*
     for (int r = 0; r <= d; ++r) G[j * (d + 1) + r] = acc[r];
 }
 
-// Banded Cholesky G = L L^T in place (one thread; L(j, j-r) stored at L[j][r]).
-__global__ void k_chol_band(int NE, int d, const double* __restrict__ G, double* __restrict__ L, int* __restrict__ flag) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    for (int j = 0; j < NE; ++j) {
-        const int k0 = (j - d > 0) ? j - d : 0;
-        for (int k = k0; k <= j; ++k) {
-            double s = G[k * (d + 1) + (j - k)];
-            for (int p = k0; p < k; ++p) s -= L[j * (d + 1) + (j - p)] * L[k * (d + 1) + (k - p)];
-            if (k < j) {
-                L[j * (d + 1) + (j - k)] = s / L[k * (d + 1)];
-            } else {
-                if (!(s > 0.0)) { atomicOr(flag, 8); return; }
-                L[j * (d + 1)] = sqrt(s);
-            }
+// Banded Cholesky G = L L^T (L(j, j-r) stored at L[j][r]), one block.  G is
+// Toeplitz away from the ends of I (uniform knots), and the rows of the
+// Cholesky factor of a banded Toeplitz SPD matrix converge geometrically to a
+// fixed row.  Thread 0 runs the recurrence until two consecutive rows agree to
+// 4e-16 (relative) on equal rows of G; the block then copies that row over
+// the following rows whose G rows are identical, and thread 0 finishes the
+// rows after them.  Without convergence the recurrence simply runs to the end.
+__device__ void chol_row(int j, int d, const double* __restrict__ G, double* __restrict__ L, int* flag) {
+    const int k0 = (j - d > 0) ? j - d : 0;
+    for (int k = k0; k <= j; ++k) {
+        double s = G[k * (d + 1) + (j - k)];
+        for (int p = k0; p < k; ++p) s -= L[j * (d + 1) + (j - p)] * L[k * (d + 1) + (k - p)];
+        if (k < j) {
+            L[j * (d + 1) + (j - k)] = s / L[k * (d + 1)];
+        } else {
+            if (!(s > 0.0)) { atomicOr(flag, 8); s = 1.0; }
+            L[j * (d + 1)] = sqrt(s);
         }
     }
+}
+
+__device__ bool same_g_row(const double* G, int d, int a, int b) {
+    for (int r = 0; r <= d; ++r)
+        if (G[a * (d + 1) + r] != G[b * (d + 1) + r]) return false;
+    return true;
+}
+
+__global__ void __launch_bounds__(256) k_chol_band(int NE, int d, const double* __restrict__ G, double* __restrict__ L,
+                                                   int* __restrict__ flag) {
+    __shared__ int s_conv, s_end;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        int conv = -1;
+        for (int j = 0; j < NE; ++j) {
+            chol_row(j, d, G, L, flag);
+            if (j >= 4 * (d + 1) && same_g_row(G, d, j, j - 1)) {
+                bool same = true;
+                for (int r = 0; r <= d && same; ++r) {
+                    const double a = L[j * (d + 1) + r], b = L[(j - 1) * (d + 1) + r];
+                    same = fabs(a - b) <= 4e-16 * fabs(a);
+                }
+                if (same) { conv = j; break; }
+            }
+        }
+        s_conv = conv;
+        s_end = NE;
+    }
+    __syncthreads();
+    const int conv = s_conv;
+    if (conv < 0) return;
+    // first row after conv whose G row differs from G[conv]
+    for (int t = conv + 1 + tid; t < NE; t += blockDim.x)
+        if (!same_g_row(G, d, t, conv)) atomicMin(&s_end, t);
+    __syncthreads();
+    const int end = s_end;
+    for (int idx = tid; idx < (end - conv - 1) * (d + 1); idx += blockDim.x) {
+        const int t = conv + 1 + idx / (d + 1), r = idx % (d + 1);
+        L[t * (d + 1) + r] = L[conv * (d + 1) + r];
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int j = end; j < NE; ++j) chol_row(j, d, G, L, flag);
 }
 
 // ----------------------------------------------------------------- moments
@@ -327,25 +373,39 @@ __global__ void k_ws(int Nq, int d, const int* __restrict__ fspan, const double*
 // shifted copies of one another (uniform knots; period 2 in the node index),
 // which the Toeplitz sequences record.
 
-// y_c = G^{-1} (B)[:, cols[c]], one thread per column; Y[c][j].
+// y_c = G^{-1} (B)[:, cols[c]], one thread per column; Y[c][j] (zeroed by the
+// caller).  The solution decays geometrically away from the column's
+// elements: each substitution stops once d+1 consecutive values are below
+// 1e-40 of the largest so far (the rest is zero to far below the 1e-20 cut
+// applied afterwards).
 __global__ void k_ycols(int ncols, int NE, int d, const int* __restrict__ cols, const int* __restrict__ fspan,
                         const double* __restrict__ Bf, const double* __restrict__ L, double* __restrict__ Y) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncols) return;
     const int mp = cols[c], e0 = fspan[mp];
     double* y = Y + (size_t)c * NE;
-    for (int j = 0; j < e0; ++j) y[j] = 0.0;
+    double big = 0.0;
+    int small = 0, jstop = NE - 1;
     for (int j = e0; j < NE; ++j) {
         double s = (j - e0 <= d) ? Bf[mp * (d + 1) + (j - e0)] : 0.0;
         const int p0 = (j - d > e0) ? j - d : e0;
         for (int p = p0; p < j; ++p) s -= L[j * (d + 1) + (j - p)] * y[p];
-        y[j] = s / L[j * (d + 1)];
+        const double v = s / L[j * (d + 1)];
+        y[j] = v;
+        big = fmax(big, fabs(v));
+        small = (j > e0 + d && fabs(v) <= 1e-40 * big) ? small + 1 : 0;
+        if (small > d) { jstop = j; break; }
     }
-    for (int j = NE - 1; j >= 0; --j) {
+    small = 0;
+    for (int j = jstop; j >= 0; --j) {
         double s = y[j];
-        const int p1 = (j + d < NE - 1) ? j + d : NE - 1;
+        const int p1 = (j + d < jstop) ? j + d : jstop;
         for (int p = j + 1; p <= p1; ++p) s -= L[p * (d + 1) + (p - j)] * y[p];
-        y[j] = s / L[j * (d + 1)];
+        const double v = s / L[j * (d + 1)];
+        y[j] = v;
+        big = fmax(big, fabs(v));
+        small = (j < e0 && fabs(v) <= 1e-40 * big) ? small + 1 : 0;
+        if (small > d) break;
     }
 }
 
@@ -544,7 +604,7 @@ void rules_build(igs_prob p) {
     ++launches;
     k_gram<<<(NE + 127) / 128, 128, 0, s>>>(NE, d, p->d_gfirst, p->d_glast, p->d_fspan, p->d_Bf, p->d_G);
     ++launches;
-    k_chol_band<<<1, 1, 0, s>>>(NE, d, p->d_G, d_L, p->d_flag);
+    k_chol_band<<<1, 256, 0, s>>>(NE, d, p->d_G, d_L, p->d_flag);
     ++launches;
     IGS_CUDA(cudaGetLastError());
 
@@ -591,6 +651,7 @@ void rules_build(igs_prob p) {
         int* d_cols = (int*)dev_alloc(p, sizeof(int) * ncols);
         IGS_CUDA(cudaMemcpyAsync(d_cols, cols.data(), sizeof(int) * ncols, cudaMemcpyHostToDevice, s));
         double* d_Y = (double*)dev_alloc(p, sizeof(double) * (size_t)ncols * NE);
+        IGS_CUDA(cudaMemsetAsync(d_Y, 0, sizeof(double) * (size_t)ncols * NE, s));
         k_ycols<<<(ncols + 63) / 64, 64, 0, s>>>(ncols, NE, d, d_cols, p->d_fspan, p->d_Bf, d_L, d_Y);
         ++launches;
         const int cap = std::min(M, 1024);
