@@ -210,6 +210,53 @@ int igs_build_rhs_noalloc(igs_prob prob, const double* uD, int nrhs, double* bet
  * Errors: STATE (not assembled / no rhs), NOT_SPD, NOT_CONVERGED, CUDA. */
 int igs_solve(igs_prob prob, const double* beta, int nrhs, double* alpha_out, double* resid_out, int mem);
 
+/* Download the assembled A (eq. IK1e2 plus IK1e2_bis, Sect. 5) without
+ * assembling again, e.g. after igs_batch_assemble.  Arguments as for
+ * igs_assemble's A_out, ld, mem, dtype.  Errors: INVALID_ARG, STATE (not
+ * assembled), NO_MEMORY, CUDA. */
+int igs_get_matrix(igs_prob prob, void* A_out, int64_t ld, int mem, int dtype);
+
+/* ------------------------------------------------------------ batched form */
+
+/* Many assemblies in one persistent launch.  The paper assembles one matrix at
+ * a time (Sect. 5, Algorithm 3); this groups the same computation for a set of
+ * MIXED-tier problems: one batched pass evaluates every problem's geometry and
+ * node records, then one persistent kernel runs all (problem, tile) units from
+ * a shared work list; both are captured in a CUDA graph.  Each problem's A is
+ * the one igs_assemble would produce (same per-tile arithmetic).
+ *
+ * igs_batch_create: `probs` are count MIXED-tier problems of ctx (borrowed;
+ *   a problem cannot be destroyed while a batch holds it: STATE).  Problems
+ *   may differ in curve, n, degree and N_ref.  Errors: INVALID_ARG.
+ * igs_batch_assemble: builds rules where missing (first call), then assembles
+ *   every problem; afterwards each problem is in the state igs_assemble leaves
+ *   (factor invalidated).  A problem whose geometry was replaced by
+ *   igs_set_geometry is picked up (the graph is rebuilt).  ms_out (may be NULL):
+ *   device time of the graph.  Errors: INVALID_ARG (a tile's node range above
+ *   512 nodes), NO_MEMORY, CUDA.
+ * igs_batch_tune: times every configuration (tile 32 or 16 DoFs; unit order
+ *   natural, interleaved across problems or largest problem first; the
+ *   occupancy limit of CTAs per SM or half of it), `reps` timed runs each
+ *   (1..100) after one warm-up, keeps and returns the fastest.
+ * igs_batch_set_config / igs_batch_get_config: explicit configuration
+ *   (ctas_per_sm 0 = occupancy limit); get returns the last run's time in ms. */
+typedef struct igs_batch_s* igs_batch;
+#define IGS_ORDER_NATURAL       0   /* problem after problem, tiles row-major */
+#define IGS_ORDER_INTERLEAVED   1   /* round-robin over the problems          */
+#define IGS_ORDER_LARGEST_FIRST 2   /* problems by tile count, largest first  */
+typedef struct igs_batch_config {
+    int32_t tile;          /* DoFs per tile side: 16 or 32 */
+    int32_t order;         /* IGS_ORDER_* */
+    int32_t ctas_per_sm;   /* resident CTAs per SM, 0 = occupancy limit */
+    float ms;              /* measured time (outputs only) */
+} igs_batch_config;
+int igs_batch_create(igs_ctx ctx, igs_batch* out, const igs_prob* probs, int count);
+int igs_batch_destroy(igs_batch batch);
+int igs_batch_assemble(igs_batch batch, float* ms_out);
+int igs_batch_tune(igs_batch batch, igs_batch_config* best_out, int reps);
+int igs_batch_set_config(igs_batch batch, const igs_batch_config* cfg);
+int igs_batch_get_config(igs_batch batch, igs_batch_config* cfg);
+
 /* Diagnostic download of the rules for parity checks (HOST outputs, FP64):
  *   eta[n_quad]; W_band[n_quad * (degree+1)]: W_band[m*(d+1)+r] = w^(i)_m for
  *   the test function i = (first(m) + r) mod n containing eta_m (0 if none),

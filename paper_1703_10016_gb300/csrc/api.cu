@@ -70,11 +70,11 @@ static void upload(igs_prob p, T*& d, const std::vector<T>& h) {
         IGS_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, p->geom->ctx->stream));
 }
 
-static void ensure_rules(igs_prob p) {
+void ensure_rules(igs_prob p) {
     if (!p->rules_ready) rules_build(p);
 }
 
-static void ensure_geometry(igs_prob p) {
+void ensure_geometry(igs_prob p) {
     ensure_rules(p);
     if (!p->geometry_ready) geometry_nodes(p);
 }
@@ -83,28 +83,32 @@ static void ensure_geometry(igs_prob p) {
 
 using namespace igs;
 
-#define API_BEGIN \
-    try {
-#define API_END                                                               \
-    }                                                                         \
-    catch (const igs::Error& e) {                                             \
-        set_error(e.msg);                                                     \
-        return e.code;                                                        \
-    }                                                                         \
-    catch (const std::bad_alloc&) {                                           \
-        set_error("host allocation failed");                                  \
-        return IGS_E_NO_MEMORY;                                               \
-    }                                                                         \
-    catch (...) {                                                             \
-        set_error("unexpected error");                                        \
-        return IGS_E_CUDA;                                                    \
-    }                                                                         \
-    return IGS_OK;
+namespace igs {
+// Copy the assembled A (tier type) to a caller buffer of the requested type.
+static void copy_matrix(igs_prob p, void* A_out, int64_t ld, int mem, int dtype) {
+    const Plan& P = p->plan;
+    cudaStream_t s = p->geom->ctx->stream;
+    const bool mixed = p->precision == IGS_MIXED;
+    const size_t osz = dtype == IGS_F64 ? 8 : 4;
+    void* dst = A_out;
+    void* tmp = nullptr;
+    if (mem == IGS_MEM_HOST) { tmp = dev_alloc(p, osz * (size_t)P.n * P.n); dst = tmp; }
+    const int64_t dld = (mem == IGS_MEM_HOST) ? P.n : ld;
+    dim3 grid((P.n + 255) / 256, P.n);
+    if (mixed && dtype == IGS_F32) k_copy_convert<float, float><<<grid, 256, 0, s>>>(P.n, (const float*)p->d_A, (float*)dst, dld);
+    else if (mixed) k_copy_convert<float, double><<<grid, 256, 0, s>>>(P.n, (const float*)p->d_A, (double*)dst, dld);
+    else if (dtype == IGS_F32) k_copy_convert<double, float><<<grid, 256, 0, s>>>(P.n, (const double*)p->d_A, (float*)dst, dld);
+    else k_copy_convert<double, double><<<grid, 256, 0, s>>>(P.n, (const double*)p->d_A, (double*)dst, dld);
+    p->launches++;
+    IGS_CUDA(cudaGetLastError());
+    if (mem == IGS_MEM_HOST) {
+        IGS_CUDA(cudaMemcpy2DAsync(A_out, ld * osz, tmp, P.n * osz, P.n * osz, P.n, cudaMemcpyDeviceToHost, s));
+        IGS_CUDA(cudaStreamSynchronize(s));
+        dev_free(p, tmp);
+    }
+}
 
-#define REQUIRE(cond, code, msg)                     \
-    do {                                             \
-        if (!(cond)) throw igs::Error((code), (msg)); \
-    } while (0)
+}  // namespace igs
 
 extern "C" {
 
@@ -133,7 +137,8 @@ int igs_create(igs_ctx* out, int device, void* cuda_stream) {
 int igs_destroy(igs_ctx ctx) {
     API_BEGIN
     REQUIRE(ctx, IGS_E_INVALID_ARG, "ctx is NULL");
-    REQUIRE(ctx->live_geoms == 0 && ctx->live_probs == 0, IGS_E_STATE, "destroy geometries and problems first");
+    REQUIRE(ctx->live_geoms == 0 && ctx->live_probs == 0 && ctx->live_batches == 0, IGS_E_STATE,
+            "destroy batches, geometries and problems first");
     IGS_CUDA(cudaSetDevice(ctx->device));
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -234,6 +239,7 @@ int igs_create_problem(igs_geom g, igs_prob* out, int degree, int n_elems, int n
 int igs_destroy_problem(igs_prob p) {
     API_BEGIN
     REQUIRE(p, IGS_E_INVALID_ARG, "prob is NULL");
+    REQUIRE(p->live_batches == 0, IGS_E_STATE, "destroy the batches that hold this problem first");
     IGS_CUDA(cudaSetDevice(p->geom->ctx->device));
     void* ptrs[] = {p->d_pos, p->d_jfirst, p->d_member, p->d_fspan,
                      p->d_lo, p->d_hi, p->d_jr, p->d_gfirst, p->d_glast,
@@ -322,26 +328,7 @@ int igs_assemble(igs_prob p, void* A_out, int64_t ld, int mem, int dtype) {
     IGS_CUDA(cudaEventRecord(e2, s));
     p->assembled = 1;
     p->factored = 0;
-    if (A_out) {
-        const bool mixed = p->precision == IGS_MIXED;
-        const size_t osz = dtype == IGS_F64 ? 8 : 4;
-        void* dst = A_out;
-        void* tmp = nullptr;
-        if (mem == IGS_MEM_HOST) { tmp = dev_alloc(p, osz * (size_t)P.n * P.n); dst = tmp; }
-        const int64_t dld = (mem == IGS_MEM_HOST) ? P.n : ld;
-        dim3 grid((P.n + 255) / 256, P.n);
-        if (mixed && dtype == IGS_F32) k_copy_convert<float, float><<<grid, 256, 0, s>>>(P.n, (const float*)p->d_A, (float*)dst, dld);
-        else if (mixed) k_copy_convert<float, double><<<grid, 256, 0, s>>>(P.n, (const float*)p->d_A, (double*)dst, dld);
-        else if (dtype == IGS_F32) k_copy_convert<double, float><<<grid, 256, 0, s>>>(P.n, (const double*)p->d_A, (float*)dst, dld);
-        else k_copy_convert<double, double><<<grid, 256, 0, s>>>(P.n, (const double*)p->d_A, (double*)dst, dld);
-        p->launches++;
-        IGS_CUDA(cudaGetLastError());
-        if (mem == IGS_MEM_HOST) {
-            IGS_CUDA(cudaMemcpy2DAsync(A_out, ld * osz, tmp, P.n * osz, P.n * osz, P.n, cudaMemcpyDeviceToHost, s));
-            IGS_CUDA(cudaStreamSynchronize(s));
-            dev_free(p, tmp);
-        }
-    }
+    if (A_out) copy_matrix(p, A_out, ld, mem, dtype);
     IGS_CUDA(cudaEventSynchronize(e2));
     float g_ms = 0, a_ms = 0;
     cudaEventElapsedTime(&g_ms, e0, e1);
@@ -350,6 +337,19 @@ int igs_assemble(igs_prob p, void* A_out, int64_t ld, int mem, int dtype) {
     p->timing.assemble_ms = a_ms;
     cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
     p->timing.kernel_launches = p->launches;
+    API_END
+}
+
+int igs_get_matrix(igs_prob p, void* A_out, int64_t ld, int mem, int dtype) {
+    API_BEGIN
+    REQUIRE(p && A_out, IGS_E_INVALID_ARG, "prob and A_out must be set");
+    REQUIRE(p->assembled, IGS_E_STATE, "not assembled");
+    REQUIRE(ld >= p->plan.n, IGS_E_INVALID_ARG, "ld < n");
+    REQUIRE(mem == IGS_MEM_HOST || mem == IGS_MEM_DEVICE, IGS_E_INVALID_ARG, "bad mem kind");
+    REQUIRE(dtype == IGS_F64 || dtype == IGS_F32, IGS_E_INVALID_ARG, "bad dtype");
+    IGS_CUDA(cudaSetDevice(p->geom->ctx->device));
+    copy_matrix(p, A_out, ld, mem, dtype);
+    IGS_CUDA(cudaStreamSynchronize(p->geom->ctx->stream));
     API_END
 }
 

@@ -21,6 +21,7 @@
 // which keeps their relative error at FP32 rounding even for adjacent nodes.
 // Limits (eq. F1_lim and the corner limit): K1(s,s) = ln J(s);
 // K1(a,b) = K1(b,a) = ln J - ln 2 on a closed curve.
+#include "bspline_dev.cuh"
 #include "igs_internal.h"
 
 namespace igs {
@@ -28,7 +29,6 @@ namespace igs {
 constexpr int kTile = 32;
 
 struct NodeD { double x, y, e, eb, lnJ; };
-struct NodeF { float xh, xl, yh, yl, eh, el, ebh, ebl, lnJ; };
 
 template <typename T> struct NodeOf;
 template <> struct NodeOf<double> { using type = NodeD; };
@@ -56,12 +56,13 @@ __device__ __forceinline__ void split(double v, float& hi, float& lo) {
     lo = (float)(v - (double)hi);
 }
 
-__global__ void k_prep_f(int Nq, int d, double L, const double* __restrict__ geo, const double* __restrict__ eta,
-                         const double* __restrict__ W, const double* __restrict__ Bt, NodeF* __restrict__ nodes,
-                         float* __restrict__ P, float* __restrict__ Q) {
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= Nq) return;
-    const double J = geo[4 * Nq + m];
+// FP32-tier node record and weights of node m (float-float coordinates and
+// parameter offsets, ln J, P = J W, Q = J B_test).
+__device__ __forceinline__ void prep_f_node(int m, int Nq, int d, double L, const double* __restrict__ geo,
+                                            const double* __restrict__ eta, const double* __restrict__ W,
+                                            const double* __restrict__ Bt, NodeF* __restrict__ nodes,
+                                            float* __restrict__ P, float* __restrict__ Q) {
+    const double J = geo[4 * (size_t)Nq + m];
     double e = eta[m] - eta[0], eb = L - e;
     if (m == Nq - 1) { e = L; eb = 0.0; }
     if (m == 0) { e = 0.0; eb = L; }
@@ -76,6 +77,14 @@ __global__ void k_prep_f(int Nq, int d, double L, const double* __restrict__ geo
         P[m * (d + 1) + k] = (float)(J * W[m * (d + 1) + k]);
         Q[m * (d + 1) + k] = (float)(J * Bt[m * (d + 1) + k]);
     }
+}
+
+__global__ void k_prep_f(int Nq, int d, double L, const double* __restrict__ geo, const double* __restrict__ eta,
+                         const double* __restrict__ W, const double* __restrict__ Bt, NodeF* __restrict__ nodes,
+                         float* __restrict__ P, float* __restrict__ Q) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nq) return;
+    prep_f_node(m, Nq, d, L, geo, eta, W, Bt, nodes, P, Q);
 }
 
 // K1 between two distinct, non-corner nodes.
@@ -200,24 +209,32 @@ __device__ __forceinline__ float ln_pos(float x) {
 // node range (rounded up to a warp), so that no thread idles in stage 1.  The
 // B-range nodes are kept in shared memory as 16-byte records read by
 // broadcast; the singular weight for the next pair is fetched one step ahead.
-template <int D, bool CLOSED>
-__global__ void __launch_bounds__(1024) k_assemble_f(
-    int n, int Nq, float invL2, const int* __restrict__ lo, const int* __restrict__ hi,
-    const int* __restrict__ jfirst, const NodeF* __restrict__ nodes, const float* __restrict__ P,
-    const float* __restrict__ Q, const WsView<float> wsv, float* __restrict__ A, int64_t ld, int maxr) {
+// Tile (I, J) of TI x TI entries of A; `smem` as sized by tile_smem_f.
+template <int D, bool CLOSED, int TI>
+__device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned char* smem) {
     constexpr int D1 = D + 1;
     constexpr int NV = (D1 + 3) / 4;                   // float4s per weight row
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int i0 = blockIdx.y * kTile, j0 = blockIdx.x * kTile;
-    const int ni = min(kTile, n - i0), nj = min(kTile, n - j0);
+    const int n = t.n, Nq = t.Nq, maxr = t.maxr;
+    const float invL2 = t.invL2;
+    const int* __restrict__ lo = t.lo;
+    const int* __restrict__ hi = t.hi;
+    const int* __restrict__ jfirst = t.jfirst;
+    const NodeF* __restrict__ nodes = t.nodes;
+    const float* __restrict__ P = t.P;
+    const float* __restrict__ Q = t.Q;
+    const WsView<float> wsv = t.ws;
+    const int i0 = I * TI, j0 = J * TI;
+    const int ni = min(TI, n - i0), nj = min(TI, n - j0);
     const int uA0 = lo[i0], Na = hi[i0 + ni - 1] - uA0 + 1;
     const int uB0 = lo[j0], Nb = hi[j0 + nj - 1] - uB0 + 1;
+    // 16-byte records first, then 8-, then 4-byte arrays: every offset stays
+    // aligned for any maxr
     float4* sBg = (float4*)smem;                       // [maxr][2]: (xh, xl, yh, yl), (eh, el, ebh, ebl)
     float4* sBw = sBg + 2 * maxr;                      // [maxr][2 NV]: P row, Q row (zero padded)
-    float* sPA = (float*)(sBw + 2 * NV * maxr);        // [maxr][D1]
-    float* sS1 = sPA + maxr * D1;                      // [maxr][kTile + 1]
-    int2* sBm = (int2*)(sS1 + maxr * (kTile + 1));     // [maxr]: (m, first column - j0)
+    int2* sBm = (int2*)(sBw + 2 * NV * maxr);          // [maxr]: (m, first column - j0)
     int* sJA = (int*)(sBm + maxr);                     // [maxr]
+    float* sPA = (float*)(sJA + maxr);                 // [maxr][D1]
+    float* sS1 = sPA + maxr * D1;                      // [maxr][TI + 1]
 
     for (int v = threadIdx.x; v < Nb; v += blockDim.x) {
         const int u = uB0 + v, m = pmod(u, Nq), per = pdiv(u, Nq);
@@ -244,8 +261,7 @@ __global__ void __launch_bounds__(1024) k_assemble_f(
     }
     __syncthreads();
 
-    const int a = threadIdx.x;
-    if (a < Na) {
+    for (int a = threadIdx.x; a < Na; a += blockDim.x) {
         const int ma = pmod(uA0 + a, Nq);
         const NodeF na = nodes[ma];
         const float lnJ = na.lnJ;
@@ -253,7 +269,7 @@ __global__ void __launch_bounds__(1024) k_assemble_f(
 #pragma unroll
         for (int r = 0; r < D1; ++r) acc[r] = 0.0f;
         int jcur = sBm[0].y;
-        float* row = sS1 + a * (kTile + 1);
+        float* row = sS1 + a * (TI + 1);
         // singular weights of the next kPre pairs in flight (ring in registers)
         constexpr int kPre = 4;
         float wq[kPre];
@@ -306,30 +322,41 @@ __global__ void __launch_bounds__(1024) k_assemble_f(
         float s = 0.0f;
         for (int b = a0; b <= a1; ++b) {
             const int r = il - sJA[b];
-            if (r >= 0 && r <= D) s += sPA[b * D1 + r] * sS1[b * (kTile + 1) + jl];
+            if (r >= 0 && r <= D) s += sPA[b * D1 + r] * sS1[b * (TI + 1) + jl];
         }
-        A[(size_t)i * ld + j0 + jl] = scale * s;
+        t.A[(size_t)i * t.ld + j0 + jl] = scale * s;
     }
 }
 
-static size_t tile_smem_f(int maxr, int d) {
+template <int D, bool CLOSED>
+__global__ void __launch_bounds__(1024) k_assemble_f(const TileF t) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    tile_f<D, CLOSED, kTile>(t, blockIdx.y, blockIdx.x, smem);
+}
+
+size_t tile_smem_f(int maxr, int d, int TI) {
     const int NV = (d + 1 + 3) / 4;
-    return (size_t)maxr * (2 + 2 * NV) * 16 + (size_t)maxr * (d + 1) * 4 + (size_t)maxr * (kTile + 1) * 4 +
+    return (size_t)maxr * (2 + 2 * NV) * 16 + (size_t)maxr * (d + 1) * 4 + (size_t)maxr * (TI + 1) * 4 +
            (size_t)maxr * 8 + (size_t)maxr * 4 + 64;
+}
+
+TileF tile_args_f(igs_prob p, int maxr) {
+    const Plan& P = p->plan;
+    return TileF{P.n, P.Nq, (float)(1.0 / (P.L * P.L)), p->d_lo, p->d_hi, p->d_jfirst, (const NodeF*)p->d_nodes,
+                 (const float*)p->d_P, (const float*)p->d_Q,
+                 WsView<float>{p->d_WsT32, p->d_WsRow32, p->d_WsToe32, P.Nq, p->ws_B, p->ws_R}, (float*)p->d_A,
+                 (int64_t)P.n, maxr};
 }
 
 template <int D, bool CLOSED>
 static void launch_tile_f(igs_prob p, int maxr, cudaStream_t s) {
     const Plan& P = p->plan;
-    const size_t sm = tile_smem_f(maxr, D);
+    const size_t sm = tile_smem_f(maxr, D, kTile);
     auto kern = k_assemble_f<D, CLOSED>;
     IGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int nt = (P.n + kTile - 1) / kTile;
     const int threads = std::min(1024, (maxr + 31) / 32 * 32);
-    kern<<<dim3(nt, nt), threads, sm, s>>>(P.n, P.Nq, (float)(1.0 / (P.L * P.L)), p->d_lo, p->d_hi, p->d_jfirst,
-                                           (const NodeF*)p->d_nodes, (const float*)p->d_P, (const float*)p->d_Q,
-                                           WsView<float>{p->d_WsT32, p->d_WsRow32, p->d_WsToe32, P.Nq, p->ws_B, p->ws_R},
-                                           (float*)p->d_A, (int64_t)P.n, maxr);
+    kern<<<dim3(nt, nt), threads, sm, s>>>(tile_args_f(p, maxr));
     IGS_CUDA(cudaGetLastError());
 }
 
@@ -383,10 +410,10 @@ static void launch_tile_deg(igs_prob p, int maxr, cudaStream_t s) {
     }
 }
 
-static int max_tile_range(const Plan& P) {
+int max_tile_range(const Plan& P, int TI) {
     int mx = 0;
-    for (int i0 = 0; i0 < P.n; i0 += kTile) {
-        int i1 = std::min(P.n, i0 + kTile) - 1;
+    for (int i0 = 0; i0 < P.n; i0 += TI) {
+        int i1 = std::min(P.n, i0 + TI) - 1;
         mx = std::max(mx, P.hi[i1] - P.lo[i0] + 1);
     }
     return mx;
@@ -422,10 +449,92 @@ void assemble_matrix(igs_prob p) {
     const bool mixed = p->precision == IGS_MIXED;
     const size_t esz = mixed ? sizeof(float) : sizeof(double);
     if (!p->d_A) p->d_A = dev_alloc(p, esz * (size_t)P.n * P.n);
-    const int maxr = max_tile_range(P);
+    const int maxr = max_tile_range(P, kTile);
     if (mixed) launch_tile_deg<float>(p, maxr, s);
     else launch_tile_deg<double>(p, maxr, s);
     p->launches++;
+}
+
+// ------------------------------------------------------------------ batched form
+constexpr int kBatchMaxThreads = 512;
+// Geometry and FP32 node records of many problems in one launch: one thread
+// per node over the concatenated node lists (items sorted by node0).
+__global__ void k_batch_geom_f(const BatchGeomF* __restrict__ items, int nitems, int total) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= total) return;
+    int lo = 0, hi = nitems - 1;                       // last item with node0 <= q
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (items[mid].node0 <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchGeomF& g = items[lo];
+    const int m = q - g.node0;
+    double v[5];
+    curve_point_any(g.gdeg, g.nb, g.knots, g.ctrl, g.w, g.eta[m], v);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) g.geo[(size_t)c * g.Nq + m] = v[c];
+    prep_f_node(m, g.Nq, g.d, g.L, g.geo, g.eta, g.W, g.Bt, g.nodes, g.P, g.Q);
+}
+
+// Persistent assembly of many problems: each CTA takes (problem, tile) units
+// from `units` in order through an atomic counter until none are left.  The
+// unit order and the grid size come from the caller (the batch autotuner).
+template <int TI>
+__global__ void __launch_bounds__(kBatchMaxThreads, 1) k_batch_assemble_f(const BatchItemF* __restrict__ items,
+                                                           const int2* __restrict__ units, int nunits,
+                                                           int* __restrict__ counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_u;
+    for (;;) {
+        if (threadIdx.x == 0) s_u = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_u;
+        if (u >= nunits) return;
+        const int2 w = units[u];
+        const BatchItemF& it = items[w.x];
+        const int I = w.y / it.nt, J = w.y % it.nt;
+        const TileF t = it.t;
+        switch (it.d * 2 + it.closed) {
+            case 4: tile_f<2, false, TI>(t, I, J, smem); break;
+            case 5: tile_f<2, true, TI>(t, I, J, smem); break;
+            case 6: tile_f<3, false, TI>(t, I, J, smem); break;
+            case 7: tile_f<3, true, TI>(t, I, J, smem); break;
+            case 8: tile_f<4, false, TI>(t, I, J, smem); break;
+            case 9: tile_f<4, true, TI>(t, I, J, smem); break;
+            case 10: tile_f<5, false, TI>(t, I, J, smem); break;
+            default: tile_f<5, true, TI>(t, I, J, smem); break;
+        }
+        __syncthreads();
+    }
+}
+
+void batch_geom_f(const BatchGeomF* d_items, int nitems, int total, cudaStream_t s) {
+    k_batch_geom_f<<<(total + 127) / 128, 128, 0, s>>>(d_items, nitems, total);
+    IGS_CUDA(cudaGetLastError());
+}
+
+template <int TI>
+static void* batch_kernel() { return (void*)k_batch_assemble_f<TI>; }
+
+int batch_blocks_per_sm(int TI, int threads, size_t smem) {
+    void* k = TI == 16 ? batch_kernel<16>() : batch_kernel<32>();
+    IGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per = 0;
+    IGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem));
+    return per;
+}
+
+void batch_assemble_f(int TI, const BatchItemF* d_items, const int2* d_units, int nunits, int* d_counter, int grid,
+                      int threads, size_t smem, cudaStream_t s) {
+    if (TI == 16) {
+        IGS_CUDA(cudaFuncSetAttribute(k_batch_assemble_f<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_batch_assemble_f<16><<<grid, threads, smem, s>>>(d_items, d_units, nunits, d_counter);
+    } else {
+        IGS_CUDA(cudaFuncSetAttribute(k_batch_assemble_f<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_batch_assemble_f<32><<<grid, threads, smem, s>>>(d_items, d_units, nunits, d_counter);
+    }
+    IGS_CUDA(cudaGetLastError());
 }
 
 }  // namespace igs

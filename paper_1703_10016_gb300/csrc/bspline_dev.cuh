@@ -97,3 +97,48 @@ __device__ __forceinline__ double piece_eval(const double* __restrict__ piece, i
 }
 
 }  // namespace igs
+
+namespace igs {
+// NURBS point, derivative and speed at parameter s (Sect. 3, eq. J):
+// f = N/W with N = sum w_i Q_i B_i, W = sum w_i B_i; f' = (N' - W' f)/W.
+// out: x, y, x', y', J.
+template <int DEG>
+__device__ __forceinline__ void curve_point(int nb, const double* __restrict__ knots, const double* __restrict__ ctrl,
+                                            const double* __restrict__ w, double s, double* out) {
+    const int span = find_span(knots, nb, DEG, s);
+    double N[DEG + 1], dN[DEG + 1];
+    basis_fixed_d1<DEG>(knots, span, s, N, dN);
+    double nx = 0, ny = 0, W = 0, dnx = 0, dny = 0, dW = 0;
+#pragma unroll
+    for (int r = 0; r <= DEG; ++r) {
+        const int i = span - DEG + r;
+        const double wi = w[i];
+        const double px = ctrl[2 * i], py = ctrl[2 * i + 1];
+        nx += wi * px * N[r]; ny += wi * py * N[r]; W += wi * N[r];
+        dnx += wi * px * dN[r]; dny += wi * py * dN[r]; dW += wi * dN[r];
+    }
+    const double fx = nx / W, fy = ny / W;
+    const double fx1 = (dnx - dW * fx) / W, fy1 = (dny - dW * fy) / W;
+    out[0] = fx;
+    out[1] = fy;
+    out[2] = fx1;
+    out[3] = fy1;
+    out[4] = sqrt(fx1 * fx1 + fy1 * fy1);
+}
+
+// Runtime geometry degree -> compile-time evaluator.
+__device__ __forceinline__ void curve_point_any(int deg, int nb, const double* __restrict__ knots,
+                                                const double* __restrict__ ctrl, const double* __restrict__ w,
+                                                double s, double* out) {
+    switch (deg) {
+        case 1: curve_point<1>(nb, knots, ctrl, w, s, out); break;
+        case 2: curve_point<2>(nb, knots, ctrl, w, s, out); break;
+        case 3: curve_point<3>(nb, knots, ctrl, w, s, out); break;
+        case 4: curve_point<4>(nb, knots, ctrl, w, s, out); break;
+        case 5: curve_point<5>(nb, knots, ctrl, w, s, out); break;
+        case 6: curve_point<6>(nb, knots, ctrl, w, s, out); break;
+        default: curve_point<7>(nb, knots, ctrl, w, s, out); break;
+    }
+}
+}  // namespace igs
+

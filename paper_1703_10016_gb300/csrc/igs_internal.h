@@ -68,7 +68,7 @@ struct igs_ctx_s {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int live_geoms = 0, live_probs = 0;
+    int live_geoms = 0, live_probs = 0, live_batches = 0;
 };
 
 struct igs_geom_s {
@@ -86,6 +86,7 @@ struct igs_prob_s {
     igs::Plan plan;
     int precision = IGS_FP64;
     int rules_ready = 0, geometry_ready = 0, assembled = 0, factored = 0;
+    int live_batches = 0;         // batches that reference this problem
     int64_t bytes = 0;
     igs_timing timing{};
     int launches = 0;
@@ -182,3 +183,84 @@ void rhs_build(igs_prob p, const double* d_uD, int nrhs);
 void rhs_build_noalloc(igs_prob p, const double* d_uD, int nrhs, double* d_beta);
 void solve_system(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double* resid);
 }  // namespace igs
+
+// ------------------------------------------------------------- FP32 assembly
+namespace igs {
+struct NodeF { float xh, xl, yh, yl, eh, el, ebh, ebl, lnJ; };
+
+// One problem's FP32 assembly inputs (device pointers).
+struct TileF {
+    int n, Nq;
+    float invL2;
+    const int* lo;
+    const int* hi;
+    const int* jfirst;
+    const NodeF* nodes;
+    const float* P;
+    const float* Q;
+    WsView<float> ws;
+    float* A;
+    int64_t ld;
+    int maxr;
+};
+
+// Batched form: per-problem tile inputs and geometry/prep inputs.
+struct BatchItemF {
+    TileF t;
+    int d, closed, nt;
+};
+struct BatchGeomF {
+    int gdeg, nb;
+    const double* knots;
+    const double* ctrl;
+    const double* w;
+    const double* eta;
+    int Nq, d;
+    double L;
+    const double* W;
+    const double* Bt;
+    double* geo;
+    NodeF* nodes;
+    float* P;
+    float* Q;
+    int node0;
+};
+
+int max_tile_range(const Plan& P, int TI);
+size_t tile_smem_f(int maxr, int d, int TI);
+TileF tile_args_f(igs_prob p, int maxr);
+void batch_geom_f(const BatchGeomF* d_items, int nitems, int total, cudaStream_t s);
+int batch_blocks_per_sm(int TI, int threads, size_t smem);
+void batch_assemble_f(int TI, const BatchItemF* d_items, const int2* d_units, int nunits, int* d_counter, int grid,
+                      int threads, size_t smem, cudaStream_t s);
+}  // namespace igs
+
+// ------------------------------------------------------- C-ABI entry helpers
+namespace igs {
+void set_error(const std::string& msg);
+void ensure_rules(igs_prob p);
+void ensure_geometry(igs_prob p);
+}  // namespace igs
+
+#define API_BEGIN \
+    try {
+#define API_END                                                               \
+    }                                                                         \
+    catch (const igs::Error& e) {                                             \
+        igs::set_error(e.msg);                                                \
+        return e.code;                                                        \
+    }                                                                         \
+    catch (const std::bad_alloc&) {                                           \
+        igs::set_error("host allocation failed");                             \
+        return IGS_E_NO_MEMORY;                                               \
+    }                                                                         \
+    catch (...) {                                                             \
+        igs::set_error("unexpected error");                                   \
+        return IGS_E_CUDA;                                                    \
+    }                                                                         \
+    return IGS_OK;
+
+#define REQUIRE(cond, code, msg)                      \
+    do {                                              \
+        if (!(cond)) throw igs::Error((code), (msg)); \
+    } while (0)

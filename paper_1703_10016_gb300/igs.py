@@ -34,7 +34,10 @@ EXPORTED = [
     "igs_build_weighted_rules", "igs_assemble", "igs_rhs_points", "igs_build_rhs", "igs_build_rhs_noalloc",
     "igs_solve",
     "igs_get_rules", "igs_get_node_geometry",
+    "igs_get_matrix", "igs_batch_create", "igs_batch_destroy", "igs_batch_assemble", "igs_batch_tune", "igs_batch_set_config",
+    "igs_batch_get_config",
 ]
+IGS_ORDER_NATURAL, IGS_ORDER_INTERLEAVED, IGS_ORDER_LARGEST_FIRST = 0, 1, 2
 
 
 class IgsError(RuntimeError):
@@ -54,6 +57,10 @@ class igs_timing(C.Structure):
     _fields_ = [("rules_ms", C.c_float), ("geometry_ms", C.c_float), ("assemble_ms", C.c_float),
                 ("rhs_ms", C.c_float), ("factor_ms", C.c_float), ("solve_ms", C.c_float),
                 ("ir_iterations", C.c_int32), ("kernel_launches", C.c_int32)]
+
+
+class igs_batch_config(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("order", C.c_int32), ("ctas_per_sm", C.c_int32), ("ms", C.c_float)]
 
 
 def _load() -> C.CDLL:
@@ -80,6 +87,13 @@ def _load() -> C.CDLL:
         "igs_solve": [vp, vp, i32, vp, vp, i32],
         "igs_get_rules": [vp, vp, vp, vp, vp],
         "igs_get_node_geometry": [vp, vp, vp],
+        "igs_get_matrix": [vp, vp, i64, i32, i32],
+        "igs_batch_create": [vp, C.POINTER(vp), C.POINTER(vp), i32],
+        "igs_batch_destroy": [vp],
+        "igs_batch_assemble": [vp, C.POINTER(C.c_float)],
+        "igs_batch_tune": [vp, C.POINTER(igs_batch_config), i32],
+        "igs_batch_set_config": [vp, C.POINTER(igs_batch_config)],
+        "igs_batch_get_config": [vp, C.POINTER(igs_batch_config)],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -188,6 +202,17 @@ def igs_assemble(prob, A_out=None, ld: int | None = None, mem: int | None = None
     _check(_lib.igs_assemble(prob, _ptr(A_out), int(ld), int(mem), int(dtype)), "igs_assemble")
 
 
+def igs_get_matrix(prob, A_out, ld: int | None = None, mem: int | None = None, dtype: int | None = None) -> None:
+    """Copy the assembled A into A_out (host numpy array or torch tensor), n x ld."""
+    if ld is None:
+        ld = A_out.shape[1]
+    if mem is None:
+        mem = IGS_MEM_DEVICE if (hasattr(A_out, "is_cuda") and A_out.is_cuda) else IGS_MEM_HOST
+    if dtype is None:
+        dtype = IGS_F32 if str(A_out.dtype).endswith("float32") else IGS_F64
+    _check(_lib.igs_get_matrix(prob, _ptr(A_out), int(ld), int(mem), int(dtype)), "igs_get_matrix")
+
+
 def igs_rhs_points(prob) -> np.ndarray:
     cnt = C.c_int64()
     _check(_lib.igs_rhs_points(prob, None, 0, C.byref(cnt)), "igs_rhs_points")
@@ -253,3 +278,42 @@ def igs_get_node_geometry(prob):
     J = np.empty(nq)
     _check(_lib.igs_get_node_geometry(prob, _ptr(xy), _ptr(J)), "igs_get_node_geometry")
     return xy, J
+
+
+# ------------------------------------------------------------------ batched form
+def _cfg_dict(c: igs_batch_config) -> dict:
+    return {"tile": c.tile, "order": c.order, "ctas_per_sm": c.ctas_per_sm, "ms": c.ms}
+
+
+def igs_batch_create(ctx, probs) -> C.c_void_p:
+    arr = (C.c_void_p * len(probs))(*[p.value if isinstance(p, C.c_void_p) else p for p in probs])
+    h = C.c_void_p()
+    _check(_lib.igs_batch_create(ctx, C.byref(h), arr, len(probs)), "igs_batch_create")
+    return h
+
+
+def igs_batch_destroy(batch) -> None:
+    _check(_lib.igs_batch_destroy(batch), "igs_batch_destroy")
+
+
+def igs_batch_assemble(batch) -> float:
+    ms = C.c_float()
+    _check(_lib.igs_batch_assemble(batch, C.byref(ms)), "igs_batch_assemble")
+    return ms.value
+
+
+def igs_batch_tune(batch, reps: int = 2) -> dict:
+    c = igs_batch_config()
+    _check(_lib.igs_batch_tune(batch, C.byref(c), int(reps)), "igs_batch_tune")
+    return _cfg_dict(c)
+
+
+def igs_batch_set_config(batch, tile: int = 32, order: int = IGS_ORDER_NATURAL, ctas_per_sm: int = 0) -> None:
+    c = igs_batch_config(int(tile), int(order), int(ctas_per_sm), 0.0)
+    _check(_lib.igs_batch_set_config(batch, C.byref(c)), "igs_batch_set_config")
+
+
+def igs_batch_get_config(batch) -> dict:
+    c = igs_batch_config()
+    _check(_lib.igs_batch_get_config(batch, C.byref(c)), "igs_batch_get_config")
+    return _cfg_dict(c)
