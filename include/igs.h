@@ -257,6 +257,79 @@ int igs_batch_tune(igs_batch batch, igs_batch_config* best_out, int reps);
 int igs_batch_set_config(igs_batch batch, const igs_batch_config* cfg);
 int igs_batch_get_config(igs_batch batch, igs_batch_config* cfg);
 
+/* ------------------------------------------------------------- served form */
+
+/* A request loop around the method: each request is one Dirichlet problem
+ * (a curve, a discretisation and 1..8 data sets) taken through rules,
+ * assembly, right-hand sides and solve (Sects. 3-5).  The paper solves one
+ * problem at a time; the server runs `slots` requests at once, each on its own
+ * CUDA stream and host thread, so their kernels overlap on the device.  A
+ * queued request is admitted, in arrival order, as soon as a slot is free and
+ * its device-memory estimate fits in what the admitted requests leave of
+ * `mem_budget`; a request that could never fit is refused at submission.
+ * Each request's result does not depend on what runs beside it.
+ *
+ * igs_data_fn: called once per request on a server thread with the request's
+ *   right-hand-side points xy[count*2] (HOST, FP64, as igs_rhs_points); fills
+ *   uD[k*count + q] for the nrhs data sets and returns 0 (nonzero fails the
+ *   request with INVALID_ARG).
+ * igs_server_create: device, opts (slots 1..64, mem_budget > 0 bytes).
+ *   Errors: INVALID_ARG, CUDA.
+ * igs_server_submit: copies the request (curve arrays included) and returns a
+ *   ticket at once.  Errors: INVALID_ARG (malformed), ADMISSION_REFUSED (its
+ *   estimate exceeds mem_budget).
+ * igs_server_wait: blocks until the request is done or failed, or until
+ *   timeout_ms (< 0: no limit) has passed (TIMEOUT); st (may be NULL) gets the
+ *   stats.  Errors: INVALID_ARG (unknown ticket), TIMEOUT.
+ * igs_server_result: for a finished request, copies alpha[nrhs*n] (HOST, data
+ *   set k at alpha[k*n]) and resid[nrhs] (either may be NULL) and forgets the
+ *   ticket; a failed request returns its error code (and is forgotten).
+ *   Errors: INVALID_ARG, STATE (not finished).
+ * igs_server_drain: waits until every submitted request has finished
+ *   (TIMEOUT after timeout_ms >= 0).
+ * igs_server_destroy: drains, stops the threads, frees everything. */
+typedef struct igs_server_s* igs_server;
+typedef int (*igs_data_fn)(void* user, const double* xy, int64_t count, int nrhs, double* uD);
+typedef struct igs_request {
+    int32_t geom_degree;        /* curve, as igs_create_geometry */
+    int32_t n_knots;
+    const double* knots;
+    int32_t n_ctrl;
+    const double* ctrl_xy;
+    const double* weights;      /* NULL: B-spline */
+    int32_t closed;
+    int32_t degree;             /* discretisation, as igs_create_problem */
+    int32_t n_elems;
+    int32_t n_ref;
+    int32_t precision;
+    int32_t nrhs;               /* 1..8 */
+    igs_data_fn data;
+    void* user;
+} igs_request;
+typedef struct igs_server_opts {
+    int32_t slots;
+    int64_t mem_budget;
+} igs_server_opts;
+#define IGS_REQ_QUEUED  0
+#define IGS_REQ_RUNNING 1
+#define IGS_REQ_DONE    2
+#define IGS_REQ_FAILED  3
+typedef struct igs_request_stats {
+    int32_t status;             /* IGS_REQ_* */
+    int32_t error;              /* IGS_E_* of a failed request */
+    int32_t n, nrhs, ir_iterations, slot;
+    int64_t device_bytes;       /* admission estimate */
+    double queue_ms;            /* submission -> admission */
+    double run_ms;              /* admission -> done */
+    double latency_ms;          /* submission -> done */
+} igs_request_stats;
+int igs_server_create(int device, const igs_server_opts* opts, igs_server* out);
+int igs_server_submit(igs_server server, const igs_request* req, int64_t* ticket);
+int igs_server_wait(igs_server server, int64_t ticket, int32_t timeout_ms, igs_request_stats* st);
+int igs_server_result(igs_server server, int64_t ticket, double* alpha, double* resid, igs_request_stats* st);
+int igs_server_drain(igs_server server, int32_t timeout_ms);
+int igs_server_destroy(igs_server server);
+
 /* Diagnostic download of the rules for parity checks (HOST outputs, FP64):
  *   eta[n_quad]; W_band[n_quad * (degree+1)]: W_band[m*(d+1)+r] = w^(i)_m for
  *   the test function i = (first(m) + r) mod n containing eta_m (0 if none),

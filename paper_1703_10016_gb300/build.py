@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libigs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "plan.cpp", "rules.cu", "geometry.cu", "assemble.cu", "rhs.cu", "solve.cu", "batch.cu"]
+SOURCES = ["api.cu", "plan.cpp", "rules.cu", "geometry.cu", "assemble.cu", "rhs.cu", "solve.cu", "batch.cu", "server.cu"]
 
 
 def _nvcc() -> str:
@@ -63,7 +63,7 @@ def build_library(verbose: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(nvcc, s, verbose), srcs))
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
         return LIB
-    cmd = [nvcc, *ARCH, "-shared", "-cudart=shared", "-o", LIB, *objs,
+    cmd = [nvcc, *ARCH, "-shared", "-cudart=shared", "-o", LIB, *objs, "-lpthread",
            "-Xlinker", "-rpath", "-Xlinker", "/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

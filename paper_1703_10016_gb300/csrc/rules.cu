@@ -1,5 +1,7 @@
 // Weighted quadrature rules on the device (FP64): Sect. 4, Algorithms 1 and 2.
 #include <cmath>
+#include <mutex>
+#include <set>
 
 #include "bspline_dev.cuh"
 #include "igs_internal.h"
@@ -533,8 +535,13 @@ static int ws_boundary_columns(int d) { return 24 * (d + 1) + 16; }
 
 // ------------------------------------------------------------------ driver
 static void upload_gauss() {
-    static bool done = false;
-    if (done) return;
+    // once per device; concurrent first calls (serving threads) are serialised
+    static std::mutex mu;
+    static std::set<int> done;
+    int dev = 0;
+    IGS_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(dev)) return;
     double gx[6][6] = {}, gw[6][6] = {};
     for (int g = 1; g <= 6; ++g) {
         // Golub-Welsch free: Newton on Legendre polynomials
@@ -559,7 +566,7 @@ static void upload_gauss() {
     }
     IGS_CUDA(cudaMemcpyToSymbol(c_gauss_x, gx, sizeof(gx)));
     IGS_CUDA(cudaMemcpyToSymbol(c_gauss_w, gw, sizeof(gw)));
-    done = true;
+    done.insert(dev);
 }
 
 void rules_build(igs_prob p) {

@@ -36,7 +36,10 @@ EXPORTED = [
     "igs_get_rules", "igs_get_node_geometry",
     "igs_get_matrix", "igs_batch_create", "igs_batch_destroy", "igs_batch_assemble", "igs_batch_tune", "igs_batch_set_config",
     "igs_batch_get_config",
+    "igs_server_create", "igs_server_submit", "igs_server_wait", "igs_server_result", "igs_server_drain",
+    "igs_server_destroy",
 ]
+IGS_REQ_QUEUED, IGS_REQ_RUNNING, IGS_REQ_DONE, IGS_REQ_FAILED = 0, 1, 2, 3
 IGS_ORDER_NATURAL, IGS_ORDER_INTERLEAVED, IGS_ORDER_LARGEST_FIRST = 0, 1, 2
 
 
@@ -61,6 +64,26 @@ class igs_timing(C.Structure):
 
 class igs_batch_config(C.Structure):
     _fields_ = [("tile", C.c_int32), ("order", C.c_int32), ("ctas_per_sm", C.c_int32), ("ms", C.c_float)]
+
+
+DATA_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_int64, C.c_int, C.POINTER(C.c_double))
+
+
+class igs_request(C.Structure):
+    _fields_ = [("geom_degree", C.c_int32), ("n_knots", C.c_int32), ("knots", C.c_void_p), ("n_ctrl", C.c_int32),
+                ("ctrl_xy", C.c_void_p), ("weights", C.c_void_p), ("closed", C.c_int32), ("degree", C.c_int32),
+                ("n_elems", C.c_int32), ("n_ref", C.c_int32), ("precision", C.c_int32), ("nrhs", C.c_int32),
+                ("data", DATA_FN), ("user", C.c_void_p)]
+
+
+class igs_server_opts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("mem_budget", C.c_int64)]
+
+
+class igs_request_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("error", C.c_int32), ("n", C.c_int32), ("nrhs", C.c_int32),
+                ("ir_iterations", C.c_int32), ("slot", C.c_int32), ("device_bytes", C.c_int64),
+                ("queue_ms", C.c_double), ("run_ms", C.c_double), ("latency_ms", C.c_double)]
 
 
 def _load() -> C.CDLL:
@@ -94,6 +117,12 @@ def _load() -> C.CDLL:
         "igs_batch_tune": [vp, C.POINTER(igs_batch_config), i32],
         "igs_batch_set_config": [vp, C.POINTER(igs_batch_config)],
         "igs_batch_get_config": [vp, C.POINTER(igs_batch_config)],
+        "igs_server_create": [i32, C.POINTER(igs_server_opts), C.POINTER(vp)],
+        "igs_server_submit": [vp, C.POINTER(igs_request), C.POINTER(i64)],
+        "igs_server_wait": [vp, i64, i32, C.POINTER(igs_request_stats)],
+        "igs_server_result": [vp, i64, vp, vp, C.POINTER(igs_request_stats)],
+        "igs_server_drain": [vp, i32],
+        "igs_server_destroy": [vp],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -317,3 +346,72 @@ def igs_batch_get_config(batch) -> dict:
     c = igs_batch_config()
     _check(_lib.igs_batch_get_config(batch, C.byref(c)), "igs_batch_get_config")
     return _cfg_dict(c)
+
+
+# ------------------------------------------------------------------ served form
+_callbacks: dict = {}     # (server, ticket) -> (callback, request) kept alive until the result is taken
+
+
+def _stats_dict(st: igs_request_stats) -> dict:
+    return {k: getattr(st, k) for k, _ in igs_request_stats._fields_}
+
+
+def igs_server_create(device: int = 0, slots: int = 4, mem_budget: int = 180 * 10**9) -> C.c_void_p:
+    h = C.c_void_p()
+    opts = igs_server_opts(int(slots), int(mem_budget))
+    _check(_lib.igs_server_create(int(device), C.byref(opts), C.byref(h)), "igs_server_create")
+    return h
+
+
+def igs_server_submit(server, curve, degree: int, n_elems: int, n_ref: int, precision: int, nrhs: int, data) -> int:
+    """data(xy, nrhs) -> array (nrhs, len(xy)): Dirichlet data at the request's
+    right-hand-side points (called on a server thread)."""
+    knots, ctrl = _f64(curve.knots), _f64(curve.ctrl)
+    w = None if curve.weights is None else _f64(curve.weights)
+
+    def cb(_user, xy_p, count, k, out_p):
+        try:
+            xy = np.ctypeslib.as_array(xy_p, shape=(int(count), 2))
+            out = np.ctypeslib.as_array(out_p, shape=(int(k), int(count)))
+            out[:, :] = np.asarray(data(xy.copy(), int(k)), dtype=np.float64).reshape(int(k), int(count))
+            return 0
+        except Exception:                                   # noqa: BLE001 - reported as a failed request
+            return 1
+
+    fn = DATA_FN(cb)
+    req = igs_request(int(curve.degree), len(knots), knots.ctypes.data, len(ctrl), ctrl.ctypes.data,
+                      None if w is None else w.ctypes.data, int(curve.closed), int(degree), int(n_elems),
+                      int(n_ref), int(precision), int(nrhs), fn, None)
+    t = C.c_int64()
+    _check(_lib.igs_server_submit(server, C.byref(req), C.byref(t)), "igs_server_submit")
+    _callbacks[(server.value, t.value)] = (fn, req, knots, ctrl, w)
+    return t.value
+
+
+def igs_server_wait(server, ticket: int, timeout_ms: int = -1) -> dict:
+    st = igs_request_stats()
+    _check(_lib.igs_server_wait(server, int(ticket), int(timeout_ms), C.byref(st)), "igs_server_wait")
+    return _stats_dict(st)
+
+
+def igs_server_result(server, ticket: int, n: int, nrhs: int):
+    """Returns (alpha (nrhs, n), resid (nrhs,), stats)."""
+    alpha = np.empty((nrhs, n), dtype=np.float64)
+    resid = np.empty(nrhs, dtype=np.float64)
+    st = igs_request_stats()
+    try:
+        _check(_lib.igs_server_result(server, int(ticket), _ptr(alpha), _ptr(resid), C.byref(st)), "igs_server_result")
+    finally:
+        if st.status in (IGS_REQ_DONE, IGS_REQ_FAILED):
+            _callbacks.pop((server.value, int(ticket)), None)
+    return alpha, resid, _stats_dict(st)
+
+
+def igs_server_drain(server, timeout_ms: int = -1) -> None:
+    _check(_lib.igs_server_drain(server, int(timeout_ms)), "igs_server_drain")
+
+
+def igs_server_destroy(server) -> None:
+    _check(_lib.igs_server_destroy(server), "igs_server_destroy")
+    for key in [k for k in _callbacks if k[0] == server.value]:
+        _callbacks.pop(key, None)
