@@ -44,8 +44,13 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["star2048", "batch"], default="star2048",
-                    help="star2048: one request per step (default); batch: 1024 uneven assemblies per step")
+    ap.add_argument("--workload", choices=["star2048", "batch", "serve"], default="star2048",
+                    help="star2048: one request per step (default); batch: 1024 uneven assemblies per step; "
+                         "serve: Poisson arrivals through the request server")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=0.5)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=180.0)
     ap.add_argument("--batch-count", type=int, default=1024)
     ap.add_argument("--fp64-sample", type=int, default=64)
     return ap.parse_args()
@@ -401,6 +406,113 @@ def run_batch(args, rank, world, local_rank):
     return out
 
 
+# --------------------------------------------------------------------------- served form
+def _serve_data(xy, k):
+    import numpy as np
+    src = [2.5 * np.array([np.cos(2 * np.pi * j / 8), np.sin(2 * np.pi * j / 8)]) for j in range(k)]
+    return np.stack([np.log(np.hypot(xy[:, 0] - s[0], xy[:, 1] - s[1])) for s in src])
+
+
+def run_serve(args, rank, world, local_rank):
+    """Served workload: Poisson arrivals (seed 5) of assemble+solve requests, random
+    stars, n log-uniform in [128, 16384], p in {2, 3, 4}, 1..8 data sets each,
+    through the request server (memory admission), against a serial FP64 loop."""
+    import numpy as np
+    import torch
+    from paper_1703_10016_gb300 import igs
+    from paper_1703_10016_gb300 import workloads as wl
+    torch.cuda.set_device(local_rank)
+    arrivals = wl.serve_arrivals(args.serve_rate, args.serve_seconds, seed=5)
+    srv = igs.igs_server_create(local_rank, slots=args.serve_slots, mem_budget=int(args.serve_budget_gb * 1e9))
+    # warm-up: a few small requests (module loading, first graph builds)
+    warm = [igs.igs_server_submit(srv, wl.star_curve(), 3, 128, 2, igs.IGS_MIXED, 1, _serve_data)
+            for _ in range(max(1, args.warmup))]
+    igs.igs_server_drain(srv)
+    for t in warm:
+        st = igs.igs_server_wait(srv, t)
+        igs.igs_server_result(srv, t, st["n"], 1)
+    clk = ClockSampler(local_rank)
+    clk.start()
+    t0 = time.perf_counter()
+    tickets = []
+    for (ta, pr, nrhs) in arrivals:
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append((igs.igs_server_submit(srv, pr.curve, pr.degree, pr.n_elems, pr.n_ref, igs.IGS_MIXED, nrhs,
+                                              _serve_data), pr, nrhs))
+    igs.igs_server_drain(srv)
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    lat, queue, run, fails, entries, solves, bytes_max = [], [], [], 0, 0, 0, 0
+    fail_kinds = {}
+    for t, pr, nrhs in tickets:
+        st = igs.igs_server_wait(srv, t)
+        if st["status"] != igs.IGS_REQ_DONE:
+            fails += 1
+            try:
+                igs.igs_server_result(srv, t, max(st["n"], 1), nrhs)
+            except igs.IgsError as e:
+                key = f"{e.code}: {str(e).split(': ', 1)[-1][:120]} (n={pr.n_elems}, p={pr.degree})"
+                fail_kinds[key] = fail_kinds.get(key, 0) + 1
+            continue
+        _, res, st = igs.igs_server_result(srv, t, st["n"], nrhs)
+        lat.append(st["latency_ms"])
+        queue.append(st["queue_ms"])
+        run.append(st["run_ms"])
+        entries += st["n"] ** 2
+        solves += 1
+        bytes_max = max(bytes_max, st["device_bytes"])
+    igs.igs_server_destroy(srv)
+    lat_s = sorted(lat)
+    pct = lambda q: lat_s[min(len(lat_s) - 1, int(math.ceil(q * len(lat_s))) - 1)] if lat_s else None
+    # serial FP64 loop on a seeded sample of the same requests (direct API, one at a time)
+    rng = np.random.default_rng(9)
+    sample = sorted(rng.choice(len(arrivals), size=min(8, len(arrivals)), replace=False).tolist())
+    ctx = igs.igs_create(local_rank)
+    fp_ms, fp_entries = 0.0, 0
+    for k in sample:
+        _, pr, nrhs = arrivals[k]
+        c = pr.curve
+        g = igs.igs_create_geometry(ctx, c.degree, c.knots, c.ctrl, c.weights, c.closed)
+        p = igs.igs_create_problem(g, pr.degree, pr.n_elems, pr.n_ref, igs.IGS_FP64)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        igs.igs_build_weighted_rules(p)
+        igs.igs_assemble(p)
+        xy = igs.igs_rhs_points(p)
+        igs.igs_build_rhs(p, _serve_data(xy, nrhs))
+        igs.igs_solve(p, nrhs=nrhs)
+        fp_ms += 1e3 * (time.perf_counter() - ts)
+        fp_entries += pr.n_elems ** 2
+        igs.igs_destroy_problem(p)
+        igs.igs_destroy_geometry(g)
+    igs.igs_destroy(ctx)
+    fp_rate = len(sample) / (fp_ms * 1e-3)
+    return {
+        "metric": "solves/s (served assemble+solve requests, MIXED tier, <=1e-6 rel. error)",
+        "value": world * solves / wall, "unit": "solves/s", "n_gpus": world, "steps": len(tickets),
+        "warmup": len(warm), "ms_per_step": 1e3 * wall / max(len(tickets), 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s (seed 5): random "
+                               "stars, n log-uniform [128,16384], p in {2,3,4}, N_ref=2, 1..8 data sets",
+                   "slots": args.serve_slots, "mem_budget_gb": args.serve_budget_gb,
+                   "parallelism": f"replicas x{world}"},
+        "requests": len(tickets), "completed": solves, "failed": fails, "failures": dict(list(fail_kinds.items())[:8]),
+        "wall_s": wall,
+        "offered_rate": args.serve_rate, "achieved_rate": solves / wall,
+        "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "mean": statistics.mean(lat) if lat else None},
+        "queue_ms": {"p50": statistics.median(queue) if queue else None, "max": max(queue) if queue else None},
+        "run_ms": {"p50": statistics.median(run) if run else None, "max": max(run) if run else None},
+        "entries_per_s": entries / wall, "max_request_bytes": bytes_max,
+        "serial_fp64_loop": {"value": fp_rate, "unit": "solves/s", "sample": len(sample), "ms": fp_ms,
+                             "entries_per_s": fp_entries / (fp_ms * 1e-3)},
+        "speedup_vs_serial_fp64": (solves / wall) / fp_rate,
+        "gpu_launches": None,
+        "clocks": clocks,
+    }
+
+
 def cpu_baseline(n, d, nref, rows=(0, 511, 1024, 2047)):
     """The oracle (plain FP64 numpy, single thread) on a bounded sample: full
     rows of A at the benchmark size."""
@@ -454,7 +566,8 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
-    out = run_batch(args, rank, world, local_rank) if args.workload == "batch" else run_ours(args, rank, world, local_rank)
+    run = {"batch": run_batch, "serve": run_serve}.get(args.workload, run_ours)
+    out = run(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -1,3 +1,4 @@
+#include <map>
 // C ABI entry points (include/igs.h): handles, validation, allocation, copies.
 #include <algorithm>
 #include <cmath>
@@ -12,6 +13,18 @@ namespace igs {
 static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+void ensure_dyn_smem(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;   // per device and kernel
+    int dev = 0;
+    IGS_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = limit[{dev, func}];
+    if (bytes <= cur) return;
+    IGS_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+}
 
 std::string cuda_msg(cudaError_t e, const char* what, const char* file, int line) {
     return std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" + std::to_string(line) + ")";

@@ -353,7 +353,7 @@ static void launch_tile_f(igs_prob p, int maxr, cudaStream_t s) {
     const Plan& P = p->plan;
     const size_t sm = tile_smem_f(maxr, D, kTile);
     auto kern = k_assemble_f<D, CLOSED>;
-    IGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ensure_dyn_smem((const void*)kern, (size_t)sm);
     const int nt = (P.n + kTile - 1) / kTile;
     const int threads = std::min(1024, (maxr + 31) / 32 * 32);
     kern<<<dim3(nt, nt), threads, sm, s>>>(tile_args_f(p, maxr));
@@ -378,7 +378,7 @@ static void launch_tile(igs_prob p, int maxr, cudaStream_t s) {
     const Plan& P = p->plan;
     const size_t sm = tile_smem<T>(maxr, D);
     auto kern = k_assemble_tile<T, D>;
-    IGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ensure_dyn_smem((const void*)kern, (size_t)sm);
     const int nt = (P.n + kTile - 1) / kTile;
     dim3 grid(nt, nt);
     const bool f32 = std::is_same<T, float>::value;
@@ -519,7 +519,7 @@ static void* batch_kernel() { return (void*)k_batch_assemble_f<TI>; }
 
 int batch_blocks_per_sm(int TI, int threads, size_t smem) {
     void* k = TI == 16 ? batch_kernel<16>() : batch_kernel<32>();
-    IGS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_dyn_smem((const void*)k, (size_t)smem);
     int per = 0;
     IGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem));
     return per;
@@ -528,10 +528,10 @@ int batch_blocks_per_sm(int TI, int threads, size_t smem) {
 void batch_assemble_f(int TI, const BatchItemF* d_items, const int2* d_units, int nunits, int* d_counter, int grid,
                       int threads, size_t smem, cudaStream_t s) {
     if (TI == 16) {
-        IGS_CUDA(cudaFuncSetAttribute(k_batch_assemble_f<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ensure_dyn_smem((const void*)k_batch_assemble_f<16>, (size_t)smem);
         k_batch_assemble_f<16><<<grid, threads, smem, s>>>(d_items, d_units, nunits, d_counter);
     } else {
-        IGS_CUDA(cudaFuncSetAttribute(k_batch_assemble_f<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ensure_dyn_smem((const void*)k_batch_assemble_f<32>, (size_t)smem);
         k_batch_assemble_f<32><<<grid, threads, smem, s>>>(d_items, d_units, nunits, d_counter);
     }
     IGS_CUDA(cudaGetLastError());

@@ -237,6 +237,10 @@ void batch_assemble_f(int TI, const BatchItemF* d_items, const int2* d_units, in
 
 // ------------------------------------------------------- C-ABI entry helpers
 namespace igs {
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`; the limit
+// only grows, under a lock, so that concurrent callers needing different
+// amounts never lower it between another caller's setting and its launch.
+void ensure_dyn_smem(const void* func, size_t bytes);
 void set_error(const std::string& msg);
 void ensure_rules(igs_prob p);
 void ensure_geometry(igs_prob p);

@@ -668,7 +668,7 @@ void rules_build(igs_prob p) {
         ++launches;
         double* d_Wc = (double*)dev_alloc(p, sizeof(double) * (size_t)ncols * Nq);
         const size_t ysm = sizeof(double) * (size_t)cap * D1;
-        IGS_CUDA(cudaFuncSetAttribute(k_wcols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm));
+        ensure_dyn_smem((const void*)k_wcols, (size_t)ysm);
         k_wcols<<<dim3((Nq + 255) / 256, ncols), 256, ysm, s>>>(Nq, d, den, dmin, cap, p->d_pos, d_Et, d_er, d_Yc,
                                                                d_Wc);
         ++launches;

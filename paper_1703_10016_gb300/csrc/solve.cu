@@ -46,10 +46,11 @@ template <> __device__ __forceinline__ double vget<double>(const double2& v, int
 // block and stores L11; CTA b >= 1 factors the tall block made of the
 // diagonal block and rows k0 + 64 b .. + 63 below it (the diagonal part
 // redundantly, so that no CTA waits for another), which turns its rows into
-// L21 = A21 L11^{-T}.  Right-looking by 8-column blocks, two barriers per
-// block: (1) each row's thread factors the 8 x 8 diagonal sub-block itself
-// (every thread the same, in registers: no communication) and solves its own
-// row against it; (2) rank-8 update of the columns to the right.
+// L21 = A21 L11^{-T}.  Right-looking by 8-column blocks, three barriers per
+// block: (1) each row's thread reads the 8 x 8 diagonal sub-block and its row,
+// then factors the sub-block itself (every thread the same, in registers: no
+// communication) and solves its own row against it; (2) rank-8 update of the
+// columns to the right.
 // A non-positive pivot sets *flag and is replaced by 1.
 constexpr int kPanelThreads = 512;
 constexpr int kPanelRows = 2 * kNB;                        // diagonal block + 64 rows below
@@ -94,16 +95,22 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel(int n, T* __restrict__ 
     const int i = tid % kPanelRows, part = tid / kPanelRows;
 #pragma unroll 1
     for (int c0 = 0; c0 < kNB; c0 += kPB) {
-        // (1) rows i >= c0: L of the 8 x 8 diagonal sub-block, then this row's 8 entries
-        if (part == 0 && i >= c0 && i < rows) {
-            T d[kPB][kPB];
+        // (1) rows i >= c0: L of the 8 x 8 diagonal sub-block, then this row's 8 entries.
+        // Every participating thread reads the sub-block before any of them writes
+        // its row back (the rows of the sub-block are among the rows written).
+        const bool act = part == 0 && i >= c0 && i < rows;
+        T d[kPB][kPB];
+        T x[kPB];
+        if (act) {
 #pragma unroll
             for (int u = 0; u < kPB; ++u)
 #pragma unroll
                 for (int w = 0; w < kPB; ++w) d[u][w] = (w <= u) ? a[c0 + u][c0 + w] : (T)0;
-            T x[kPB];
 #pragma unroll
             for (int w = 0; w < kPB; ++w) x[w] = a[i][c0 + w];
+        }
+        __syncthreads();
+        if (act) {
 #pragma unroll
             for (int w = 0; w < kPB; ++w) {
                 T pv = d[w][w];
@@ -676,8 +683,8 @@ static int factor_launches(int n) {
 template <typename T>
 static void factor(igs_prob p, cudaStream_t s) {
     const int n = p->plan.n;
-    IGS_CUDA(cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem<T>()));
-    IGS_CUDA(cudaFuncSetAttribute(k_syrk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syrk_smem<T>()));
+    ensure_dyn_smem((const void*)k_panel<T>, (size_t)panel_smem<T>());
+    ensure_dyn_smem((const void*)k_syrk<T>, (size_t)syrk_smem<T>());
     if (!p->factor_exec) {
         // capture the fixed launch sequence once, on two private streams
         cudaStream_t cs = nullptr, cs1 = nullptr;
