@@ -30,6 +30,9 @@ SM_COUNT = 152
 FP32_LANES = 128          # FP32 FMA lanes per SM
 SM_MAX_MHZ = 2070.0
 FP64_NOMINAL_TFLOPS = 1.25
+# DRAM read + write of one launch of the FP32 assembly kernel on this workload (ncu
+# capture summarised in profiles/ncu_assemble_f_star2048.md); None after the kernel changes
+ASSEMBLY_TRAFFIC_BYTES = 8.42e6
 
 
 def parse():
@@ -251,7 +254,8 @@ def run_ours(args, rank, world, local_rank):
                  "steps": fp["steps"]},
         "speedup_mixed_vs_fp64": fp_step / step_ms,
         "roofline": {"kernel": f"k_assemble_f<{d},{'true' if curve.closed else 'false'}>", "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": ASSEMBLY_TRAFFIC_BYTES if (n, d, nref) == (2048, 3, 2) else None,
                      "work": f"{flops_per_pair} flop per node pair x n_quad^2 + stage-2 contraction",
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "gpu_launches": int(sum(mixed["launches"])),

@@ -337,21 +337,48 @@ __global__ void __launch_bounds__(128) k_mu_tab(int NE, int M, int d, int den, i
     Z[(size_t)j * ldz + col] = mu;
 }
 
-// z = G^{-1} mu in place, one thread per column (node).
+// z = G^{-1} mu in place, one thread per column (node).  The last d values of
+// each substitution stay in a register window, so the only memory traffic on
+// the dependency chain is the streamed factor row and one store per step.
+template <int D>
+__device__ void gsolve_col(int NE, const double* __restrict__ L, double* __restrict__ Z, int ldz, int c) {
+    double win[D + 1];
+#pragma unroll
+    for (int r = 0; r <= D; ++r) win[r] = 0.0;             // win[r] = z[j - r] after step j
+    for (int j = 0; j < NE; ++j) {
+        double s = Z[(size_t)j * ldz + c];
+#pragma unroll
+        for (int r = 1; r <= D; ++r)
+            if (j - r >= 0) s -= L[j * (D + 1) + r] * win[r - 1];
+        const double v = s / L[j * (D + 1)];
+#pragma unroll
+        for (int r = D; r > 0; --r) win[r] = win[r - 1];
+        win[0] = v;
+        Z[(size_t)j * ldz + c] = v;
+    }
+#pragma unroll
+    for (int r = 0; r <= D; ++r) win[r] = 0.0;             // win[r] = y[j + r] after step j
+    for (int j = NE - 1; j >= 0; --j) {
+        double s = Z[(size_t)j * ldz + c];
+#pragma unroll
+        for (int r = 1; r <= D; ++r)
+            if (j + r < NE) s -= L[(j + r) * (D + 1) + r] * win[r - 1];
+        const double v = s / L[j * (D + 1)];
+#pragma unroll
+        for (int r = D; r > 0; --r) win[r] = win[r - 1];
+        win[0] = v;
+        Z[(size_t)j * ldz + c] = v;
+    }
+}
+
 __global__ void k_gsolve(int NE, int d, int ncol, const double* __restrict__ L, double* __restrict__ Z, int ldz) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncol) return;
-    for (int j = 0; j < NE; ++j) {
-        double s = Z[(size_t)j * ldz + c];
-        const int p0 = (j - d > 0) ? j - d : 0;
-        for (int p = p0; p < j; ++p) s -= L[j * (d + 1) + (j - p)] * Z[(size_t)p * ldz + c];
-        Z[(size_t)j * ldz + c] = s / L[j * (d + 1)];
-    }
-    for (int j = NE - 1; j >= 0; --j) {
-        double s = Z[(size_t)j * ldz + c];
-        const int p1 = (j + d < NE - 1) ? j + d : NE - 1;
-        for (int p = j + 1; p <= p1; ++p) s -= L[p * (d + 1) + (p - j)] * Z[(size_t)p * ldz + c];
-        Z[(size_t)j * ldz + c] = s / L[j * (d + 1)];
+    switch (d) {
+        case 2: gsolve_col<2>(NE, L, Z, ldz, c); break;
+        case 3: gsolve_col<3>(NE, L, Z, ldz, c); break;
+        case 4: gsolve_col<4>(NE, L, Z, ldz, c); break;
+        default: gsolve_col<5>(NE, L, Z, ldz, c); break;
     }
 }
 

@@ -99,3 +99,29 @@ def test_memory_admission_and_failures():
         assert e.value.code == g.IGS_E_INVALID_ARG
     finally:
         g.igs_server_destroy(s)
+
+
+def test_many_mid_size_requests_on_eight_slots():
+    """Heavier overlap (16 requests, n 500..2500, 8 slots): every factorisation
+    and solve must still equal its solo result (this load exposed a shared-
+    memory race in the Cholesky panel that a lone problem never hit)."""
+    g = lib()
+    rng = np.random.default_rng(23)
+    reqs = []
+    for _ in range(16):
+        n = int(rng.integers(500, 2500))
+        d = int(rng.integers(2, 5))
+        reqs.append((wl.random_star(rng), d, n, 2, g.IGS_MIXED, int(rng.integers(1, 5))))
+    s = g.igs_server_create(0, slots=8, mem_budget=64 * 10**9)
+    try:
+        tickets = [g.igs_server_submit(s, c, d, n, r, p, k, _data) for c, d, n, r, p, k in reqs]
+        g.igs_server_drain(s, 600_000)
+        for t, (c, d, n, r, p, k) in zip(tickets, reqs):
+            st = g.igs_server_wait(s, t)
+            assert st["status"] == g.IGS_REQ_DONE, st
+            alpha, res, st = g.igs_server_result(s, t, st["n"], k)
+            assert np.all(res <= 1e-10)
+            ref, _ = _solo(g, c, d, n, r, p, k)
+            assert np.max(np.abs(alpha - ref)) <= 1e-8 * np.max(np.abs(ref))
+    finally:
+        g.igs_server_destroy(s)
