@@ -8,7 +8,8 @@
 //            of the panel, which yields L21 = A21 L11^{-T} for that slice;
 //   k_syrk   trailing update of the lower triangle, 64 x 64 tiles; the tile
 //            column that holds the next panel goes first, the rest runs on a
-//            second captured stream beside the next panel (look-ahead).
+//            second captured stream beside the next panel (look-ahead); in the
+//            MIXED tier that rest runs on the tensor cores (k_syrk_tc).
 // FP64 tier: all in FP64, then one substitution pair.  MIXED tier: the same in
 // FP32, then iterative refinement with FP64 residuals r = beta - A_s alpha until
 // ||r|| <= 1e-10 ||beta||.  The triangular solves go by 64-row blocks in solve
@@ -627,6 +628,186 @@ template <typename T>
 static size_t syrk_smem() { return 2 * kST * syrk_ld<T>() * sizeof(T); }
 
 // Issue the whole factorisation on stream s (used under stream capture).
+// Trailing update on the 5th-generation tensor cores (MIXED tier).  Tile of
+// 128 rows x 64 columns, K = 64 (the panel): D = sum_l F[i][k0+l] F[j][k0+l]
+// accumulated in tensor memory by tcgen05.mma kind::tf32 in a 3-term split
+// (x = hi + lo with hi = x rounded to TF32: hi.hi + hi.lo + lo.hi; the lo.lo term
+// is below FP32 rounding), so the update keeps FP32-level accuracy.  Operands
+// are staged in shared memory in the canonical K-major layout without swizzle
+// (core matrices of 8 rows x 16 bytes; LBO = stride between core matrices
+// along K, SBO = along M/N).  One thread issues the 24 MMAs and commits them to
+// an mbarrier; every thread waits on it with a bounded number of polls (a miss
+// sets bit 2 of *flag and skips the epilogue), then each warp reads its 32
+// rows of the accumulator with tcgen05.ld and applies C -= D to the lower
+// triangle.  Tiles align with the 64-wide panels, so `mode` splits the update
+// as k_syrk does: 1 = the next panel's column block, 2 = the rest.
+namespace tc {
+constexpr uint32_t kM = 128, kN = 64, kK = 64;
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// D F32, A and B TF32, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc() { return (1u << 4) | (2u << 7) | (2u << 10) | ((kN >> 3) << 17) | ((kM >> 4) << 24); }
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d), "l"(a), "l"(b), "r"(idesc()), "r"(accumulate));
+}
+__device__ __forceinline__ float tf32_hi(float x) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    return __uint_as_float(h);
+}
+constexpr size_t smem_bytes() { return (size_t)(2 * kM * kK + 2 * kN * kK) * 4 + 64; }
+}  // namespace tc
+
+__global__ void __launch_bounds__(256) k_syrk_tc(int n, float* __restrict__ F, int k0, int kb, int mode,
+                                                 int* __restrict__ flag) {
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int base = k0 + kb;
+    const int ti = blockIdx.y, tj = (mode == 1) ? 0 : blockIdx.x + 1;
+    const int i0 = base + ti * (int)kM, j0 = base + tj * (int)kN;
+    if (j0 > i0 + (int)kM - 1 || j0 >= n) return;              // no lower-triangle entry in this tile
+    float* Ahi = (float*)smem_raw;
+    float* Alo = Ahi + kM * kK;
+    float* Bhi = Alo + kM * kK;
+    float* Blo = Bhi + kN * kK;
+    uint64_t* mbar = (uint64_t*)(Blo + kN * kK);
+    uint32_t* s_taddr = (uint32_t*)(mbar + 1);
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(su32(s_taddr)), "r"(kN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // Staging: element (r, l) at float offset (((r/8)*(kK/4) + l/4)*8 + r%8)*4 + l%4.  A warp
+    // covers 8 rows x 16 columns (512 contiguous bytes of shared memory).  Every thread
+    // issues all its loads (8 float4 of A, 4 of B) before splitting and storing any.
+    constexpr int kPA = (int)(kM * kK / 4) / 256, kPB = (int)(kN * kK / 4) / 256;
+    float4 v[kPA + kPB];
+#pragma unroll
+    for (int q = 0; q < kPA + kPB; ++q) {
+        const bool isA = q < kPA;
+        const int idx = tid + (isA ? q : q - kPA) * 256;
+        const int rr = idx % 8, c = (idx / 8) % (kK / 4), r = (idx / (8 * (kK / 4))) * 8 + rr;
+        const int row = (isA ? i0 : j0) + r;
+        v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row < n) {
+            const float* src = F + (size_t)row * n + k0 + 4 * c;
+            if ((n & 3) == 0) v[q] = *(const float4*)src;
+            else v[q] = make_float4(src[0], src[1], src[2], src[3]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kPA + kPB; ++q) {
+        const bool isA = q < kPA;
+        const int idx = tid + (isA ? q : q - kPA) * 256;
+        const int rr = idx % 8, c = (idx / 8) % (kK / 4), g = idx / (8 * (kK / 4));
+        float4 h, l;
+        h.x = tf32_hi(v[q].x); l.x = v[q].x - h.x;
+        h.y = tf32_hi(v[q].y); l.y = v[q].y - h.y;
+        h.z = tf32_hi(v[q].z); l.z = v[q].z - h.z;
+        h.w = tf32_hi(v[q].w); l.w = v[q].w - h.w;
+        const size_t off = ((size_t)(g * (kK / 4) + c) * 8 + rr) * 4;
+        *(float4*)((isA ? Ahi : Bhi) + off) = h;
+        *(float4*)((isA ? Alo : Blo) + off) = l;
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t taddr = *s_taddr;
+    if (tid == 0) {
+        const uint32_t lbo = 128, sbo = (kK / 4) * 128;
+        for (uint32_t ks = 0; ks < kK / 8; ++ks) {
+            const uint32_t koff = ks * 256;                        // K = 8: two core matrices
+            const uint64_t ah = sdesc(su32(Ahi) + koff, lbo, sbo), al = sdesc(su32(Alo) + koff, lbo, sbo);
+            const uint64_t bh = sdesc(su32(Bhi) + koff, lbo, sbo), bl = sdesc(su32(Blo) + koff, lbo, sbo);
+            mma(taddr, ah, bh, ks > 0 ? 1u : 0u);
+            mma(taddr, ah, bl, 1u);
+            mma(taddr, al, bh, 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(su32(mbar)));
+    }
+    bool done = false;
+    for (long it = 0; it < (1L << 24) && !done; ++it) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(su32(mbar)), "r"(0));
+        done = ok != 0;
+    }
+    if (!done && tid == 0) atomicOr(flag, 2);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // accumulator -> shared (over the operand tiles, no longer read): warp w takes lanes
+    // 32 (w % 4) .. +31 and columns 32 (w / 4) .. +31
+    float (*D)[kN + 1] = (float (*)[kN + 1])smem_raw;
+    if (done) {
+        const int rbase = (warp % 4) * 32, cbase = (warp / 4) * 32;
+#pragma unroll
+        for (int c0 = 0; c0 < 32; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t a = taddr + ((uint32_t)rbase << 16) + (uint32_t)(cbase + c0);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                         : "r"(a));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int q = 0; q < 16; ++q) D[rbase + lane][cbase + c0 + q] = __uint_as_float(r[q]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(kN));
+    if (!done) return;
+    // C -= D on the lower triangle, coalesced: warp w takes rows w, w+8, ..., a lane two
+    // columns; every C value of the thread is loaded before any is written
+    constexpr int kRows = (int)kM / 8;
+    float cv[kRows][2];
+#pragma unroll
+    for (int t = 0; t < kRows; ++t) {
+        const int i = i0 + warp + 8 * t;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + lane + 32 * h;
+            cv[t][h] = (i < n && j <= i) ? F[(size_t)i * n + j] : 0.0f;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kRows; ++t) {
+        const int rl = warp + 8 * t, i = i0 + rl;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h, j = j0 + c;
+            if (i < n && j <= i) F[(size_t)i * n + j] = cv[t][h] - D[rl][c];
+        }
+    }
+}
+
+template <typename T>
+static void launch_update(igs_prob p, int n, T* F, int k0, int kb, int mode, cudaStream_t s);
+template <>
+void launch_update<double>(igs_prob, int n, double* F, int k0, int kb, int mode, cudaStream_t s) {
+    const int rem = n - k0 - kb, nt = (rem + kST - 1) / kST;
+    if (mode == 1) k_syrk<double><<<nt, 256, syrk_smem<double>(), s>>>(n, F, k0, kb, 1);
+    else k_syrk<double><<<(nt - 1) * nt / 2, 256, syrk_smem<double>(), s>>>(n, F, k0, kb, 2);
+}
+// MIXED tier: the next panel's column block (on the critical path, few tiles) by the
+// SIMT kernel, whose 64 x 64 tiles have the shorter latency; the rest of the trailing
+// matrix, which runs beside the next panel, on the tensor cores.
+template <>
+void launch_update<float>(igs_prob p, int n, float* F, int k0, int kb, int mode, cudaStream_t s) {
+    const int rem = n - k0 - kb;
+    const int ntr = (rem + (int)tc::kM - 1) / (int)tc::kM, ntc = (rem + (int)tc::kN - 1) / (int)tc::kN;
+    if (mode == 1) k_syrk<float><<<(rem + kST - 1) / kST, 256, syrk_smem<float>(), s>>>(n, F, k0, kb, 1);
+    else k_syrk_tc<<<dim3(ntc - 1, ntr), 256, tc::smem_bytes(), s>>>(n, F, k0, kb, 2, p->d_flag);
+}
+
 // One factorisation as a two-stream launch sequence (captured into a graph):
 // s0 carries panel k, the update of column block k+1 and panel k+1; s1 the
 // rest of the update of step k, concurrent with panel k+1.  Ordering: the
@@ -652,11 +833,11 @@ static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent
             IGS_CUDA(cudaStreamWaitEvent(s0, evB, 0));
             pending = false;
         }
-        k_syrk<T><<<nt, 256, syrk_smem<T>(), s0>>>(n, F, k0, kb, 1);
+        launch_update<T>(p, n, F, k0, kb, 1, s0);
         if (nt > 1) {
             IGS_CUDA(cudaStreamWaitEvent(s1, evP, 0));
             forked = true;
-            k_syrk<T><<<(nt - 1) * nt / 2, 256, syrk_smem<T>(), s1>>>(n, F, k0, kb, 2);
+            launch_update<T>(p, n, F, k0, kb, 2, s1);
             IGS_CUDA(cudaEventRecord(evB, s1));
             pending = true;
         }
@@ -685,6 +866,7 @@ static void factor(igs_prob p, cudaStream_t s) {
     const int n = p->plan.n;
     ensure_dyn_smem((const void*)k_panel<T>, (size_t)panel_smem<T>());
     ensure_dyn_smem((const void*)k_syrk<T>, (size_t)syrk_smem<T>());
+    ensure_dyn_smem((const void*)k_syrk_tc, tc::smem_bytes());
     if (!p->factor_exec) {
         // capture the fixed launch sequence once, on two private streams
         cudaStream_t cs = nullptr, cs1 = nullptr;
@@ -726,6 +908,7 @@ static void factor(igs_prob p, cudaStream_t s) {
     int flag = 0;
     IGS_CUDA(cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     IGS_CUDA(cudaStreamSynchronize(s));
+    if (flag & 2) throw Error(IGS_E_TIMEOUT, "tensor-core update: MMA completion wait exceeded its budget");
     if (flag) throw Error(IGS_E_NOT_SPD, "Cholesky met a non-positive pivot");
 }
 
