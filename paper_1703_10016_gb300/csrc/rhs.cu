@@ -9,10 +9,12 @@
 // an N_quad x N_GQ kernel sum.  The Gauss range is split in kSplit slices, one
 // grid row each, so that every node has kSplit partial sums (reduced in a fixed
 // order by k_beta: results do not depend on scheduling).  MIXED tier: FP32 with
-// float-float coordinate differences for every pair except the Gauss points of
-// the node's refined element and its two neighbours, where the numerator
-// (f(t)-f(s)).n(t) is second-order small; those are summed in FP64 by
-// k_double_layer_near into one more partial slot.  FP64 tier: every pair in FP64.
+// float-float coordinate differences for every pair.  At the Gauss points of
+// the node's refined element and its two neighbours the numerator
+// (f(t)-f(s)).n(t) is second-order small and the FP32 value is poor, so
+// k_double_layer_near recomputes those pairs in FP64 and, in one more partial
+// slot, replaces their FP32 contributions (reproduced bit for bit by the same
+// FP32 operations, kb32_pair) by the FP64 ones.  FP64 tier: every pair in FP64.
 #include <mutex>
 
 #include "igs_internal.h"
@@ -37,31 +39,35 @@ __device__ __forceinline__ void split2(double v, float& hi, float& lo) {
     lo = (float)(v - (double)hi);
 }
 
-__device__ __forceinline__ bool near_elem(int eg, int em, int M) {
-    int dd = eg - em;
-    if (dd < 0) dd = -dd;
-    if (dd > M / 2) dd = M - dd;              // closed curve: cyclic distance
-    return dd <= 1;
+// FP32 double-layer kernel value of one pair from float-float coordinates; the
+// operations are spelled out (no contraction) so that the far-field and near-
+// field kernels compute identical bits.
+__device__ __forceinline__ float kb32_pair(float gxh, float gxl, float gyh, float gyl, float a, float b, float xh,
+                                           float xl, float yh, float yl) {
+    const float dx = __fadd_rn(__fsub_rn(gxh, xh), __fsub_rn(gxl, xl));
+    const float dy = __fadd_rn(__fsub_rn(gyh, yh), __fsub_rn(gyl, yl));
+    const float num = __fmaf_rn(dy, b, __fmul_rn(dx, a));
+    const float r2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+    return __fdividef(num, r2);
 }
 
-// MIXED far field: partial sums over Gauss slice blockIdx.y, FP32, near pairs masked.
+// MIXED far field: partial sums over Gauss slice blockIdx.y, FP32, every pair
+// (the near pairs are replaced by k_double_layer_near).  Gauss data in shared
+// memory as 16-byte coordinate records and 8-byte (a, b) records.
 template <int NR>
-__global__ void __launch_bounds__(256) k_double_layer_f(int Nq, int Ng, int M, const double* __restrict__ geo,
-                                                        const int* __restrict__ fspan, const double* __restrict__ rgeo,
+__global__ void __launch_bounds__(256) k_double_layer_f(int Nq, int Ng, const double* __restrict__ geo,
+                                                        const double* __restrict__ rgeo,
                                                         const double* __restrict__ rw, const double* __restrict__ uD,
                                                         int ldu, int off, double* __restrict__ part) {
-    __shared__ float sxh[kRhsChunk], sxl[kRhsChunk], syh[kRhsChunk], syl[kRhsChunk];
-    __shared__ float sa[kRhsChunk], sb[kRhsChunk];
-    __shared__ int se[kRhsChunk];
+    __shared__ float4 sg[kRhsChunk];
+    __shared__ float2 sab[kRhsChunk];
     __shared__ float su[NR][kRhsChunk];
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = m < Nq;
     float xh = 0, xl = 0, yh = 0, yl = 0;
-    int em = 0;
     if (live) {
         split2(geo[m], xh, xl);
         split2(geo[Nq + m], yh, yl);
-        em = fspan[m];
     }
     float acc[NR];
 #pragma unroll
@@ -73,11 +79,11 @@ __global__ void __launch_bounds__(256) k_double_layer_f(int Nq, int Ng, int M, c
         __syncthreads();
         for (int q = threadIdx.x; q < cn; q += blockDim.x) {
             const int g = g0 + q;
-            split2(rgeo[g], sxh[q], sxl[q]);
-            split2(rgeo[Ng + g], syh[q], syl[q]);
-            sa[q] = (float)rgeo[3 * Ng + g];          //  f2'(t)
-            sb[q] = (float)(-rgeo[2 * Ng + g]);       // -f1'(t)
-            se[q] = g / kGaussRhs;
+            float4 c;
+            split2(rgeo[g], c.x, c.y);
+            split2(rgeo[Ng + g], c.z, c.w);
+            sg[q] = c;
+            sab[q] = make_float2((float)rgeo[3 * Ng + g], (float)(-rgeo[2 * Ng + g]));   // f2'(t), -f1'(t)
             const double w = rw[g];
 #pragma unroll
             for (int k = 0; k < NR; ++k) su[k][q] = (float)(w * uD[(size_t)k * ldu + off + g]);
@@ -86,12 +92,9 @@ __global__ void __launch_bounds__(256) k_double_layer_f(int Nq, int Ng, int M, c
         if (live) {
 #pragma unroll 4
             for (int q = 0; q < cn; ++q) {
-                const float dx = (sxh[q] - xh) + (sxl[q] - xl);
-                const float dy = (syh[q] - yh) + (syl[q] - yl);
-                const float num = dx * sa[q] + dy * sb[q];
-                const float r2 = dx * dx + dy * dy;
-                float kb = num * __frcp_rn(r2);
-                kb = near_elem(se[q], em, M) ? 0.f : kb;
+                const float4 c = sg[q];
+                const float2 ab = sab[q];
+                const float kb = kb32_pair(c.x, c.y, c.z, c.w, ab.x, ab.y, xh, xl, yh, yl);
 #pragma unroll
                 for (int k = 0; k < NR; ++k) acc[k] = fmaf(kb, su[k][q], acc[k]);
             }
@@ -145,7 +148,9 @@ __global__ void __launch_bounds__(256) k_double_layer_d(int Nq, int Ng, const do
     }
 }
 
-// MIXED near field: Gauss points of the node's element and its two neighbours, FP64.
+// MIXED near field: Gauss points of the node's element and its two neighbours.
+// Adds their FP64 contributions and removes the FP32 ones the far-field kernel
+// summed (same bits from kb32_pair; the product of two floats is exact in FP64).
 __global__ void k_double_layer_near(int Nq, int Ng, int M, int nrhs, const double* __restrict__ geo,
                                     const int* __restrict__ fspan, const double* __restrict__ rgeo,
                                     const double* __restrict__ rw, const double* __restrict__ uD, int ldu, int off,
@@ -153,6 +158,9 @@ __global__ void k_double_layer_near(int Nq, int Ng, int M, int nrhs, const doubl
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= Nq) return;
     const double xm = geo[m], ym = geo[Nq + m];
+    float xh, xl, yh, yl;
+    split2(xm, xh, xl);
+    split2(ym, yh, yl);
     const int em = fspan[m];
     double acc[kMaxRhs];
     for (int k = 0; k < nrhs; ++k) acc[k] = 0.0;
@@ -164,8 +172,16 @@ __global__ void k_double_layer_near(int Nq, int Ng, int M, int nrhs, const doubl
             const int g = e * kGaussRhs + q;
             const double dx = rgeo[g] - xm, dy = rgeo[Ng + g] - ym;
             const double kb = (dx * rgeo[3 * Ng + g] - dy * rgeo[2 * Ng + g]) / (dx * dx + dy * dy);
+            float gxh, gxl, gyh, gyl;
+            split2(rgeo[g], gxh, gxl);
+            split2(rgeo[Ng + g], gyh, gyl);
+            const float kb32 = kb32_pair(gxh, gxl, gyh, gyl, (float)rgeo[3 * Ng + g], (float)(-rgeo[2 * Ng + g]), xh,
+                                         xl, yh, yl);
             const double w = rw[g];
-            for (int k = 0; k < nrhs; ++k) acc[k] += kb * w * uD[(size_t)k * ldu + off + g];
+            for (int k = 0; k < nrhs; ++k) {
+                const double u = uD[(size_t)k * ldu + off + g];
+                acc[k] += kb * w * u - (double)kb32 * (double)(float)(w * u);
+            }
         }
     }
     for (int k = 0; k < nrhs; ++k) part[(size_t)k * Nq + m] = acc[k];
@@ -248,8 +264,8 @@ static void launch_far(igs_prob p, const double* d_uD, int ldu, double* part) {
     cudaStream_t s = p->geom->ctx->stream;
     dim3 grid((P.Nq + 255) / 256, kSplit);
     if (p->precision == IGS_MIXED)
-        k_double_layer_f<NR><<<grid, 256, 0, s>>>(P.Nq, p->Ng, P.M, p->d_geo, p->d_fspan, p->d_rhs_geo, p->d_rhs_w,
-                                                  d_uD, ldu, P.Nq, part);
+        k_double_layer_f<NR><<<grid, 256, 0, s>>>(P.Nq, p->Ng, p->d_geo, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq,
+                                                  part);
     else
         k_double_layer_d<NR><<<grid, 256, 0, s>>>(P.Nq, p->Ng, p->d_geo, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq,
                                                   part);
