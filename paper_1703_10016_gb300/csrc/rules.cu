@@ -341,7 +341,8 @@ __global__ void __launch_bounds__(128) k_mu_tab(int NE, int M, int d, int den, i
 // each substitution stay in a register window, so the only memory traffic on
 // the dependency chain is the streamed factor row and one store per step.
 template <int D>
-__device__ void gsolve_col(int NE, const double* __restrict__ L, double* __restrict__ Z, int ldz, int c) {
+__device__ void gsolve_col(int NE, const double* __restrict__ L, const double* __restrict__ rd, double* __restrict__ Z,
+                           int ldz, int c) {
     double win[D + 1];
 #pragma unroll
     for (int r = 0; r <= D; ++r) win[r] = 0.0;             // win[r] = z[j - r] after step j
@@ -350,7 +351,7 @@ __device__ void gsolve_col(int NE, const double* __restrict__ L, double* __restr
 #pragma unroll
         for (int r = 1; r <= D; ++r)
             if (j - r >= 0) s -= L[j * (D + 1) + r] * win[r - 1];
-        const double v = s / L[j * (D + 1)];
+        const double v = s * rd[j];
 #pragma unroll
         for (int r = D; r > 0; --r) win[r] = win[r - 1];
         win[0] = v;
@@ -363,7 +364,7 @@ __device__ void gsolve_col(int NE, const double* __restrict__ L, double* __restr
 #pragma unroll
         for (int r = 1; r <= D; ++r)
             if (j + r < NE) s -= L[(j + r) * (D + 1) + r] * win[r - 1];
-        const double v = s / L[j * (D + 1)];
+        const double v = s * rd[j];
 #pragma unroll
         for (int r = D; r > 0; --r) win[r] = win[r - 1];
         win[0] = v;
@@ -371,15 +372,23 @@ __device__ void gsolve_col(int NE, const double* __restrict__ L, double* __restr
     }
 }
 
-__global__ void k_gsolve(int NE, int d, int ncol, const double* __restrict__ L, double* __restrict__ Z, int ldz) {
+__global__ void k_gsolve(int NE, int d, int ncol, const double* __restrict__ L, const double* __restrict__ rd,
+                         double* __restrict__ Z, int ldz) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncol) return;
     switch (d) {
-        case 2: gsolve_col<2>(NE, L, Z, ldz, c); break;
-        case 3: gsolve_col<3>(NE, L, Z, ldz, c); break;
-        case 4: gsolve_col<4>(NE, L, Z, ldz, c); break;
-        default: gsolve_col<5>(NE, L, Z, ldz, c); break;
+        case 2: gsolve_col<2>(NE, L, rd, Z, ldz, c); break;
+        case 3: gsolve_col<3>(NE, L, rd, Z, ldz, c); break;
+        case 4: gsolve_col<4>(NE, L, rd, Z, ldz, c); break;
+        default: gsolve_col<5>(NE, L, rd, Z, ldz, c); break;
     }
+}
+
+// Reciprocals of the Cholesky diagonal: the substitutions multiply instead of
+// dividing (an FP64 division is a long dependent sequence on this GPU).
+__global__ void k_recip_diag(int NE, int d, const double* __restrict__ L, double* __restrict__ rd) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < NE) rd[j] = 1.0 / L[j * (d + 1)];
 }
 
 // WsT[nn][m] = w^{eta_m}_{nn} = sum_r B-bar_{e+r}(eta_nn) z_m[e+r], e = fspan[nn].
@@ -408,7 +417,8 @@ __global__ void k_ws(int Nq, int d, const int* __restrict__ fspan, const double*
 // 1e-40 of the largest so far (the rest is zero to far below the 1e-20 cut
 // applied afterwards).
 __global__ void k_ycols(int ncols, int NE, int d, const int* __restrict__ cols, const int* __restrict__ fspan,
-                        const double* __restrict__ Bf, const double* __restrict__ L, double* __restrict__ Y) {
+                        const double* __restrict__ Bf, const double* __restrict__ L, const double* __restrict__ rd,
+                        double* __restrict__ Y) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncols) return;
     const int mp = cols[c], e0 = fspan[mp];
@@ -419,7 +429,7 @@ __global__ void k_ycols(int ncols, int NE, int d, const int* __restrict__ cols, 
         double s = (j - e0 <= d) ? Bf[mp * (d + 1) + (j - e0)] : 0.0;
         const int p0 = (j - d > e0) ? j - d : e0;
         for (int p = p0; p < j; ++p) s -= L[j * (d + 1) + (j - p)] * y[p];
-        const double v = s / L[j * (d + 1)];
+        const double v = s * rd[j];
         y[j] = v;
         big = fmax(big, fabs(v));
         small = (j > e0 + d && fabs(v) <= 1e-40 * big) ? small + 1 : 0;
@@ -430,7 +440,7 @@ __global__ void k_ycols(int ncols, int NE, int d, const int* __restrict__ cols, 
         double s = y[j];
         const int p1 = (j + d < jstop) ? j + d : jstop;
         for (int p = j + 1; p <= p1; ++p) s -= L[p * (d + 1) + (p - j)] * y[p];
-        const double v = s / L[j * (d + 1)];
+        const double v = s * rd[j];
         y[j] = v;
         big = fmax(big, fabs(v));
         small = (j < e0 && fabs(v) <= 1e-40 * big) ? small + 1 : 0;
@@ -514,26 +524,34 @@ __global__ void k_wrows(int Nq, int d, int nrow, const int* __restrict__ fspan, 
     Wr[(size_t)r * Nq + mp] = s;
 }
 
-// Interior Toeplitz sequences from the anchor columns: T[p][delta + Nq - 1] =
-// W^s[m][m'] for interior m' of parity p and m - m' = delta; the left anchor
-// gives delta >= 0, the right one delta < 0.
-__global__ void k_toeplitz(int Nq, int R, int aL0, int aL1, int aR0, int aR1, const double* __restrict__ WcL0,
-                           const double* __restrict__ WcL1, const double* __restrict__ WcR0,
-                           const double* __restrict__ WcR1, double* __restrict__ T) {
+// Interior Toeplitz sequences from the two left anchor columns (node indices
+// aL0 = B and aL1 = B + 1): T[p][delta + Nq - 1] = W^s[m][m'] for interior m'
+// of parity p = (m' - B) & 1 and m - m' = delta.  delta >= 0 reads the anchor
+// of parity p directly; delta < 0 reads it through the centrosymmetry
+// W^s[m][m'] = W^s[Nq-1-m][Nq-1-m'], where the reflected column Nq-1-m' has
+// parity (Nq - 1 - p) & 1.
+__global__ void k_toeplitz(int Nq, int R, int aL0, int aL1, const double* __restrict__ WcL0,
+                           const double* __restrict__ WcL1, double* __restrict__ T) {
     const size_t len = 2 * (size_t)Nq - 1;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 2 * len) return;
     const int p = int(idx / len);
     const int delta = int(idx % len) - (Nq - 1);
-    double v = 0.0;
-    if (delta >= 0) {
-        const int m = (p ? aL1 : aL0) + delta;
-        if (m <= Nq - R - 1) v = (p ? WcL1 : WcL0)[m];
-    } else {
-        const int m = (p ? aR1 : aR0) + delta;
-        if (m >= R) v = (p ? WcR1 : WcR0)[m];
-    }
-    T[idx] = v;
+    const int q = (delta >= 0) ? p : ((Nq - 1 - p) & 1);
+    const int m = (q ? aL1 : aL0) + (delta >= 0 ? delta : -delta);
+    T[idx] = (m <= Nq - R - 1) ? (q ? WcL1 : WcL0)[m] : 0.0;
+}
+
+// Right-end boundary columns (or rows) from the left-end ones.  The nodes, the
+// knots and ln|u - v| are symmetric under u -> a + b - u, so W^s is
+// centrosymmetric: W^s[m][m'] = W^s[Nq-1-m][Nq-1-m'].  dst has 2K rows of
+// length Nq; rows c0 .. 2K-1 are written, dst[c] = src[c] for c < K and
+// dst[c][m] = src[2K-1-c][Nq-1-m] for c >= K.  With c0 = K, src may be dst.
+__global__ void k_mirror(int Nq, int K, int c0, const double* src, double* dst) {
+    const int c = c0 + blockIdx.y;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nq) return;
+    dst[(size_t)c * Nq + m] = (c < K) ? src[(size_t)c * Nq + m] : src[(size_t)(2 * K - 1 - c) * Nq + (Nq - 1 - m)];
 }
 
 __global__ void k_to_f32(size_t count, const double* __restrict__ x, float* __restrict__ y) {
@@ -640,6 +658,9 @@ void rules_build(igs_prob p) {
     ++launches;
     k_chol_band<<<1, 256, 0, s>>>(NE, d, p->d_G, d_L, p->d_flag);
     ++launches;
+    double* d_rd = (double*)dev_alloc(p, sizeof(double) * NE);
+    k_recip_diag<<<(NE + 255) / 256, 256, 0, s>>>(NE, d, d_L, d_rd);
+    ++launches;
     IGS_CUDA(cudaGetLastError());
 
     // element-moment table over all node/element offsets
@@ -660,7 +681,7 @@ void rules_build(igs_prob p) {
         k_mu_tab<<<dim3((NE + 127) / 128, Nq), 128, 0, s>>>(NE, M, d, den, dmin, p->d_pos, nullptr, p->d_piece, d_Et,
                                                            p->d_Z, Nq);
         ++launches;
-        k_gsolve<<<(Nq + 127) / 128, 128, 0, s>>>(NE, d, Nq, d_L, p->d_Z, Nq);
+        k_gsolve<<<(Nq + 127) / 128, 128, 0, s>>>(NE, d, Nq, d_L, d_rd, p->d_Z, Nq);
         ++launches;
         p->d_WsT = (double*)dev_alloc(p, sizeof(double) * (size_t)Nq * Nq);
         if (mixed) p->d_WsT32 = (float*)dev_alloc(p, sizeof(float) * (size_t)Nq * Nq);
@@ -669,24 +690,19 @@ void rules_build(igs_prob p) {
         ++launches;
         IGS_CUDA(cudaGetLastError());
     } else {
-        // compressed: B boundary columns at each end, four interior anchor
-        // columns (two per node parity, one near each end), R boundary rows
+        // compressed: B boundary columns and R boundary rows at the left end,
+        // two interior anchor columns (one per node parity); the right end
+        // follows by centrosymmetry
         p->ws_B = B;
         p->ws_R = R;
-        const int ncols = 2 * B + 4;
+        const int ncols = B + 2;
         std::vector<int> cols(ncols);
-        for (int c = 0; c < B; ++c) { cols[c] = c; cols[B + c] = Nq - B + c; }
-        int aR[2];
-        for (int q = 0; q < 2; ++q) aR[q] = Nq - B - 1 - ((Nq - B - 1 - B - q) & 1);
-        cols[2 * B] = B;
-        cols[2 * B + 1] = B + 1;
-        cols[2 * B + 2] = aR[0];
-        cols[2 * B + 3] = aR[1];
+        for (int c = 0; c < ncols; ++c) cols[c] = c;
         int* d_cols = (int*)dev_alloc(p, sizeof(int) * ncols);
         IGS_CUDA(cudaMemcpyAsync(d_cols, cols.data(), sizeof(int) * ncols, cudaMemcpyHostToDevice, s));
         double* d_Y = (double*)dev_alloc(p, sizeof(double) * (size_t)ncols * NE);
         IGS_CUDA(cudaMemsetAsync(d_Y, 0, sizeof(double) * (size_t)ncols * NE, s));
-        k_ycols<<<(ncols + 63) / 64, 64, 0, s>>>(ncols, NE, d, d_cols, p->d_fspan, p->d_Bf, d_L, d_Y);
+        k_ycols<<<(ncols + 63) / 64, 64, 0, s>>>(ncols, NE, d, d_cols, p->d_fspan, p->d_Bf, d_L, d_rd, d_Y);
         ++launches;
         const int cap = std::min(M, 1024);
         int* d_er = (int*)dev_alloc(p, sizeof(int) * 2 * ncols);
@@ -699,27 +715,27 @@ void rules_build(igs_prob p) {
         k_wcols<<<dim3((Nq + 255) / 256, ncols), 256, ysm, s>>>(Nq, d, den, dmin, cap, p->d_pos, d_Et, d_er, d_Yc,
                                                                d_Wc);
         ++launches;
-        // boundary rows: full rules at the first and last R nodes
-        std::vector<int> rows(2 * R);
-        for (int r = 0; r < R; ++r) { rows[r] = r; rows[R + r] = Nq - R + r; }
-        int* d_rows = (int*)dev_alloc(p, sizeof(int) * 2 * R);
-        IGS_CUDA(cudaMemcpyAsync(d_rows, rows.data(), sizeof(int) * 2 * R, cudaMemcpyHostToDevice, s));
-        double* d_Zr = (double*)dev_alloc(p, sizeof(double) * (size_t)NE * 2 * R);
-        k_mu_tab<<<dim3((NE + 127) / 128, 2 * R), 128, 0, s>>>(NE, M, d, den, dmin, p->d_pos, d_rows, p->d_piece,
-                                                              d_Et, d_Zr, 2 * R);
-        k_gsolve<<<1, 2 * R, 0, s>>>(NE, d, 2 * R, d_L, d_Zr, 2 * R);
+        // boundary rows: full rules at the first R nodes, mirrored to the last R
+        std::vector<int> rows(R);
+        for (int r = 0; r < R; ++r) rows[r] = r;
+        int* d_rows = (int*)dev_alloc(p, sizeof(int) * R);
+        IGS_CUDA(cudaMemcpyAsync(d_rows, rows.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
+        double* d_Zr = (double*)dev_alloc(p, sizeof(double) * (size_t)NE * R);
+        k_mu_tab<<<dim3((NE + 127) / 128, R), 128, 0, s>>>(NE, M, d, den, dmin, p->d_pos, d_rows, p->d_piece, d_Et,
+                                                          d_Zr, R);
+        k_gsolve<<<1, R, 0, s>>>(NE, d, R, d_L, d_rd, d_Zr, R);
         p->d_WsRow = (double*)dev_alloc(p, sizeof(double) * (size_t)2 * R * Nq);
-        k_wrows<<<dim3((Nq + 255) / 256, 2 * R), 256, 0, s>>>(Nq, d, 2 * R, p->d_fspan, p->d_Bf, d_Zr, p->d_WsRow);
-        launches += 3;
-        // boundary columns (first 2B rows of Wc) and Toeplitz sequences
+        k_wrows<<<dim3((Nq + 255) / 256, R), 256, 0, s>>>(Nq, d, R, p->d_fspan, p->d_Bf, d_Zr, p->d_WsRow);
+        k_mirror<<<dim3((Nq + 255) / 256, R), 256, 0, s>>>(Nq, R, R, p->d_WsRow, p->d_WsRow);
+        launches += 4;
+        // boundary columns at both ends and the Toeplitz sequences
         p->d_WsT = (double*)dev_alloc(p, sizeof(double) * (size_t)2 * B * Nq);
-        IGS_CUDA(cudaMemcpyAsync(p->d_WsT, d_Wc, sizeof(double) * (size_t)2 * B * Nq, cudaMemcpyDeviceToDevice, s));
+        k_mirror<<<dim3((Nq + 255) / 256, 2 * B), 256, 0, s>>>(Nq, B, 0, d_Wc, p->d_WsT);
         const size_t tlen = 2 * (2 * (size_t)Nq - 1);
         p->d_WsToe = (double*)dev_alloc(p, sizeof(double) * tlen);
-        k_toeplitz<<<(unsigned)((tlen + 255) / 256), 256, 0, s>>>(
-            Nq, R, B, B + 1, aR[0], aR[1], d_Wc + (size_t)(2 * B) * Nq, d_Wc + (size_t)(2 * B + 1) * Nq,
-            d_Wc + (size_t)(2 * B + 2) * Nq, d_Wc + (size_t)(2 * B + 3) * Nq, p->d_WsToe);
-        launches += 1;
+        k_toeplitz<<<(unsigned)((tlen + 255) / 256), 256, 0, s>>>(Nq, R, B, B + 1, d_Wc + (size_t)B * Nq,
+                                                                   d_Wc + (size_t)(B + 1) * Nq, p->d_WsToe);
+        launches += 2;
         if (mixed) {
             const size_t nc = (size_t)2 * B * Nq, nr = (size_t)2 * R * Nq;
             p->d_WsT32 = (float*)dev_alloc(p, sizeof(float) * nc);
@@ -751,6 +767,7 @@ void rules_build(igs_prob p) {
     cudaEventDestroy(e1);
     if (p->d_Z) dev_free(p, p->d_Z);
     dev_free(p, d_L);
+    dev_free(p, d_rd);
     dev_free(p, d_tk);
     p->timing.rules_ms = ms;
     p->launches += launches;
