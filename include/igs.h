@@ -343,6 +343,13 @@ int igs_get_rules(igs_prob prob, double* eta, double* W_band, int32_t* first, do
  * (f(eta_n)), J[n_quad] (|f'(eta_n)|).  Errors: STATE, CUDA. */
 int igs_get_node_geometry(igs_prob prob, double* xy, double* J);
 
+/* Self-test of the bounded waits that the triangular solves use between
+ * thread blocks: one GPU thread waits for a 64-bit word that nothing writes,
+ * with a budget of `budget_s` seconds (clamped to [1e-4, 2]), and must give
+ * up.  *gave_up = 1 when the wait ended by its budget (the expected result),
+ * 0 otherwise.  The CUDA context stays usable.  Errors: INVALID_ARG, CUDA. */
+int igs_selftest_wait(igs_ctx ctx, double budget_s, int* gave_up);
+
 #ifdef __cplusplus
 }
 #endif

@@ -158,6 +158,16 @@ int igs_destroy(igs_ctx ctx) {
     API_END
 }
 
+int igs_selftest_wait(igs_ctx ctx, double budget_s, int* gave_up) {
+    API_BEGIN
+    REQUIRE(ctx && gave_up, IGS_E_INVALID_ARG, "ctx or gave_up is NULL");
+    REQUIRE(budget_s == budget_s, IGS_E_INVALID_ARG, "budget is NaN");
+    const int st = wait_selftest(ctx->device, std::min(2.0, std::max(1e-4, budget_s)));
+    REQUIRE(st == 0 || st == 1, IGS_E_CUDA, "wait self-test kernel did not report");
+    *gave_up = st;
+    API_END
+}
+
 int igs_create_geometry(igs_ctx ctx, igs_geom* out, int degree, const double* knots, int n_knots,
                         const double* ctrl_xy, const double* weights, int n_ctrl, int closed) {
     API_BEGIN
@@ -260,7 +270,7 @@ int igs_destroy_problem(igs_prob p) {
                      p->d_Bt, p->d_W, p->d_G, p->d_Z, p->d_WsT,
                      p->d_WsT32, p->d_WsRow, p->d_WsRow32, p->d_WsToe, p->d_WsToe32,
                      p->d_flag, p->d_geo, p->d_nodes,
-                     p->d_P, p->d_Q, p->d_A, p->d_F, p->d_As64, p->d_diagL, p->d_diagLinv, p->d_tflags,
+                     p->d_P, p->d_Q, p->d_A, p->d_F, p->d_As64, p->d_diagL, p->d_diagLinv, p->d_tflags, p->d_tpub,
                      p->d_beta, p->d_rhs_geo, p->d_rhs_w, p->d_rhs_t};
     for (void* q : ptrs) dev_free_raw(p, q);
     if (p->factor_exec) cudaGraphExecDestroy(p->factor_exec);

@@ -57,7 +57,9 @@ __device__ __forceinline__ void split(double v, float& hi, float& lo) {
 }
 
 // FP32-tier node record and weights of node m (float-float coordinates and
-// parameter offsets, ln J, P = J W, Q = J B_test).
+// parameter offsets, both divided by the parameter length L, ln J, P = J W,
+// Q = J B_test).  The common factor 1/L leaves |f(s) - f(t)| / D unchanged and
+// turns the three-image factor's 1/L^2 into 1.
 __device__ __forceinline__ void prep_f_node(int m, int Nq, int d, double L, const double* __restrict__ geo,
                                             const double* __restrict__ eta, const double* __restrict__ W,
                                             const double* __restrict__ Bt, NodeF* __restrict__ nodes,
@@ -66,11 +68,12 @@ __device__ __forceinline__ void prep_f_node(int m, int Nq, int d, double L, cons
     double e = eta[m] - eta[0], eb = L - e;
     if (m == Nq - 1) { e = L; eb = 0.0; }
     if (m == 0) { e = 0.0; eb = L; }
+    const double s = 1.0 / L;
     NodeF r;
-    split(geo[m], r.xh, r.xl);
-    split(geo[Nq + m], r.yh, r.yl);
-    split(e, r.eh, r.el);
-    split(eb, r.ebh, r.ebl);
+    split(geo[m] * s, r.xh, r.xl);
+    split(geo[Nq + m] * s, r.yh, r.yl);
+    split(e * s, r.eh, r.el);
+    split(eb * s, r.ebh, r.ebl);
     r.lnJ = (float)log(J);
     nodes[m] = r;
     for (int k = 0; k <= d; ++k) {
@@ -193,33 +196,108 @@ __global__ void __launch_bounds__(256) k_assemble_tile(
     }
 }
 
-// Natural logarithm for the FP32 tier, x > 0 and normal: x = 2^e m with m in
-// [sqrt(1/2), sqrt(2)) by exponent arithmetic, ln x = (e + log2 m) ln 2.  On
+// Base-2 logarithm for the FP32 tier, x > 0 and normal: x = 2^e m with m in
+// [sqrt(1/2), sqrt(2)) by exponent arithmetic, log2 x = e + log2 m.  On
 // [0.5, 2] the hardware base-2 logarithm (__log2f) has an absolute error of
-// at most 2^-22, so ln x carries an absolute error of about 2^-22 ln 2 plus
-// the rounding of the result.
-__device__ __forceinline__ float ln_pos(float x) {
+// at most 2^-22, so the result carries that absolute error plus its rounding.
+__device__ __forceinline__ float log2_pos(float x) {
     const int ix = __float_as_int(x);
     const int e = (ix - 0x3f3504f3) >> 23;            // 0x3f3504f3 = sqrt(1/2)
     const float m = __int_as_float(ix - (e << 23));
-    return ((float)e + __log2f(m)) * 0.693147180559945309f;
+    return (float)e + __log2f(m);
 }
 
 // FP32 tier, one thread per A-range node: the block is as wide as the largest
 // node range (rounded up to a warp), so that no thread idles in stage 1.  The
 // B-range nodes are kept in shared memory as 16-byte records read by
-// broadcast; the singular weight for the next pair is fetched one step ahead.
-// Tile (I, J) of TI x TI entries of A; `smem` as sized by tile_smem_f.
+// broadcast, and walked in groups of equal first column, so that the window
+// of d+1 running sums moves once per group.  The kernel value is formed in
+// base-2 units, c = log2(|f(s) - f(t)|^2 / D^2) = 2 K1 / ln 2, on node
+// coordinates scaled by 1/L (which leaves the ratio unchanged and removes the
+// 1/L^2 of the three-image factor); the factor ln 2 / 2 rides on the staged
+// regular weights P.  Tiles whose nodes all lie where W^s is a Toeplitz
+// sequence (interior columns and rows of the stored rules) stage the window of
+// the two sequences they touch, so the singular weight is one shared-memory
+// read at a per-node offset; the other tiles read the stored rules through
+// ws_at, fetched a few steps ahead.  Only tiles whose A- and B-ranges share a
+// node test for the diagonal limit.
+template <int D, bool CLOSED, bool TOE, bool DIAG>
+__device__ __forceinline__ void tile_walk_f(const TileF& t, int ma, int a, int Nb, int nj,
+                                            const float4* __restrict__ sBg, const float4* __restrict__ sBw,
+                                            const int4* __restrict__ sBr, const int* __restrict__ sGs,
+                                            const float* __restrict__ sT, float* __restrict__ row) {
+    constexpr int D1 = D + 1;
+    constexpr int NV = (D1 + 3) / 4;
+    const NodeF na = t.nodes[ma];
+    const float cdiag = na.lnJ * 2.88539008177792681f;    // K1(s,s) = ln J in base-2 units (x 2 / ln 2)
+    const float ccorner = cdiag - 2.0f;                    // ln J - ln 2 in the same units
+    float acc[D1];
+#pragma unroll
+    for (int r = 0; r < D1; ++r) acc[r] = 0.0f;
+    int jcur = sBr[0].y;
+    const int G = sBr[Nb - 1].y - jcur + 1;
+    constexpr int kPre = TOE ? 1 : 4;                      // singular weights in flight (general tiles)
+    float wq[kPre];
+    if (!TOE) {
+#pragma unroll
+        for (int q = 0; q < kPre; ++q) wq[q] = (q < Nb) ? ws_at(t.ws, ma, sBr[q].x) : 0.0f;
+    }
+    for (int k = 0; k < G; ++k) {
+        if (k > 0) {
+            if (jcur >= 0 && jcur < nj) row[jcur] = acc[0];
+#pragma unroll
+            for (int r = 0; r < D; ++r) acc[r] = acc[r + 1];
+            acc[D] = 0.0f;
+            ++jcur;
+        }
+        const int ve = sGs[k + 1];
+        for (int v = sGs[k]; v < ve; ++v) {
+            const int4 br = sBr[v];
+            float ws;
+            if (TOE) {
+                ws = sT[br.z + a];
+            } else {
+                ws = wq[0];
+#pragma unroll
+                for (int q = 0; q < kPre - 1; ++q) wq[q] = wq[q + 1];
+                wq[kPre - 1] = (v + kPre < Nb) ? ws_at(t.ws, ma, sBr[v + kPre].x) : 0.0f;
+            }
+            const float4 g0 = sBg[2 * v], g1 = sBg[2 * v + 1];
+            const float dx = (g0.x - na.xh) + (g0.y - na.xl);
+            const float dy = (g0.z - na.yh) + (g0.w - na.yl);
+            float Dd = (g1.x - na.eh) + (g1.y - na.el);
+            // x + L and L - x as sums of non-negative numbers: the high parts
+            // alone keep FP32 relative accuracy
+            if (CLOSED) Dd *= (g1.x + na.ebh) * (g1.z + na.eh);
+            float c0 = log2_pos(__fdividef(fmaf(dx, dx, dy * dy), Dd * Dd));
+            if (DIAG) c0 = (br.x == ma) ? cdiag : c0;
+            if (CLOSED && !TOE) c0 = (ma + br.x == t.Nq - 1 && (ma == 0 || br.x == 0)) ? ccorner : c0;
+            float w[2][4 * NV];
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    const float4 t4 = sBw[(2 * v + kk) * NV + q];
+                    w[kk][4 * q] = t4.x; w[kk][4 * q + 1] = t4.y; w[kk][4 * q + 2] = t4.z; w[kk][4 * q + 3] = t4.w;
+                }
+#pragma unroll
+            for (int r = 0; r < D1; ++r) acc[r] = fmaf(w[0][r], c0, fmaf(w[1][r], ws, acc[r]));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < D1; ++r)
+        if (jcur + r >= 0 && jcur + r < nj) row[jcur + r] = acc[r];
+}
+
 template <int D, bool CLOSED, int TI>
 __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned char* smem) {
+    static_assert(TI <= 32, "stage 2 maps one lane to one column of the tile");
     constexpr int D1 = D + 1;
     constexpr int NV = (D1 + 3) / 4;                   // float4s per weight row
     const int n = t.n, Nq = t.Nq, maxr = t.maxr;
-    const float invL2 = t.invL2;
     const int* __restrict__ lo = t.lo;
     const int* __restrict__ hi = t.hi;
     const int* __restrict__ jfirst = t.jfirst;
-    const NodeF* __restrict__ nodes = t.nodes;
     const float* __restrict__ P = t.P;
     const float* __restrict__ Q = t.Q;
     const WsView<float> wsv = t.ws;
@@ -227,24 +305,33 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
     const int ni = min(TI, n - i0), nj = min(TI, n - j0);
     const int uA0 = lo[i0], Na = hi[i0 + ni - 1] - uA0 + 1;
     const int uB0 = lo[j0], Nb = hi[j0 + nj - 1] - uB0 + 1;
-    // 16-byte records first, then 8-, then 4-byte arrays: every offset stays
-    // aligned for any maxr
+    // block-uniform tile classes: every node where W^s is a Toeplitz
+    // sequence; A- and B-ranges sharing a node (mod Nq)
+    const bool toe = uB0 >= wsv.B && uB0 + Nb <= Nq - wsv.B && uA0 >= wsv.R && uA0 + Na <= Nq - wsv.R;
+    bool diag = false;
+    for (int k = -1; k <= 1; ++k)
+        diag |= uA0 < uB0 + k * Nq + Nb && uB0 + k * Nq < uA0 + Na;
+    const int tlen = Na + Nb - 1;
+    // 16-byte records first, then 4-byte arrays: every offset stays aligned
+    // for any maxr
     float4* sBg = (float4*)smem;                       // [maxr][2]: (xh, xl, yh, yl), (eh, el, ebh, ebl)
-    float4* sBw = sBg + 2 * maxr;                      // [maxr][2 NV]: P row, Q row (zero padded)
-    int2* sBm = (int2*)(sBw + 2 * NV * maxr);          // [maxr]: (m, first column - j0)
-    int* sJA = (int*)(sBm + maxr);                     // [maxr]
+    float4* sBw = sBg + 2 * maxr;                      // [maxr][2 NV]: P ln2/2 row, Q row (zero padded)
+    int4* sBr = (int4*)(sBw + 2 * NV * maxr);          // [maxr]: (m, first column - j0, Toeplitz offset, 0)
+    int* sJA = (int*)(sBr + maxr);                     // [maxr]
     float* sPA = (float*)(sJA + maxr);                 // [maxr][D1]
-    float* sS1 = sPA + maxr * D1;                      // [maxr][TI + 1]
+    float* sT = sPA + maxr * D1;                       // [2][Na + Nb - 1] (Toeplitz tiles)
+    int* sGs = (int*)(sT + 4 * maxr);                  // [TI + D + 2] first B node of each column group
+    float* sS1 = (float*)(sGs + TI + D + 2);           // [maxr][TI + 1]
 
     for (int v = threadIdx.x; v < Nb; v += blockDim.x) {
         const int u = uB0 + v, m = pmod(u, Nq), per = pdiv(u, Nq);
-        const NodeF b = nodes[m];
+        const NodeF b = t.nodes[m];
         sBg[2 * v] = make_float4(b.xh, b.xl, b.yh, b.yl);
         sBg[2 * v + 1] = make_float4(b.eh, b.el, b.ebh, b.ebl);
         float w[2][4 * NV];
 #pragma unroll
         for (int r = 0; r < 4 * NV; ++r) {
-            w[0][r] = r < D1 ? P[m * D1 + r] : 0.0f;
+            w[0][r] = r < D1 ? P[m * D1 + r] * 0.346573590279972655f : 0.0f;   // x ln2 / 2
             w[1][r] = r < D1 ? Q[m * D1 + r] : 0.0f;
         }
 #pragma unroll
@@ -252,79 +339,77 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
 #pragma unroll
             for (int q = 0; q < NV; ++q)
                 sBw[(2 * v + k) * NV + q] = make_float4(w[k][4 * q], w[k][4 * q + 1], w[k][4 * q + 2], w[k][4 * q + 3]);
-        sBm[v] = make_int2(m, jfirst[m] + n * per - j0);
+        // W^s[ma][mb] = T[(mb - B) & 1][ma - mb + Nq - 1] = sT[offset + a]
+        const int off = ((m - wsv.B) & 1) * tlen + (Nb - 1) - v;
+        sBr[v] = make_int4(m, jfirst[m] + n * per - j0, off, 0);
     }
     for (int v = threadIdx.x; v < Na; v += blockDim.x) {
         const int u = uA0 + v, m = pmod(u, Nq), per = pdiv(u, Nq);
         sJA[v] = jfirst[m] + n * per - i0;
         for (int r = 0; r < D1; ++r) sPA[v * D1 + r] = P[m * D1 + r];
     }
+    if (toe) {
+        const int tbase = (uA0 - uB0) - (Nb - 1) + Nq - 1;      // sequence index of window entry 0
+        const size_t slen = 2 * (size_t)Nq - 1;
+        for (int k = threadIdx.x; k < 2 * tlen; k += blockDim.x) {
+            const int p = k >= tlen, kk = k - p * tlen;
+            sT[k] = wsv.toe[p * slen + tbase + kk];
+        }
+    }
+    __syncthreads();
+    // column groups: the B nodes whose first column is jrel_0 + k start at
+    // sGs[k] (empty groups repeat the next start); sGs[G] = Nb
+    for (int v = threadIdx.x; v < Nb; v += blockDim.x) {
+        const int j0r = sBr[0].y;
+        const int k1 = sBr[v].y - j0r, k0 = (v == 0) ? -1 : sBr[v - 1].y - j0r;
+        for (int k = k0 + 1; k <= k1; ++k) sGs[k] = v;
+        if (v == Nb - 1) sGs[k1 + 1] = Nb;
+    }
     __syncthreads();
 
     for (int a = threadIdx.x; a < Na; a += blockDim.x) {
         const int ma = pmod(uA0 + a, Nq);
-        const NodeF na = nodes[ma];
-        const float lnJ = na.lnJ;
-        float acc[D1];
-#pragma unroll
-        for (int r = 0; r < D1; ++r) acc[r] = 0.0f;
-        int jcur = sBm[0].y;
         float* row = sS1 + a * (TI + 1);
-        // singular weights of the next kPre pairs in flight (ring in registers)
-        constexpr int kPre = 4;
-        float wq[kPre];
-#pragma unroll
-        for (int q = 0; q < kPre; ++q) wq[q] = (q < Nb) ? ws_at(wsv, ma, sBm[q].x) : 0.0f;
-        for (int v = 0; v < Nb; ++v) {
-            const int2 bm = sBm[v];
-            const float ws = wq[0];
-#pragma unroll
-            for (int q = 0; q < kPre - 1; ++q) wq[q] = wq[q + 1];
-            wq[kPre - 1] = (v + kPre < Nb) ? ws_at(wsv, ma, sBm[v + kPre].x) : 0.0f;
-            while (jcur < bm.y) {
-                if (jcur >= 0 && jcur < nj) row[jcur] = acc[0];
-#pragma unroll
-                for (int r = 0; r < D; ++r) acc[r] = acc[r + 1];
-                acc[D] = 0.0f;
-                ++jcur;
-            }
-            const float4 g0 = sBg[2 * v], g1 = sBg[2 * v + 1];
-            const float dx = (g0.x - na.xh) + (g0.y - na.xl);
-            const float dy = (g0.z - na.yh) + (g0.w - na.yl);
-            float Dd = fabsf((g1.x - na.eh) + (g1.y - na.el));
-            if (CLOSED) Dd *= ((g1.x + na.ebh) + (g1.y + na.ebl)) * ((g1.z + na.eh) + (g1.w + na.el)) * invL2;
-            float c0 = 0.5f * ln_pos(__fdividef(dx * dx + dy * dy, Dd * Dd));
-            const int mb = bm.x;
-            c0 = (mb == ma) ? lnJ : c0;
-            if (CLOSED) c0 = (ma + mb == Nq - 1 && (ma == 0 || mb == 0)) ? lnJ - 0.693147180559945309f : c0;
-            float w[2][4 * NV];
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-#pragma unroll
-                for (int q = 0; q < NV; ++q) {
-                    const float4 t4 = sBw[(2 * v + k) * NV + q];
-                    w[k][4 * q] = t4.x; w[k][4 * q + 1] = t4.y; w[k][4 * q + 2] = t4.z; w[k][4 * q + 3] = t4.w;
-                }
-#pragma unroll
-            for (int r = 0; r < D1; ++r) acc[r] = fmaf(w[0][r], c0, fmaf(w[1][r], ws, acc[r]));
+        if (toe) {
+            if (diag) tile_walk_f<D, CLOSED, true, true>(t, ma, a, Nb, nj, sBg, sBw, sBr, sGs, sT, row);
+            else tile_walk_f<D, CLOSED, true, false>(t, ma, a, Nb, nj, sBg, sBw, sBr, sGs, sT, row);
+        } else {
+            tile_walk_f<D, CLOSED, false, true>(t, ma, a, Nb, nj, sBg, sBw, sBr, sGs, sT, row);
         }
-#pragma unroll
-        for (int r = 0; r < D1; ++r)
-            if (jcur + r >= 0 && jcur + r < nj) row[jcur + r] = acc[r];
     }
     __syncthreads();
 
+    // stage 2: A[i][j] = -(1/2pi) sum_a P[a][i - jA(a)] S1[a][j].  Each warp
+    // owns a run of rows and one column per lane, and walks the A nodes of
+    // those rows once with a window of d+1 row sums (rows jA(a)..jA(a)+d).
     const float scale = (float)(-1.0 / (2.0 * kPi));
-    for (int idx = threadIdx.x; idx < ni * nj; idx += blockDim.x) {
-        const int il = idx / nj, jl = idx % nj;
-        const int i = i0 + il;
-        const int a0 = lo[i] - uA0, a1 = hi[i] - uA0;
-        float s = 0.0f;
-        for (int b = a0; b <= a1; ++b) {
-            const int r = il - sJA[b];
-            if (r >= 0 && r <= D) s += sPA[b * D1 + r] * sS1[b * (TI + 1) + jl];
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int RW = (ni + nw - 1) / nw;
+    const int r0 = w * RW, r1 = min(ni, r0 + RW);
+    if (r0 < r1) {
+        const int bs = lo[i0 + r0] - uA0, be = hi[i0 + r1 - 1] - uA0;
+        float acc[D1];
+#pragma unroll
+        for (int r = 0; r < D1; ++r) acc[r] = 0.0f;
+        int jc = sJA[bs];
+        float* Arow = t.A + (size_t)i0 * t.ld + j0 + lane;
+        const bool col = lane < nj;
+        for (int b = bs; b <= be; ++b) {
+            const int jb = sJA[b];
+            while (jc < jb) {
+                if (col && jc >= r0 && jc < r1) Arow[(size_t)jc * t.ld] = scale * acc[0];
+#pragma unroll
+                for (int r = 0; r < D; ++r) acc[r] = acc[r + 1];
+                acc[D] = 0.0f;
+                ++jc;
+            }
+            const float s1 = col ? sS1[b * (TI + 1) + lane] : 0.0f;
+#pragma unroll
+            for (int r = 0; r < D1; ++r) acc[r] = fmaf(sPA[b * D1 + r], s1, acc[r]);
         }
-        t.A[(size_t)i * t.ld + j0 + jl] = scale * s;
+#pragma unroll
+        for (int r = 0; r < D1; ++r)
+            if (col && jc + r >= r0 && jc + r < r1) Arow[(size_t)(jc + r) * t.ld] = scale * acc[r];
     }
 }
 
@@ -336,13 +421,13 @@ __global__ void __launch_bounds__(1024) k_assemble_f(const TileF t) {
 
 size_t tile_smem_f(int maxr, int d, int TI) {
     const int NV = (d + 1 + 3) / 4;
-    return (size_t)maxr * (2 + 2 * NV) * 16 + (size_t)maxr * (d + 1) * 4 + (size_t)maxr * (TI + 1) * 4 +
-           (size_t)maxr * 8 + (size_t)maxr * 4 + 64;
+    return (size_t)maxr * (2 + 2 * NV) * 16 + (size_t)maxr * 16 + (size_t)maxr * 4 + (size_t)maxr * (d + 1) * 4 +
+           (size_t)maxr * 4 * 4 + (size_t)(TI + d + 2) * 4 + (size_t)maxr * (TI + 1) * 4 + 64;
 }
 
 TileF tile_args_f(igs_prob p, int maxr) {
     const Plan& P = p->plan;
-    return TileF{P.n, P.Nq, (float)(1.0 / (P.L * P.L)), p->d_lo, p->d_hi, p->d_jfirst, (const NodeF*)p->d_nodes,
+    return TileF{P.n, P.Nq, p->d_lo, p->d_hi, p->d_jfirst, (const NodeF*)p->d_nodes,
                  (const float*)p->d_P, (const float*)p->d_Q,
                  WsView<float>{p->d_WsT32, p->d_WsRow32, p->d_WsToe32, P.Nq, p->ws_B, p->ws_R}, (float*)p->d_A,
                  (int64_t)P.n, maxr};
@@ -384,7 +469,7 @@ static void launch_tile(igs_prob p, int maxr, cudaStream_t s) {
     const bool f32 = std::is_same<T, float>::value;
     const WsView<T> ws{f32 ? (const T*)p->d_WsT32 : (const T*)p->d_WsT, f32 ? (const T*)p->d_WsRow32 : (const T*)p->d_WsRow,
                        f32 ? (const T*)p->d_WsToe32 : (const T*)p->d_WsToe, P.Nq, p->ws_B, p->ws_R};
-    kern<<<grid, 256, sm, s>>>(P.n, P.Nq, P.closed, (T)(1.0 / (P.L * P.L)), p->d_lo, p->d_hi, p->d_jfirst,
+    kern<<<grid, 256, sm, s>>>(P.n, P.Nq, P.closed, (T)(f32 ? 1.0 : 1.0 / (P.L * P.L)), p->d_lo, p->d_hi, p->d_jfirst,
                                (const typename NodeOf<T>::type*)p->d_nodes, (const T*)p->d_P, (const T*)p->d_Q, ws,
                                (T*)p->d_A, (int64_t)P.n, maxr);
     IGS_CUDA(cudaGetLastError());

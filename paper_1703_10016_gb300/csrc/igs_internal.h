@@ -131,6 +131,7 @@ struct igs_prob_s {
     void* d_diagLinv = nullptr;   // [n][64] inverses of the diagonal blocks of L (tier type)
     cudaGraphExec_t factor_exec = nullptr;   // captured factorisation (fixed pointers and sizes)
     int* d_tflags = nullptr;      // [n/64] per-block completion flags of the triangular solves
+    unsigned long long* d_tpub = nullptr;  // [8][n] published FP32 solution words (value, epoch)
     int tepoch = 0;               // flag value of the current triangular solve
     bool coop_ok = false;         // cooperative launch available
     double* d_As64 = nullptr;     // (A+A^T)/2 in FP64 for residuals (MIXED)
@@ -182,16 +183,18 @@ void rhs_prepare(igs_prob p);
 void rhs_build(igs_prob p, const double* d_uD, int nrhs);
 void rhs_build_noalloc(igs_prob p, const double* d_uD, int nrhs, double* d_beta);
 void solve_system(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double* resid);
+int wait_selftest(int device, double budget_s);   // 1: the bounded wait gave up
 }  // namespace igs
 
 // ------------------------------------------------------------- FP32 assembly
 namespace igs {
+// Coordinates x, y and parameter offsets e = eta - eta_0, eb = L - e, each
+// divided by L and held as float-float (hi, lo) pairs; ln J.
 struct NodeF { float xh, xl, yh, yl, eh, el, ebh, ebl, lnJ; };
 
 // One problem's FP32 assembly inputs (device pointers).
 struct TileF {
     int n, Nq;
-    float invL2;
     const int* lo;
     const int* hi;
     const int* jfirst;

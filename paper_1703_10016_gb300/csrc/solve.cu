@@ -577,19 +577,189 @@ static void launch_trsv_coop(int n, const T* F, const T* Linv, T* X, int nrhs, i
     }
 }
 
+// FP32 blocked triangular solve in one cooperative launch, blocks of 64 rows,
+// with the solution published as 64-bit words (value bits, epoch): a word is
+// written once, atomically, so a reader that sees the current epoch holds the
+// value it needs without a separate flag or fence.  Block blk waits on the
+// words of each earlier block (lower) or later block (upper) in turn, applies
+// that block's off-diagonal panel and finally its inverted diagonal block.
+// X holds the right-hand sides on entry and the solution on exit; pub is
+// [NR][n].  A wait that exceeds its budget (one second, or 2^22 polls) sets
+// *err and ends the kernel; the blocks waiting on it then run out of budget.
+__device__ __forceinline__ unsigned long long ld_word(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_word(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Wait until the word at w carries `tag` in its upper half; false after
+// `limit` polls or `ns` nanoseconds without it.
+__device__ __forceinline__ bool wait_word(const unsigned long long* w, unsigned long long tag, unsigned long long& v,
+                                          long long limit, unsigned long long ns) {
+    v = ld_word(w);
+    if ((v & 0xffffffff00000000ull) == tag) return true;
+    long long it = 0;
+    const unsigned long long t0 = global_ns();
+    do {
+        __nanosleep(20);
+        v = ld_word(w);
+        if (++it > limit || global_ns() - t0 > ns) return false;
+    } while ((v & 0xffffffff00000000ull) != tag);
+    return true;
+}
+
+// Self-test of the bounded wait: one thread waits for a tag that nothing
+// writes and records whether the wait gave up (1) or, impossibly, succeeded (0).
+__global__ void k_wait_probe(const unsigned long long* w, unsigned long long ns, int* status) {
+    unsigned long long v = 0;
+    *status = wait_word(w, 0xabcd000000000000ull, v, 1LL << 40, ns) ? 0 : 1;
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256) k_trsv_pk(int n, const float* __restrict__ F, const float* __restrict__ Linv,
+                                                 float* __restrict__ X, int lower, unsigned long long* pub,
+                                                 int epoch, int* __restrict__ err) {
+    __shared__ float acc[NR][kNB];
+    __shared__ float yin[NR][kNB];
+    const int tid = threadIdx.x;
+    const int nblk = (n + kNB - 1) / kNB;
+    const int i = tid / 4, part = tid % 4;          // row of the block, column phase
+    const unsigned long long tag = (unsigned long long)(unsigned)epoch << 32;
+    for (int J = blockIdx.x; J < nblk; J += gridDim.x) {
+        const int blk = lower ? J : nblk - 1 - J;
+        const int b0 = blk * kNB, bn = min(kNB, n - b0);
+        // this thread's slice of the inverted diagonal block, fetched before any wait:
+        // row i (lower) or column i (upper), entries l = part + 4 m
+        float lv[kNB / 4];
+#pragma unroll
+        for (int m = 0; m < kNB / 4; ++m) {
+            const int l = part + 4 * m;
+            if (lower) lv[m] = (i < bn) ? Linv[(size_t)(b0 + i) * kNB + l] : 0.0f;
+            else lv[m] = (l < bn && i < bn) ? Linv[(size_t)(b0 + l) * kNB + i] : 0.0f;
+        }
+        for (int idx = tid; idx < NR * kNB; idx += blockDim.x) {
+            const int k = idx / kNB, r = idx % kNB;
+            acc[k][r] = (r < bn) ? X[(size_t)k * n + b0 + r] : 0.0f;
+        }
+        const int ndep = lower ? blk : nblk - 1 - blk;
+        float fr[kNB / 4];                          // F[b0 + i][d0 + part + 4 m] of the next dependency
+        auto fetch = [&](int q) {
+            const int D = lower ? q : nblk - 1 - q;
+            const int d0 = D * kNB, dn = min(kNB, n - d0);
+#pragma unroll
+            for (int m = 0; m < kNB / 4; ++m) {
+                const int c = part + 4 * m;
+                fr[m] = (i < bn && c < dn) ? F[(size_t)(b0 + i) * n + d0 + c] : 0.0f;
+            }
+        };
+        if (ndep > 0) fetch(0);
+        __syncthreads();
+        for (int q = 0; q < ndep; ++q) {
+            const int D = lower ? q : nblk - 1 - q;
+            const int d0 = D * kNB, dn = min(kNB, n - d0);
+            int bad = 0;
+            for (int idx = tid; idx < NR * kNB; idx += blockDim.x) {
+                const int k = idx / kNB, c = idx % kNB;
+                float y = 0.0f;
+                if (c < dn) {
+                    unsigned long long v = 0;
+                    if (!wait_word(pub + (size_t)k * n + d0 + c, tag, v, kSpinLimit, kSpinNs)) bad = 1;
+                    y = __uint_as_float((unsigned)(v & 0xffffffffull));
+                }
+                yin[k][c] = y;
+            }
+            if (__syncthreads_or(bad)) {
+                if (tid == 0) atomicOr(err, 1);
+                return;
+            }
+            // acc[k][i] -= sum_c F[b0+i][d0+c] yin[k][c]  (four threads per row)
+            float sk[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                float v = 0.0f;
+#pragma unroll
+                for (int m = 0; m < kNB / 4; ++m) v += fr[m] * yin[k][part + 4 * m];
+                sk[k] = v;
+            }
+            if (q + 1 < ndep) fetch(q + 1);
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                float v = sk[k];
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                if (part == 0 && i < bn) acc[k][i] -= v;
+            }
+            __syncthreads();
+        }
+        // own block: y = Linv acc (lower) or Linv^T acc (upper), stored and published
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            float v = 0.0f;
+#pragma unroll
+            for (int m = 0; m < kNB / 4; ++m) v += lv[m] * acc[k][part + 4 * m];
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            if (part == 0 && i < bn) {
+                X[(size_t)k * n + b0 + i] = v;
+                st_word(pub + (size_t)k * n + b0 + i, tag | __float_as_uint(v));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int NR>
+static void pk_launch(int n, const float* F, const float* Linv, float* X, int lower, unsigned long long* pub,
+                      int epoch, int* err, cudaStream_t s) {
+    static int max_blocks = -1;                   // co-resident CTAs of this instantiation
+    if (max_blocks < 0) {
+        int dev = 0, sms = 0, per = 0;
+        IGS_CUDA(cudaGetDevice(&dev));
+        IGS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        IGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trsv_pk<NR>, 256, 0));
+        max_blocks = sms * per;
+    }
+    const int nblk = (n + kNB - 1) / kNB;
+    const int grid = std::max(1, std::min(nblk, max_blocks));
+    void* args[] = {(void*)&n, (void*)&F, (void*)&Linv, (void*)&X, (void*)&lower, (void*)&pub, (void*)&epoch,
+                    (void*)&err};
+    IGS_CUDA(cudaLaunchCooperativeKernel((void*)k_trsv_pk<NR>, dim3(grid), dim3(256), args, 0, s));
+}
+
+static void launch_trsv_pk(int n, const float* F, const float* Linv, float* X, int nrhs, int lower,
+                           unsigned long long* pub, int epoch, int* err, cudaStream_t s) {
+    switch (nrhs) {
+        case 1: pk_launch<1>(n, F, Linv, X, lower, pub, epoch, err, s); break;
+        case 2: pk_launch<2>(n, F, Linv, X, lower, pub, epoch, err, s); break;
+        case 3: pk_launch<3>(n, F, Linv, X, lower, pub, epoch, err, s); break;
+        case 4: pk_launch<4>(n, F, Linv, X, lower, pub, epoch, err, s); break;
+        case 5: pk_launch<5>(n, F, Linv, X, lower, pub, epoch, err, s); break;
+        case 6: pk_launch<6>(n, F, Linv, X, lower, pub, epoch, err, s); break;
+        case 7: pk_launch<7>(n, F, Linv, X, lower, pub, epoch, err, s); break;
+        default: pk_launch<8>(n, F, Linv, X, lower, pub, epoch, err, s); break;
+    }
+}
+
 // r = beta - As alpha (FP64), one warp per row; also |r|^2 and |beta|^2 per rhs.
-__global__ void k_resid(int n, int nrhs, const double* __restrict__ As, const double* __restrict__ alpha,
+template <int NR>
+__global__ void k_resid(int n, const double* __restrict__ As, const double* __restrict__ alpha,
                         const double* __restrict__ beta, double* __restrict__ r, double* __restrict__ norms) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
     if (warp >= n) return;
     const int i = warp;
-    double s[8];
-    for (int k = 0; k < nrhs; ++k) s[k] = 0.0;
+    double s[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) s[k] = 0.0;
     for (int j = lane; j < n; j += 32) {
         const double a = As[(size_t)i * n + j];
-        for (int k = 0; k < nrhs; ++k) s[k] += a * alpha[(size_t)k * n + j];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) s[k] = fma(a, alpha[(size_t)k * n + j], s[k]);
     }
-    for (int k = 0; k < nrhs; ++k) {
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
         double v = s[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) {
@@ -598,6 +768,21 @@ __global__ void k_resid(int n, int nrhs, const double* __restrict__ As, const do
             atomicAdd(&norms[2 * k], rv * rv);
             atomicAdd(&norms[2 * k + 1], beta[(size_t)k * n + i] * beta[(size_t)k * n + i]);
         }
+    }
+}
+
+static void launch_resid(int n, int nrhs, const double* As, const double* alpha, const double* beta, double* r,
+                         double* norms, cudaStream_t s) {
+    const dim3 g((n * 32 + 255) / 256), b(256);
+    switch (nrhs) {
+        case 1: k_resid<1><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
+        case 2: k_resid<2><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
+        case 3: k_resid<3><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
+        case 4: k_resid<4><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
+        case 5: k_resid<5><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
+        case 6: k_resid<6><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
+        case 7: k_resid<7><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
+        default: k_resid<8><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
     }
 }
 
@@ -921,6 +1106,10 @@ static void prepare_factor(igs_prob p, cudaStream_t s) {
         p->d_diagLinv = dev_alloc(p, sizeof(T) * (size_t)n * kNB);
         p->d_tflags = (int*)dev_alloc(p, sizeof(int) * ((n + kNB - 1) / kNB));
         IGS_CUDA(cudaMemsetAsync(p->d_tflags, 0, sizeof(int) * ((n + kNB - 1) / kNB), s));
+        if (std::is_same<T, float>::value) {
+            p->d_tpub = (unsigned long long*)dev_alloc(p, sizeof(unsigned long long) * 8 * (size_t)n);
+            IGS_CUDA(cudaMemsetAsync(p->d_tpub, 0, sizeof(unsigned long long) * 8 * (size_t)n, s));
+        }
         p->tepoch = 0;
         int dev = 0, coop = 0;
         IGS_CUDA(cudaGetDevice(&dev));
@@ -952,7 +1141,12 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
     IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s));
     for (;;) {
         k_cast_in<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, src, d_x, scale, n);
-        if (p->coop_ok) {
+        if (std::is_same<T, float>::value && p->coop_ok) {
+            launch_trsv_pk(n, (const float*)p->d_F, (const float*)p->d_diagLinv, (float*)d_x, nrhs, 1, p->d_tpub,
+                           ++p->tepoch, p->d_flag, s);
+            launch_trsv_pk(n, (const float*)p->d_F, (const float*)p->d_diagLinv, (float*)d_x, nrhs, 0, p->d_tpub,
+                           ++p->tepoch, p->d_flag, s);
+        } else if (p->coop_ok) {
             launch_trsv_coop<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 1, p->d_tflags,
                                 ++p->tepoch, p->d_flag, s);
             launch_trsv_coop<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 0, p->d_tflags,
@@ -963,7 +1157,7 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
         }
         k_accum<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, d_x, d_alpha, scale, n, it == 0);
         IGS_CUDA(cudaMemsetAsync(d_norm, 0, sizeof(double) * 2 * nrhs, s));
-        k_resid<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, nrhs, p->d_As64, d_alpha, d_beta, d_r, d_norm);
+        launch_resid(n, nrhs, p->d_As64, d_alpha, d_beta, d_r, d_norm, s);
         p->launches += 5;
         IGS_CUDA(cudaGetLastError());
         IGS_CUDA(cudaMemcpyAsync(hn.data(), d_norm, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, s));
@@ -994,6 +1188,23 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
     double worst = 0;
     for (int k = 0; k < nrhs; ++k) worst = std::max(worst, hn[2 * k + 1] > 0 ? std::sqrt(hn[2 * k] / hn[2 * k + 1]) : 0.0);
     if (worst > tol && max_it > 1) throw Error(IGS_E_NOT_CONVERGED, "iterative refinement did not reach 1e-10");
+}
+
+int wait_selftest(int device, double budget_s) {
+    IGS_CUDA(cudaSetDevice(device));
+    unsigned long long* d_w = nullptr;
+    int* d_st = nullptr;
+    IGS_CUDA(cudaMalloc(&d_w, sizeof(unsigned long long)));
+    IGS_CUDA(cudaMalloc(&d_st, sizeof(int)));
+    IGS_CUDA(cudaMemset(d_w, 0, sizeof(unsigned long long)));
+    IGS_CUDA(cudaMemset(d_st, 0xff, sizeof(int)));
+    k_wait_probe<<<1, 1>>>(d_w, (unsigned long long)(budget_s * 1e9), d_st);
+    IGS_CUDA(cudaGetLastError());
+    int st = -1;
+    IGS_CUDA(cudaMemcpy(&st, d_st, sizeof(int), cudaMemcpyDeviceToHost));
+    cudaFree(d_w);
+    cudaFree(d_st);
+    return st;
 }
 
 void solve_system(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double* resid) {

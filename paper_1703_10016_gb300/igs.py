@@ -37,7 +37,7 @@ EXPORTED = [
     "igs_get_matrix", "igs_batch_create", "igs_batch_destroy", "igs_batch_assemble", "igs_batch_tune", "igs_batch_set_config",
     "igs_batch_get_config",
     "igs_server_create", "igs_server_submit", "igs_server_wait", "igs_server_result", "igs_server_drain",
-    "igs_server_destroy",
+    "igs_server_destroy", "igs_selftest_wait",
 ]
 IGS_REQ_QUEUED, IGS_REQ_RUNNING, IGS_REQ_DONE, IGS_REQ_FAILED = 0, 1, 2, 3
 IGS_ORDER_NATURAL, IGS_ORDER_INTERLEAVED, IGS_ORDER_LARGEST_FIRST = 0, 1, 2
@@ -123,6 +123,7 @@ def _load() -> C.CDLL:
         "igs_server_result": [vp, i64, vp, vp, C.POINTER(igs_request_stats)],
         "igs_server_drain": [vp, i32],
         "igs_server_destroy": [vp],
+        "igs_selftest_wait": [vp, C.c_double, C.POINTER(i32)],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -307,6 +308,13 @@ def igs_get_node_geometry(prob):
     J = np.empty(nq)
     _check(_lib.igs_get_node_geometry(prob, _ptr(xy), _ptr(J)), "igs_get_node_geometry")
     return xy, J
+
+
+def igs_selftest_wait(ctx, budget_s=0.01):
+    """Run the bounded-wait self-test; returns 1 when the wait gave up by its budget."""
+    out = C.c_int(0)
+    _check(_lib.igs_selftest_wait(ctx, float(budget_s), C.byref(out)), "igs_selftest_wait")
+    return out.value
 
 
 # ------------------------------------------------------------------ batched form
