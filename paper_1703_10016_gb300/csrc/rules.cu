@@ -338,37 +338,74 @@ __global__ void __launch_bounds__(128) k_mu_tab(int NE, int M, int d, int den, i
 }
 
 // z = G^{-1} mu in place, one thread per column (node).  The last d values of
-// each substitution stay in a register window, so the only memory traffic on
-// the dependency chain is the streamed factor row and one store per step.
+// each substitution stay in a register window and the sum takes the most
+// recent value last, so one step's dependency chain is one FMA and one
+// multiply; the right-hand side is read a chunk ahead (those loads precede
+// the stores of the current chunk in program order, so they are issued
+// together instead of once per step).
+constexpr int kSubChunk = 8;
 template <int D>
 __device__ void gsolve_col(int NE, const double* __restrict__ L, const double* __restrict__ rd, double* __restrict__ Z,
                            int ldz, int c) {
-    double win[D + 1];
+    double win[D];
 #pragma unroll
-    for (int r = 0; r <= D; ++r) win[r] = 0.0;             // win[r] = z[j - r] after step j
-    for (int j = 0; j < NE; ++j) {
-        double s = Z[(size_t)j * ldz + c];
+    for (int r = 0; r < D; ++r) win[r] = 0.0;              // win[r] = z[j - 1 - r] before step j
+    double zc[kSubChunk];
 #pragma unroll
-        for (int r = 1; r <= D; ++r)
-            if (j - r >= 0) s -= L[j * (D + 1) + r] * win[r - 1];
-        const double v = s * rd[j];
+    for (int t = 0; t < kSubChunk; ++t) zc[t] = (t < NE) ? Z[(size_t)t * ldz + c] : 0.0;
+    for (int j0 = 0; j0 < NE; j0 += kSubChunk) {
+        double zn[kSubChunk];
 #pragma unroll
-        for (int r = D; r > 0; --r) win[r] = win[r - 1];
-        win[0] = v;
-        Z[(size_t)j * ldz + c] = v;
+        for (int t = 0; t < kSubChunk; ++t) {
+            const int j = j0 + kSubChunk + t;
+            zn[t] = (j < NE) ? Z[(size_t)j * ldz + c] : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < kSubChunk; ++t) {
+            const int j = j0 + t;
+            if (j < NE) {
+                double s = zc[t];
+#pragma unroll
+                for (int r = D; r >= 1; --r)
+                    if (j - r >= 0) s -= L[j * (D + 1) + r] * win[r - 1];
+                const double v = s * rd[j];
+#pragma unroll
+                for (int r = D - 1; r > 0; --r) win[r] = win[r - 1];
+                win[0] = v;
+                Z[(size_t)j * ldz + c] = v;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kSubChunk; ++t) zc[t] = zn[t];
     }
 #pragma unroll
-    for (int r = 0; r <= D; ++r) win[r] = 0.0;             // win[r] = y[j + r] after step j
-    for (int j = NE - 1; j >= 0; --j) {
-        double s = Z[(size_t)j * ldz + c];
+    for (int r = 0; r < D; ++r) win[r] = 0.0;              // win[r] = y[j + 1 + r] before step j
 #pragma unroll
-        for (int r = 1; r <= D; ++r)
-            if (j + r < NE) s -= L[(j + r) * (D + 1) + r] * win[r - 1];
-        const double v = s * rd[j];
+    for (int t = 0; t < kSubChunk; ++t) zc[t] = (NE - 1 - t >= 0) ? Z[(size_t)(NE - 1 - t) * ldz + c] : 0.0;
+    for (int j0 = NE - 1; j0 >= 0; j0 -= kSubChunk) {
+        double zn[kSubChunk];
 #pragma unroll
-        for (int r = D; r > 0; --r) win[r] = win[r - 1];
-        win[0] = v;
-        Z[(size_t)j * ldz + c] = v;
+        for (int t = 0; t < kSubChunk; ++t) {
+            const int j = j0 - kSubChunk - t;
+            zn[t] = (j >= 0) ? Z[(size_t)j * ldz + c] : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < kSubChunk; ++t) {
+            const int j = j0 - t;
+            if (j >= 0) {
+                double s = zc[t];
+#pragma unroll
+                for (int r = D; r >= 1; --r)
+                    if (j + r < NE) s -= L[(j + r) * (D + 1) + r] * win[r - 1];
+                const double v = s * rd[j];
+#pragma unroll
+                for (int r = D - 1; r > 0; --r) win[r] = win[r - 1];
+                win[0] = v;
+                Z[(size_t)j * ldz + c] = v;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kSubChunk; ++t) zc[t] = zn[t];
     }
 }
 
@@ -415,36 +452,76 @@ __global__ void k_ws(int Nq, int d, const int* __restrict__ fspan, const double*
 // caller).  The solution decays geometrically away from the column's
 // elements: each substitution stops once d+1 consecutive values are below
 // 1e-40 of the largest so far (the rest is zero to far below the 1e-20 cut
-// applied afterwards).
+// applied afterwards).  Register window and chunked reads as in gsolve_col.
+template <int D>
+__device__ void ycols_col(int NE, int e0, const double* __restrict__ bf, const double* __restrict__ L,
+                          const double* __restrict__ rd, double* __restrict__ y) {
+    double win[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) win[r] = 0.0;              // win[r] = y[j - 1 - r] (zero before e0)
+    double big = 0.0;
+    int small = 0, jstop = NE - 1;
+    for (int j = e0; j < NE; ++j) {
+        double s = (j - e0 <= D) ? bf[j - e0] : 0.0;
+#pragma unroll
+        for (int r = D; r >= 1; --r) s -= L[j * (D + 1) + r] * win[r - 1];
+        const double v = s * rd[j];
+#pragma unroll
+        for (int r = D - 1; r > 0; --r) win[r] = win[r - 1];
+        win[0] = v;
+        y[j] = v;
+        big = fmax(big, fabs(v));
+        small = (j > e0 + D && fabs(v) <= 1e-40 * big) ? small + 1 : 0;
+        if (small > D) { jstop = j; break; }
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r) win[r] = 0.0;              // win[r] = y[j + 1 + r] (zero past jstop)
+    small = 0;
+    double yc[kSubChunk];
+#pragma unroll
+    for (int t = 0; t < kSubChunk; ++t) yc[t] = (jstop - t >= 0) ? y[jstop - t] : 0.0;
+    for (int j0 = jstop; j0 >= 0; j0 -= kSubChunk) {
+        double yn[kSubChunk];
+#pragma unroll
+        for (int t = 0; t < kSubChunk; ++t) yn[t] = (j0 - kSubChunk - t >= 0) ? y[j0 - kSubChunk - t] : 0.0;
+        bool stop = false;
+#pragma unroll
+        for (int t = 0; t < kSubChunk; ++t) {
+            const int j = j0 - t;
+            if (j >= 0 && !stop) {
+                double s = yc[t];
+#pragma unroll
+                for (int r = D; r >= 1; --r)
+                    if (j + r <= jstop) s -= L[(j + r) * (D + 1) + r] * win[r - 1];
+                const double v = s * rd[j];
+#pragma unroll
+                for (int r = D - 1; r > 0; --r) win[r] = win[r - 1];
+                win[0] = v;
+                y[j] = v;
+                big = fmax(big, fabs(v));
+                small = (j < e0 && fabs(v) <= 1e-40 * big) ? small + 1 : 0;
+                stop = small > D;
+            }
+        }
+        if (stop) break;
+#pragma unroll
+        for (int t = 0; t < kSubChunk; ++t) yc[t] = yn[t];
+    }
+}
+
 __global__ void k_ycols(int ncols, int NE, int d, const int* __restrict__ cols, const int* __restrict__ fspan,
                         const double* __restrict__ Bf, const double* __restrict__ L, const double* __restrict__ rd,
                         double* __restrict__ Y) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncols) return;
     const int mp = cols[c], e0 = fspan[mp];
+    const double* bf = Bf + mp * (d + 1);
     double* y = Y + (size_t)c * NE;
-    double big = 0.0;
-    int small = 0, jstop = NE - 1;
-    for (int j = e0; j < NE; ++j) {
-        double s = (j - e0 <= d) ? Bf[mp * (d + 1) + (j - e0)] : 0.0;
-        const int p0 = (j - d > e0) ? j - d : e0;
-        for (int p = p0; p < j; ++p) s -= L[j * (d + 1) + (j - p)] * y[p];
-        const double v = s * rd[j];
-        y[j] = v;
-        big = fmax(big, fabs(v));
-        small = (j > e0 + d && fabs(v) <= 1e-40 * big) ? small + 1 : 0;
-        if (small > d) { jstop = j; break; }
-    }
-    small = 0;
-    for (int j = jstop; j >= 0; --j) {
-        double s = y[j];
-        const int p1 = (j + d < jstop) ? j + d : jstop;
-        for (int p = j + 1; p <= p1; ++p) s -= L[p * (d + 1) + (p - j)] * y[p];
-        const double v = s * rd[j];
-        y[j] = v;
-        big = fmax(big, fabs(v));
-        small = (j < e0 && fabs(v) <= 1e-40 * big) ? small + 1 : 0;
-        if (small > d) break;
+    switch (d) {
+        case 2: ycols_col<2>(NE, e0, bf, L, rd, y); break;
+        case 3: ycols_col<3>(NE, e0, bf, L, rd, y); break;
+        case 4: ycols_col<4>(NE, e0, bf, L, rd, y); break;
+        default: ycols_col<5>(NE, e0, bf, L, rd, y); break;
     }
 }
 
