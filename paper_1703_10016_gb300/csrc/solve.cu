@@ -58,6 +58,12 @@ constexpr int kPanelRows = 2 * kNB;                        // diagonal block + 6
 constexpr int kPanelParts = kPanelThreads / kPanelRows;   // threads per row in the update
 constexpr int kPB = 8;                                     // inner block width
 
+// Programmatic dependent launch: a kernel of the panel chain lets the next
+// one be scheduled at once (its CTAs park at the wait) and itself waits for
+// its predecessor's completion and memory before touching shared data.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
@@ -67,6 +73,8 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel(int n, T* __restrict__ 
                                                          T* __restrict__ diagL, int* __restrict__ flag) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T (*P)[kPB] = (T (*)[kPB])smem_raw;                     // current 8 columns of L, one row of 8 per row
     T (*a)[kNB + 1] = (T (*)[kNB + 1])(P + kPanelRows);    // rows 0..63 diagonal block, 64..127 rows below
@@ -217,6 +225,8 @@ __global__ void __launch_bounds__(256) k_syrk(int n, T* __restrict__ F, int k0, 
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
     constexpr int LD = syrk_ld<T>();
+    pdl_wait();
+    pdl_trigger();
     int ti, tj;
     if (mode == 1) {
         ti = blockIdx.x;
@@ -974,12 +984,28 @@ __global__ void __launch_bounds__(256) k_syrk_tc(int n, float* __restrict__ F, i
     }
 }
 
+// Launch with programmatic stream serialisation (see pdl_wait).
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    IGS_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+}
+
 template <typename T>
 static void launch_update(igs_prob p, int n, T* F, int k0, int kb, int mode, cudaStream_t s);
 template <>
 void launch_update<double>(igs_prob, int n, double* F, int k0, int kb, int mode, cudaStream_t s) {
     const int rem = n - k0 - kb, nt = (rem + kST - 1) / kST;
-    if (mode == 1) k_syrk<double><<<nt, 256, syrk_smem<double>(), s>>>(n, F, k0, kb, 1);
+    if (mode == 1) launch_pdl(k_syrk<double>, dim3(nt), dim3(256), syrk_smem<double>(), s, n, F, k0, kb, 1);
     else k_syrk<double><<<(nt - 1) * nt / 2, 256, syrk_smem<double>(), s>>>(n, F, k0, kb, 2);
 }
 // MIXED tier: the next panel's column block (on the critical path, few tiles) by the
@@ -989,7 +1015,8 @@ template <>
 void launch_update<float>(igs_prob p, int n, float* F, int k0, int kb, int mode, cudaStream_t s) {
     const int rem = n - k0 - kb;
     const int ntr = (rem + (int)tc::kM - 1) / (int)tc::kM, ntc = (rem + (int)tc::kN - 1) / (int)tc::kN;
-    if (mode == 1) k_syrk<float><<<(rem + kST - 1) / kST, 256, syrk_smem<float>(), s>>>(n, F, k0, kb, 1);
+    if (mode == 1)
+        launch_pdl(k_syrk<float>, dim3((rem + kST - 1) / kST), dim3(256), syrk_smem<float>(), s, n, F, k0, kb, 1);
     else k_syrk_tc<<<dim3(ntc - 1, ntr), 256, tc::smem_bytes(), s>>>(n, F, k0, kb, 2, p->d_flag);
 }
 
@@ -1008,8 +1035,8 @@ static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent
     for (int k0 = 0; k0 < n; k0 += kNB) {
         const int kb = std::min(kNB, n - k0);
         const int rows = n - k0;
-        k_panel<T><<<(rows + kNB - 1) / kNB, kPanelThreads, panel_smem<T>(), s0>>>(n, F, k0, kb, (T*)p->d_diagL,
-                                                                                 p->d_flag);
+        launch_pdl(k_panel<T>, dim3((rows + kNB - 1) / kNB), dim3(kPanelThreads), panel_smem<T>(), s0, n, F, k0, kb,
+                   (T*)p->d_diagL, p->d_flag);
         const int rem = n - k0 - kb;
         if (rem <= 0) continue;
         const int nt = (rem + kST - 1) / kST;

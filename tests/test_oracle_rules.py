@@ -155,6 +155,20 @@ def test_singular_rules_match_dense_minimum_norm():
     np.testing.assert_allclose(Ws @ Bc.T, Mu, atol=1e-13)
 
 
+@pytest.mark.parametrize("closed,nh,d,nref", [(True, 12, 3, 2), (False, 10, 4, 1), (True, 9, 5, 2),
+                                                (False, 11, 2, 3)])
+def test_singular_rules_centrosymmetric(closed, nh, d, nref):
+    """The nodes, the spline spaces and ln|u - v| are symmetric under the
+    reflection u -> a + b - u of the parameter interval, so the singular rules
+    are centrosymmetric: W^s[m][m'] = W^s[N-1-m][N-1-m'] (the GPU path builds
+    the right end of its stored rules from the left end by this identity)."""
+    a, b = (0.0, 1.0) if closed else (-1.0, 1.0)
+    disc = Discretization(a, b, nh, d, nref, closed)
+    np.testing.assert_allclose(disc.eta[::-1], a + b - disc.eta, rtol=0, atol=1e-15)
+    Ws = rules.singular_rules(disc)
+    assert np.max(np.abs(Ws - Ws[::-1, ::-1])) <= 1e-12 * np.max(np.abs(Ws))
+
+
 def test_table1_testdiff_error_decreases_and_is_below_printed_values():
     """Sect. 4.2, test 3 (eq. testdiff): the error of the singular rule on
     sqrt(1-t^2)/(t^2+25) decreases monotonically with N_h.  Table 1 prints
