@@ -235,6 +235,10 @@ __global__ void __launch_bounds__(256) k_syrk(int n, T* __restrict__ F, int k0, 
         tri_decode(blockIdx.x, ti, tj);
         ++ti;
         ++tj;
+    } else if (mode == 3) {                       // column tiles blockIdx.y < gridDim.y, all rows below
+        ti = blockIdx.x;
+        tj = blockIdx.y;
+        if (ti < tj) return;
     } else {
         tri_decode(blockIdx.x, ti, tj);
     }
@@ -984,6 +988,158 @@ __global__ void __launch_bounds__(256) k_syrk_tc(int n, float* __restrict__ F, i
     }
 }
 
+// Trailing update by a whole outer column block on the tensor cores (MIXED
+// tier, large n): F[i][j] -= sum_{l < kbo} F[i][K0+l] F[j][K0+l] for the lower
+// triangle of rows and columns >= base = K0 + kbo, 128 x 64 output tiles,
+// column tiles tj_off + blockIdx.x.  The K range is consumed in chunks of 64
+// staged as TF32 high/low parts (3xTF32, as k_syrk_tc) into one TMEM
+// accumulator, so C is read and written once per outer block instead of once
+// per panel.  The next chunk's loads are issued before the current chunk's
+// MMAs are waited for.
+__global__ void __launch_bounds__(256) k_syrk_tck(int n, float* __restrict__ F, int K0, int kbo, int tj_off,
+                                                  int* __restrict__ flag) {
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int base = K0 + kbo;
+    const int ti = blockIdx.y, tj = tj_off + blockIdx.x;
+    const int i0 = base + ti * (int)kM, j0 = base + tj * (int)kN;
+    if (j0 > i0 + (int)kM - 1 || j0 >= n) return;              // no lower-triangle entry in this tile
+    float* Ahi = (float*)smem_raw;
+    float* Alo = Ahi + kM * kK;
+    float* Bhi = Alo + kM * kK;
+    float* Blo = Bhi + kN * kK;
+    uint64_t* mbar = (uint64_t*)(Blo + kN * kK);
+    uint32_t* s_taddr = (uint32_t*)(mbar + 1);
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(su32(s_taddr)), "r"(kN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // staging layout as in k_syrk_tc: element (r, l) at float offset
+    // (((r/8)*(kK/4) + l/4)*8 + r%8)*4 + l%4
+    constexpr int kPA = (int)(kM * kK / 4) / 256, kPB = (int)(kN * kK / 4) / 256;
+    const int nch = (kbo + (int)kK - 1) / (int)kK;
+    const bool vec = (n & 3) == 0;
+    float4 v[kPA + kPB];
+    auto load = [&](int kc) {
+        const int c0 = K0 + kc * (int)kK;
+#pragma unroll
+        for (int q = 0; q < kPA + kPB; ++q) {
+            const bool isA = q < kPA;
+            const int idx = tid + (isA ? q : q - kPA) * 256;
+            const int rr = idx % 8, c = (idx / 8) % (kK / 4), r = (idx / (8 * (kK / 4))) * 8 + rr;
+            const int row = (isA ? i0 : j0) + r, col = c0 + 4 * c;
+            v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row < n) {
+                const float* src = F + (size_t)row * n + col;
+                if (vec && col + 3 < base) {
+                    v[q] = *(const float4*)src;
+                } else {
+                    v[q].x = (col + 0 < base) ? src[0] : 0.f;
+                    v[q].y = (col + 1 < base) ? src[1] : 0.f;
+                    v[q].z = (col + 2 < base) ? src[2] : 0.f;
+                    v[q].w = (col + 3 < base) ? src[3] : 0.f;
+                }
+            }
+        }
+    };
+    load(0);
+    const uint32_t lbo = 128, sbo = (kK / 4) * 128;
+    bool done = true;
+    uint32_t taddr = 0;
+    for (int kc = 0; kc < nch; ++kc) {
+#pragma unroll
+        for (int q = 0; q < kPA + kPB; ++q) {
+            const bool isA = q < kPA;
+            const int idx = tid + (isA ? q : q - kPA) * 256;
+            const int rr = idx % 8, c = (idx / 8) % (kK / 4), g = idx / (8 * (kK / 4));
+            float4 h, l;
+            h.x = tf32_hi(v[q].x); l.x = v[q].x - h.x;
+            h.y = tf32_hi(v[q].y); l.y = v[q].y - h.y;
+            h.z = tf32_hi(v[q].z); l.z = v[q].z - h.z;
+            h.w = tf32_hi(v[q].w); l.w = v[q].w - h.w;
+            const size_t off = ((size_t)(g * (kK / 4) + c) * 8 + rr) * 4;
+            *(float4*)((isA ? Ahi : Bhi) + off) = h;
+            *(float4*)((isA ? Alo : Blo) + off) = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        taddr = *s_taddr;
+        if (tid == 0) {
+            for (uint32_t ks = 0; ks < kK / 8; ++ks) {
+                const uint32_t koff = ks * 256;                    // K = 8: two core matrices
+                const uint64_t ah = sdesc(su32(Ahi) + koff, lbo, sbo), al = sdesc(su32(Alo) + koff, lbo, sbo);
+                const uint64_t bh = sdesc(su32(Bhi) + koff, lbo, sbo), bl = sdesc(su32(Blo) + koff, lbo, sbo);
+                mma(taddr, ah, bh, (kc > 0 || ks > 0) ? 1u : 0u);
+                mma(taddr, ah, bl, 1u);
+                mma(taddr, al, bh, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(su32(mbar)));
+        }
+        if (kc + 1 < nch) load(kc + 1);                            // in flight while the MMAs run
+        bool ok = false;
+        for (long it = 0; it < (1L << 24) && !ok; ++it) {
+            uint32_t r;
+            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                         : "=r"(r) : "r"(su32(mbar)), "r"((uint32_t)(kc & 1)));
+            ok = r != 0;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!ok) {
+            done = false;
+            break;
+        }
+    }
+    if (!done && tid == 0) atomicOr(flag, 2);
+    // accumulator -> shared (over the operand tiles, no longer read)
+    float (*D)[kN + 1] = (float (*)[kN + 1])smem_raw;
+    if (done) {
+        const int rbase = (warp % 4) * 32, cbase = (warp / 4) * 32;
+#pragma unroll
+        for (int c0 = 0; c0 < 32; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t a = taddr + ((uint32_t)rbase << 16) + (uint32_t)(cbase + c0);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                         : "r"(a));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int q = 0; q < 16; ++q) D[rbase + lane][cbase + c0 + q] = __uint_as_float(r[q]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(*s_taddr), "r"(kN));
+    if (!done) return;
+    constexpr int kRows = (int)kM / 8;
+    float cv[kRows][2];
+#pragma unroll
+    for (int t = 0; t < kRows; ++t) {
+        const int i = i0 + warp + 8 * t;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + lane + 32 * h;
+            cv[t][h] = (i < n && j <= i) ? F[(size_t)i * n + j] : 0.0f;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kRows; ++t) {
+        const int rl = warp + 8 * t, i = i0 + rl;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h, j = j0 + c;
+            if (i < n && j <= i) F[(size_t)i * n + j] = cv[t][h] - D[rl][c];
+        }
+    }
+}
+
 // Launch with programmatic stream serialisation (see pdl_wait).
 template <typename... KArgs, typename... Args>
 static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
@@ -1063,6 +1219,81 @@ static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent
     IGS_CUDA(cudaGetLastError());
 }
 
+// MIXED tier, large n: the same panels, with the trailing update blocked by
+// outer column blocks of kOB = 4 panels.  Inside an outer block each panel
+// updates only the remaining columns of that block (SIMT, mode 3); after the
+// block's last panel the rest of the matrix is updated once with K = kOB on
+// the tensor cores.  Look-ahead as in issue_factor, one level up: the next
+// outer block's columns are updated first on s0; the rest of the outer update
+// runs on s1 beside the next outer block's panels, and the next outer step's
+// s0 update waits for it (both touch the columns after the next block).
+constexpr int kOB = 4 * kNB;
+constexpr int kBlockedMinN = 4096;
+
+static void tck_launch(int n, float* F, int K0, int kbo, int tj_off, int tcols, int* flag, cudaStream_t s) {
+    const int rem = n - K0 - kbo;
+    const int ntr = (rem + (int)tc::kM - 1) / (int)tc::kM;
+    if (tcols <= 0 || ntr <= 0) return;
+    k_syrk_tck<<<dim3(tcols, ntr), 256, tc::smem_bytes(), s>>>(n, F, K0, kbo, tj_off, flag);
+}
+
+static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evP, cudaEvent_t evB,
+                                 cudaEvent_t evJ) {
+    const int n = p->plan.n;
+    float* F = (float*)p->d_F;
+    IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s0));
+    bool pending = false, forked = false;
+    for (int K0 = 0; K0 < n; K0 += kOB) {
+        const int kbo = std::min(kOB, n - K0);
+        for (int k0 = K0; k0 < K0 + kbo; k0 += kNB) {
+            const int kb = std::min(kNB, n - k0);
+            const int rows = n - k0;
+            launch_pdl(k_panel<float>, dim3((rows + kNB - 1) / kNB), dim3(kPanelThreads), panel_smem<float>(), s0, n,
+                       F, k0, kb, (float*)p->d_diagL, p->d_flag);
+            const int inner = (K0 + kbo - (k0 + kb) + kST - 1) / kST;   // column tiles left in this block
+            if (inner > 0) {
+                const int nt = (n - k0 - kb + kST - 1) / kST;
+                launch_pdl(k_syrk<float>, dim3(nt, inner), dim3(256), syrk_smem<float>(), s0, n, F, k0, kb, 3);
+            }
+        }
+        const int rem = n - K0 - kbo;
+        if (rem <= 0) continue;
+        const int ntc = (rem + (int)tc::kN - 1) / (int)tc::kN;
+        const int first = std::min(ntc, kOB / (int)tc::kN);          // the next outer block's column tiles
+        if (ntc > first) IGS_CUDA(cudaEventRecord(evP, s0));
+        if (pending) {
+            IGS_CUDA(cudaStreamWaitEvent(s0, evB, 0));
+            pending = false;
+        }
+        tck_launch(n, F, K0, kbo, 0, first, p->d_flag, s0);
+        if (ntc > first) {
+            IGS_CUDA(cudaStreamWaitEvent(s1, evP, 0));
+            forked = true;
+            tck_launch(n, F, K0, kbo, first, ntc - first, p->d_flag, s1);
+            IGS_CUDA(cudaEventRecord(evB, s1));
+            pending = true;
+        }
+    }
+    if (forked) {
+        IGS_CUDA(cudaEventRecord(evJ, s1));
+        IGS_CUDA(cudaStreamWaitEvent(s0, evJ, 0));
+    }
+    k_finalize<float><<<dim3((n + 255) / 256, n), 256, 0, s0>>>(n, F, (const float*)p->d_diagL);
+    k_diag_inverse<float><<<(n + kNB - 1) / kNB, 256, 0, s0>>>(n, (const float*)p->d_diagL, (float*)p->d_diagLinv);
+    IGS_CUDA(cudaGetLastError());
+}
+
+static int factor_launches_blocked(int n) {
+    int c = 2;
+    for (int K0 = 0; K0 < n; K0 += kOB) {
+        const int kbo = std::min(kOB, n - K0);
+        for (int k0 = K0; k0 < K0 + kbo; k0 += kNB) c += (k0 + kNB < K0 + kbo) ? 2 : 1;
+        const int rem = n - K0 - kbo;
+        if (rem > 0) c += (rem > kOB) ? 2 : 1;
+    }
+    return c;
+}
+
 static int factor_launches(int n) {
     int c = 2;
     for (int k0 = 0; k0 < n; k0 += kNB) {
@@ -1079,6 +1310,8 @@ static void factor(igs_prob p, cudaStream_t s) {
     ensure_dyn_smem((const void*)k_panel<T>, (size_t)panel_smem<T>());
     ensure_dyn_smem((const void*)k_syrk<T>, (size_t)syrk_smem<T>());
     ensure_dyn_smem((const void*)k_syrk_tc, tc::smem_bytes());
+    ensure_dyn_smem((const void*)k_syrk_tck, tc::smem_bytes());
+    const bool blocked = std::is_same<T, float>::value && n >= kBlockedMinN;
     if (!p->factor_exec) {
         // capture the fixed launch sequence once, on two private streams
         cudaStream_t cs = nullptr, cs1 = nullptr;
@@ -1096,7 +1329,8 @@ static void factor(igs_prob p, cudaStream_t s) {
             for (cudaEvent_t& e : ev) IGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
             IGS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
             try {
-                issue_factor<T>(p, cs, cs1, ev[0], ev[1], ev[2]);
+                if (blocked) issue_factor_blocked(p, cs, cs1, ev[0], ev[1], ev[2]);
+                else issue_factor<T>(p, cs, cs1, ev[0], ev[1], ev[2]);
             } catch (...) {
                 cudaStreamEndCapture(cs, &graph);
                 if (graph) cudaGraphDestroy(graph);
@@ -1116,7 +1350,7 @@ static void factor(igs_prob p, cudaStream_t s) {
         }
     }
     IGS_CUDA(cudaGraphLaunch(p->factor_exec, s));
-    p->launches += factor_launches(n);
+    p->launches += blocked ? factor_launches_blocked(n) : factor_launches(n);
     int flag = 0;
     IGS_CUDA(cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     IGS_CUDA(cudaStreamSynchronize(s));

@@ -212,3 +212,25 @@ def test_invalid_arguments(ctx):
             g.igs_destroy_problem(prob)
     finally:
         g.igs_destroy_geometry(geom)
+
+
+def test_blocked_factor_large_n(ctx):
+    """MIXED tier at n = 4160 (>= 4096): the factorisation takes the path whose
+    trailing update is blocked by four panels on the tensor cores, with a
+    ragged last outer block (4160 = 16 x 256 + 64).  The refined solution must
+    satisfy the FP64 system of the assembled matrix, checked on the host."""
+    g = lib()
+    curve = wl.star_curve()
+    n, d, nref = 4160, 3, 1
+    p = Prob(ctx, curve, n, d, nref, g.IGS_MIXED)
+    try:
+        A = p.assemble()
+        xy = g.igs_rhs_points(p.prob)
+        beta = g.igs_build_rhs(p.prob, wl.Harmonic("log").value(xy[:, 0], xy[:, 1])[None, :])[0]
+        alpha, res = g.igs_solve(p.prob)
+        assert res[0] <= 1e-10
+        assert g.igs_problem_timing(p.prob).ir_iterations <= 4
+        As = 0.5 * (A + A.T)
+        assert np.linalg.norm(As @ alpha[0] - beta) <= 1e-9 * np.linalg.norm(beta)
+    finally:
+        p.close()
