@@ -32,7 +32,7 @@ SM_MAX_MHZ = 2070.0
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM read + write of one launch of the FP32 assembly kernel on this workload (ncu
 # capture summarised in profiles/ncu_assemble_f_star2048.md); None after the kernel changes
-ASSEMBLY_TRAFFIC_BYTES = 8.42e6
+ASSEMBLY_TRAFFIC_BYTES = 8.44e6
 
 
 def parse():
