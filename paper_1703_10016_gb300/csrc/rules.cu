@@ -463,8 +463,11 @@ __device__ void ycols_col(int NE, int e0, const double* __restrict__ bf, const d
     int small = 0, jstop = NE - 1;
     for (int j = e0; j < NE; ++j) {
         double s = (j - e0 <= D) ? bf[j - e0] : 0.0;
+        // only band entries of rows with a predecessor are read (the factor
+        // stores nothing left of column 0)
 #pragma unroll
-        for (int r = D; r >= 1; --r) s -= L[j * (D + 1) + r] * win[r - 1];
+        for (int r = D; r >= 1; --r)
+            if (j - r >= e0) s -= L[j * (D + 1) + r] * win[r - 1];
         const double v = s * rd[j];
 #pragma unroll
         for (int r = D - 1; r > 0; --r) win[r] = win[r - 1];
@@ -708,6 +711,7 @@ void rules_build(igs_prob p) {
     p->d_W = (double*)dev_alloc(p, sizeof(double) * Nq * D1);
     p->d_G = (double*)dev_alloc(p, sizeof(double) * NE * D1);
     double* d_L = (double*)dev_alloc(p, sizeof(double) * NE * D1);
+    IGS_CUDA(cudaMemsetAsync(d_L, 0, sizeof(double) * NE * D1, s));    // band entries left of column 0 stay 0
     IGS_CUDA(cudaMemsetAsync(p->d_W, 0, sizeof(double) * Nq * D1, s));
     IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s));
 
