@@ -132,6 +132,7 @@ struct igs_prob_s {
     cudaGraphExec_t factor_exec = nullptr;   // captured factorisation (fixed pointers and sizes)
     int* d_tflags = nullptr;      // [n/64] per-block completion flags of the triangular solves
     unsigned long long* d_tpub = nullptr;  // [8][n] published FP32 solution words (value, epoch)
+    float* d_timg = nullptr;      // two outer blocks of split factor columns (MIXED tier, n >= 4096)
     int tepoch = 0;               // flag value of the current triangular solve
     bool coop_ok = false;         // cooperative launch available
     double* d_As64 = nullptr;     // (A+A^T)/2 in FP64 for residuals (MIXED)

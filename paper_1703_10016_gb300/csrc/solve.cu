@@ -988,116 +988,141 @@ __global__ void __launch_bounds__(256) k_syrk_tc(int n, float* __restrict__ F, i
     }
 }
 
-// Trailing update by a whole outer column block on the tensor cores (MIXED
-// tier, large n): F[i][j] -= sum_{l < kbo} F[i][K0+l] F[j][K0+l] for the lower
-// triangle of rows and columns >= base = K0 + kbo, 128 x 64 output tiles,
-// column tiles tj_off + blockIdx.x.  The K range is consumed in chunks of 64
-// staged as TF32 high/low parts (3xTF32, as k_syrk_tc) into one TMEM
-// accumulator, so C is read and written once per outer block instead of once
-// per panel.  The next chunk's loads are issued before the current chunk's
-// MMAs are waited for.
-__global__ void __launch_bounds__(256) k_syrk_tck(int n, float* __restrict__ F, int K0, int kbo, int tj_off,
-                                                  int* __restrict__ flag) {
+// Outer-block operands for the tensor-core update, split once per outer block:
+// rows base .. base + 64 G2 - 1 of columns K0 .. K0 + kbo - 1 of F, as TF32
+// high and low parts, in the shared-memory image the MMA descriptors read
+// (K-major core matrices: element (r, l) of a 64-row group and a chunk of
+// kKC = 32 columns at float offset (((r/8)*8 + l/4)*8 + r%8)*4 + l%4).
+// img[(kc*2 + part)*G2 + g] is the 8 KB image of row group g, K chunk kc,
+// part 0 = high, 1 = low; rows >= n and columns >= K0 + kbo are zero.
+// Grid (G2, chunks).
+constexpr int kKC = 32;
+constexpr int kImgFloats = 64 * kKC;
+__global__ void __launch_bounds__(256) k_split_panel(int n, const float* __restrict__ F, int K0, int kbo, int base,
+                                                     int G2, float* __restrict__ img) {
+    const int g = blockIdx.x, kc = blockIdx.y;
+    float* hi = img + ((size_t)(kc * 2 + 0) * G2 + g) * kImgFloats;
+    float* lo = img + ((size_t)(kc * 2 + 1) * G2 + g) * kImgFloats;
+    for (int idx = threadIdx.x; idx < kImgFloats / 4; idx += blockDim.x) {
+        const int r8 = idx % 8, c = (idx / 8) % (kKC / 4), rg = idx / (8 * (kKC / 4));
+        const int row = base + g * 64 + rg * 8 + r8, col = K0 + kc * kKC + 4 * c;
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = (row < n && col + q < K0 + kbo) ? F[(size_t)row * n + col + q] : 0.0f;
+        float4 h, l;
+        h.x = tc::tf32_hi(v[0]); l.x = v[0] - h.x;
+        h.y = tc::tf32_hi(v[1]); l.y = v[1] - h.y;
+        h.z = tc::tf32_hi(v[2]); l.z = v[2] - h.z;
+        h.w = tc::tf32_hi(v[3]); l.w = v[3] - h.w;
+        reinterpret_cast<float4*>(hi)[idx] = h;                 // idx = ((rg*8 + c)*8 + r8)
+        reinterpret_cast<float4*>(lo)[idx] = l;
+    }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long it = 0; it < (1L << 24); ++it) {
+        uint32_t r;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(r) : "r"(bar), "r"(parity) : "memory");
+        if (r) return true;
+    }
+    return false;
+}
+
+// Trailing update by a whole outer column block (MIXED tier, n >= 4096):
+// F[i][j] -= sum_{l < kbo} F[i][K0+l] F[j][K0+l], lower triangle of rows and
+// columns >= base = K0 + kbo, 128 x 64 output tiles, column tiles tj_off +
+// blockIdx.x.  Operands come from the split images by bulk copies into two
+// shared-memory stages of 32-column chunks (chunk kc+1 loads while chunk kc
+// multiplies; 96 KB, two CTAs per SM); one
+// thread issues copies and MMAs (3xTF32 into one TMEM accumulator), all
+// threads run the epilogue.  Waits are bounded: on a timeout the kernel sets
+// *flag |= 2 and skips the update.
+__global__ void __launch_bounds__(256) k_syrk_tcb(int n, float* __restrict__ F, const float* __restrict__ img, int K0,
+                                                  int kbo, int G2, int tj_off, int* __restrict__ flag) {
     using namespace tc;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int base = K0 + kbo;
     const int ti = blockIdx.y, tj = tj_off + blockIdx.x;
     const int i0 = base + ti * (int)kM, j0 = base + tj * (int)kN;
     if (j0 > i0 + (int)kM - 1 || j0 >= n) return;              // no lower-triangle entry in this tile
-    float* Ahi = (float*)smem_raw;
-    float* Alo = Ahi + kM * kK;
-    float* Bhi = Alo + kM * kK;
-    float* Blo = Bhi + kN * kK;
-    uint64_t* mbar = (uint64_t*)(Blo + kN * kK);
-    uint32_t* s_taddr = (uint32_t*)(mbar + 1);
+    constexpr uint32_t kStageFloats = 2 * kM * kKC + 2 * kN * kKC;   // Ahi, Alo, Bhi, Blo
+    constexpr uint32_t kStageBytes = kStageFloats * 4;
+    float* stage0 = (float*)smem_raw;
+    uint64_t* bars = (uint64_t*)(stage0 + 2 * kStageFloats);   // full[2], empty[2]
+    uint32_t* s_taddr = (uint32_t*)(bars + 4);
+    int* s_bad = (int*)(s_taddr + 1);
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(su32(s_taddr)), "r"(kN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(mbar)), "r"(1));
+        for (int b = 0; b < 4; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(bars + b)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
+        *s_bad = 0;
     }
-    // staging layout as in k_syrk_tc: element (r, l) at float offset
-    // (((r/8)*(kK/4) + l/4)*8 + r%8)*4 + l%4
-    constexpr int kPA = (int)(kM * kK / 4) / 256, kPB = (int)(kN * kK / 4) / 256;
-    const int nch = (kbo + (int)kK - 1) / (int)kK;
-    const bool vec = (n & 3) == 0;
-    float4 v[kPA + kPB];
-    auto load = [&](int kc) {
-        const int c0 = K0 + kc * (int)kK;
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t taddr = *s_taddr;
+    const int nch = (kbo + kKC - 1) / kKC;
+    if (tid == 0) {
+        auto issue = [&](int kc, int st) {
+            float* sA = stage0 + (size_t)st * kStageFloats;
+            const uint32_t full = su32(bars + st);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(full), "r"(kStageBytes) : "memory");
+            const float* srcs[4] = {img + ((size_t)(kc * 2 + 0) * G2 + 2 * ti) * kImgFloats,
+                                    img + ((size_t)(kc * 2 + 1) * G2 + 2 * ti) * kImgFloats,
+                                    img + ((size_t)(kc * 2 + 0) * G2 + tj) * kImgFloats,
+                                    img + ((size_t)(kc * 2 + 1) * G2 + tj) * kImgFloats};
+            float* dsts[4] = {sA, sA + kM * kKC, sA + 2 * kM * kKC, sA + 2 * kM * kKC + kN * kKC};
+            const uint32_t sizes[4] = {kM * kKC * 4, kM * kKC * 4, kN * kKC * 4, kN * kKC * 4};
 #pragma unroll
-        for (int q = 0; q < kPA + kPB; ++q) {
-            const bool isA = q < kPA;
-            const int idx = tid + (isA ? q : q - kPA) * 256;
-            const int rr = idx % 8, c = (idx / 8) % (kK / 4), r = (idx / (8 * (kK / 4))) * 8 + rr;
-            const int row = (isA ? i0 : j0) + r, col = c0 + 4 * c;
-            v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (row < n) {
-                const float* src = F + (size_t)row * n + col;
-                if (vec && col + 3 < base) {
-                    v[q] = *(const float4*)src;
-                } else {
-                    v[q].x = (col + 0 < base) ? src[0] : 0.f;
-                    v[q].y = (col + 1 < base) ? src[1] : 0.f;
-                    v[q].z = (col + 2 < base) ? src[2] : 0.f;
-                    v[q].w = (col + 3 < base) ? src[3] : 0.f;
-                }
-            }
-        }
-    };
-    load(0);
-    const uint32_t lbo = 128, sbo = (kK / 4) * 128;
-    bool done = true;
-    uint32_t taddr = 0;
-    for (int kc = 0; kc < nch; ++kc) {
-#pragma unroll
-        for (int q = 0; q < kPA + kPB; ++q) {
-            const bool isA = q < kPA;
-            const int idx = tid + (isA ? q : q - kPA) * 256;
-            const int rr = idx % 8, c = (idx / 8) % (kK / 4), g = idx / (8 * (kK / 4));
-            float4 h, l;
-            h.x = tf32_hi(v[q].x); l.x = v[q].x - h.x;
-            h.y = tf32_hi(v[q].y); l.y = v[q].y - h.y;
-            h.z = tf32_hi(v[q].z); l.z = v[q].z - h.z;
-            h.w = tf32_hi(v[q].w); l.w = v[q].w - h.w;
-            const size_t off = ((size_t)(g * (kK / 4) + c) * 8 + rr) * 4;
-            *(float4*)((isA ? Ahi : Bhi) + off) = h;
-            *(float4*)((isA ? Alo : Blo) + off) = l;
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        taddr = *s_taddr;
-        if (tid == 0) {
-            for (uint32_t ks = 0; ks < kK / 8; ++ks) {
+            for (int q = 0; q < 4; ++q)
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             :: "r"(su32(dsts[q])), "l"(srcs[q]), "r"(sizes[q]), "r"(full) : "memory");
+        };
+        bool ok = true;
+        for (int kc = 0; kc < nch && kc < 2; ++kc) issue(kc, kc);
+        const uint32_t lbo = 128, sbo = (kKC / 4) * 128;
+        for (int kc = 0; kc < nch && ok; ++kc) {
+            const int st = kc & 1;
+            const uint32_t ph = (uint32_t)((kc >> 1) & 1);
+            if (!mbar_wait(su32(bars + st), ph)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const float* sA = stage0 + (size_t)st * kStageFloats;
+            const uint32_t aH = su32(sA), aL = su32(sA + kM * kKC), bH = su32(sA + 2 * kM * kKC),
+                           bL = su32(sA + 2 * kM * kKC + kN * kKC);
+            for (uint32_t ks = 0; ks < kKC / 8; ++ks) {
                 const uint32_t koff = ks * 256;                    // K = 8: two core matrices
-                const uint64_t ah = sdesc(su32(Ahi) + koff, lbo, sbo), al = sdesc(su32(Alo) + koff, lbo, sbo);
-                const uint64_t bh = sdesc(su32(Bhi) + koff, lbo, sbo), bl = sdesc(su32(Blo) + koff, lbo, sbo);
+                const uint64_t ah = sdesc(aH + koff, lbo, sbo), al = sdesc(aL + koff, lbo, sbo);
+                const uint64_t bh = sdesc(bH + koff, lbo, sbo), bl = sdesc(bL + koff, lbo, sbo);
                 mma(taddr, ah, bh, (kc > 0 || ks > 0) ? 1u : 0u);
                 mma(taddr, ah, bl, 1u);
                 mma(taddr, al, bh, 1u);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(su32(mbar)));
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(su32(bars + 2 + st)) : "memory");
+            if (kc + 2 < nch) {
+                if (!mbar_wait(su32(bars + 2 + st), ph)) { ok = false; break; }
+                issue(kc + 2, st);
+            }
         }
-        if (kc + 1 < nch) load(kc + 1);                            // in flight while the MMAs run
-        bool ok = false;
-        for (long it = 0; it < (1L << 24) && !ok; ++it) {
-            uint32_t r;
-            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                         : "=r"(r) : "r"(su32(mbar)), "r"((uint32_t)(kc & 1)));
-            ok = r != 0;
+        if (ok) {                                                  // the last commit covers every MMA
+            const int kl = nch - 1;
+            ok = mbar_wait(su32(bars + 2 + (kl & 1)), (uint32_t)((kl >> 1) & 1));
         }
-        asm volatile("tcgen05.fence::after_thread_sync;");
         if (!ok) {
-            done = false;
-            break;
+            *s_bad = 1;
+            atomicOr(flag, 2);
         }
     }
-    if (!done && tid == 0) atomicOr(flag, 2);
-    // accumulator -> shared (over the operand tiles, no longer read)
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const bool done = *s_bad == 0;
+    // accumulator -> shared (stage 0, no longer read by the tensor cores)
     float (*D)[kN + 1] = (float (*)[kN + 1])smem_raw;
     if (done) {
         const int rbase = (warp % 4) * 32, cbase = (warp / 4) * 32;
@@ -1116,7 +1141,7 @@ __global__ void __launch_bounds__(256) k_syrk_tck(int n, float* __restrict__ F, 
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(*s_taddr), "r"(kN));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(kN));
     if (!done) return;
     constexpr int kRows = (int)kM / 8;
     float cv[kRows][2];
@@ -1139,6 +1164,8 @@ __global__ void __launch_bounds__(256) k_syrk_tck(int n, float* __restrict__ F, 
         }
     }
 }
+
+constexpr size_t tcb_smem_bytes() { return 2 * (size_t)(2 * tc::kM * kKC + 2 * tc::kN * kKC) * 4 + 64; }
 
 // Launch with programmatic stream serialisation (see pdl_wait).
 template <typename... KArgs, typename... Args>
@@ -1230,11 +1257,18 @@ static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent
 constexpr int kOB = 4 * kNB;
 constexpr int kBlockedMinN = 4096;
 
-static void tck_launch(int n, float* F, int K0, int kbo, int tj_off, int tcols, int* flag, cudaStream_t s) {
+// The image buffers hold two outer blocks (alternating), so the split of
+// block k+1 does not overwrite what the rest-update of block k still reads;
+// the split of block k+2 comes after the s0 wait on that rest-update.
+static int tcb_groups(int n) { return 2 * ((n + (int)tc::kM - 1) / (int)tc::kM); }
+static size_t tcb_image_floats(int n) { return (size_t)(kOB / kKC) * 2 * tcb_groups(n) * kImgFloats; }
+
+static void tcb_launch(int n, float* F, const float* img, int K0, int kbo, int tj_off, int tcols, int* flag,
+                       cudaStream_t s) {
     const int rem = n - K0 - kbo;
     const int ntr = (rem + (int)tc::kM - 1) / (int)tc::kM;
     if (tcols <= 0 || ntr <= 0) return;
-    k_syrk_tck<<<dim3(tcols, ntr), 256, tc::smem_bytes(), s>>>(n, F, K0, kbo, tj_off, flag);
+    k_syrk_tcb<<<dim3(tcols, ntr), 256, tcb_smem_bytes(), s>>>(n, F, img, K0, kbo, 2 * ntr, tj_off, flag);
 }
 
 static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evP, cudaEvent_t evB,
@@ -1259,17 +1293,20 @@ static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, c
         const int rem = n - K0 - kbo;
         if (rem <= 0) continue;
         const int ntc = (rem + (int)tc::kN - 1) / (int)tc::kN;
+        const int G2 = 2 * ((rem + (int)tc::kM - 1) / (int)tc::kM);
+        float* img = p->d_timg + (size_t)((K0 / kOB) & 1) * tcb_image_floats(n);
+        k_split_panel<<<dim3(G2, (kbo + kKC - 1) / kKC), 256, 0, s0>>>(n, F, K0, kbo, K0 + kbo, G2, img);
         const int first = std::min(ntc, kOB / (int)tc::kN);          // the next outer block's column tiles
         if (ntc > first) IGS_CUDA(cudaEventRecord(evP, s0));
         if (pending) {
             IGS_CUDA(cudaStreamWaitEvent(s0, evB, 0));
             pending = false;
         }
-        tck_launch(n, F, K0, kbo, 0, first, p->d_flag, s0);
+        tcb_launch(n, F, img, K0, kbo, 0, first, p->d_flag, s0);
         if (ntc > first) {
             IGS_CUDA(cudaStreamWaitEvent(s1, evP, 0));
             forked = true;
-            tck_launch(n, F, K0, kbo, first, ntc - first, p->d_flag, s1);
+            tcb_launch(n, F, img, K0, kbo, first, ntc - first, p->d_flag, s1);
             IGS_CUDA(cudaEventRecord(evB, s1));
             pending = true;
         }
@@ -1289,7 +1326,7 @@ static int factor_launches_blocked(int n) {
         const int kbo = std::min(kOB, n - K0);
         for (int k0 = K0; k0 < K0 + kbo; k0 += kNB) c += (k0 + kNB < K0 + kbo) ? 2 : 1;
         const int rem = n - K0 - kbo;
-        if (rem > 0) c += (rem > kOB) ? 2 : 1;
+        if (rem > 0) c += (rem > kOB) ? 3 : 2;
     }
     return c;
 }
@@ -1310,7 +1347,7 @@ static void factor(igs_prob p, cudaStream_t s) {
     ensure_dyn_smem((const void*)k_panel<T>, (size_t)panel_smem<T>());
     ensure_dyn_smem((const void*)k_syrk<T>, (size_t)syrk_smem<T>());
     ensure_dyn_smem((const void*)k_syrk_tc, tc::smem_bytes());
-    ensure_dyn_smem((const void*)k_syrk_tck, tc::smem_bytes());
+    ensure_dyn_smem((const void*)k_syrk_tcb, tcb_smem_bytes());
     const bool blocked = std::is_same<T, float>::value && n >= kBlockedMinN;
     if (!p->factor_exec) {
         // capture the fixed launch sequence once, on two private streams
@@ -1367,6 +1404,8 @@ static void prepare_factor(igs_prob p, cudaStream_t s) {
         p->d_diagLinv = dev_alloc(p, sizeof(T) * (size_t)n * kNB);
         p->d_tflags = (int*)dev_alloc(p, sizeof(int) * ((n + kNB - 1) / kNB));
         IGS_CUDA(cudaMemsetAsync(p->d_tflags, 0, sizeof(int) * ((n + kNB - 1) / kNB), s));
+        if (std::is_same<T, float>::value && n >= kBlockedMinN)
+            p->d_timg = (float*)dev_alloc(p, sizeof(float) * 2 * tcb_image_floats(n));
         if (std::is_same<T, float>::value) {
             p->d_tpub = (unsigned long long*)dev_alloc(p, sizeof(unsigned long long) * 8 * (size_t)n);
             IGS_CUDA(cudaMemsetAsync(p->d_tpub, 0, sizeof(unsigned long long) * 8 * (size_t)n, s));
