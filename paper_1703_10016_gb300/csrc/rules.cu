@@ -340,72 +340,90 @@ __global__ void __launch_bounds__(128) k_mu_tab(int NE, int M, int d, int den, i
 // z = G^{-1} mu in place, one thread per column (node).  The last d values of
 // each substitution stay in a register window and the sum takes the most
 // recent value last, so one step's dependency chain is one FMA and one
-// multiply; the right-hand side is read a chunk ahead (those loads precede
-// the stores of the current chunk in program order, so they are issued
-// together instead of once per step).
+// multiply.  Everything a chunk of steps reads from memory (right-hand side,
+// factor band, reciprocal diagonal) is loaded one chunk ahead, before the
+// current chunk's stores, so no step waits on a memory round trip.
 constexpr int kSubChunk = 8;
+template <int D>
+struct SubChunk {
+    double z[kSubChunk];
+    double l[kSubChunk][D];
+    double rd[kSubChunk];
+};
+// forward: rows j0 .. j0+7, band entries L[j][r] (r = 1..D) of row j
+template <int D>
+__device__ __forceinline__ void sub_load_fwd(SubChunk<D>& c, int j0, int NE, const double* __restrict__ L,
+                                             const double* __restrict__ rd, const double* Z, int ldz, int col) {
+#pragma unroll
+    for (int t = 0; t < kSubChunk; ++t) {
+        const int j = j0 + t;
+        const bool in = j < NE;
+        c.z[t] = in ? Z[(size_t)j * ldz + col] : 0.0;
+        c.rd[t] = in ? rd[j] : 0.0;
+#pragma unroll
+        for (int r = 1; r <= D; ++r) c.l[t][r - 1] = (in && j - r >= 0) ? L[j * (D + 1) + r] : 0.0;
+    }
+}
+// backward: rows j0, j0-1, ..., band entries L[j+r][r] (column j of L)
+template <int D>
+__device__ __forceinline__ void sub_load_bwd(SubChunk<D>& c, int j0, int NE, const double* __restrict__ L,
+                                             const double* __restrict__ rd, const double* Z, int ldz, int col) {
+#pragma unroll
+    for (int t = 0; t < kSubChunk; ++t) {
+        const int j = j0 - t;
+        const bool in = j >= 0;
+        c.z[t] = in ? Z[(size_t)j * ldz + col] : 0.0;
+        c.rd[t] = in ? rd[j] : 0.0;
+#pragma unroll
+        for (int r = 1; r <= D; ++r) c.l[t][r - 1] = (in && j + r < NE) ? L[(j + r) * (D + 1) + r] : 0.0;
+    }
+}
 template <int D>
 __device__ void gsolve_col(int NE, const double* __restrict__ L, const double* __restrict__ rd, double* __restrict__ Z,
                            int ldz, int c) {
     double win[D];
+    SubChunk<D> cur, nxt;
 #pragma unroll
     for (int r = 0; r < D; ++r) win[r] = 0.0;              // win[r] = z[j - 1 - r] before step j
-    double zc[kSubChunk];
-#pragma unroll
-    for (int t = 0; t < kSubChunk; ++t) zc[t] = (t < NE) ? Z[(size_t)t * ldz + c] : 0.0;
+    sub_load_fwd<D>(cur, 0, NE, L, rd, Z, ldz, c);
     for (int j0 = 0; j0 < NE; j0 += kSubChunk) {
-        double zn[kSubChunk];
-#pragma unroll
-        for (int t = 0; t < kSubChunk; ++t) {
-            const int j = j0 + kSubChunk + t;
-            zn[t] = (j < NE) ? Z[(size_t)j * ldz + c] : 0.0;
-        }
+        sub_load_fwd<D>(nxt, j0 + kSubChunk, NE, L, rd, Z, ldz, c);
 #pragma unroll
         for (int t = 0; t < kSubChunk; ++t) {
             const int j = j0 + t;
             if (j < NE) {
-                double s = zc[t];
+                double s = cur.z[t];
 #pragma unroll
-                for (int r = D; r >= 1; --r)
-                    if (j - r >= 0) s -= L[j * (D + 1) + r] * win[r - 1];
-                const double v = s * rd[j];
+                for (int r = D; r >= 1; --r) s -= cur.l[t][r - 1] * win[r - 1];
+                const double v = s * cur.rd[t];
 #pragma unroll
                 for (int r = D - 1; r > 0; --r) win[r] = win[r - 1];
                 win[0] = v;
                 Z[(size_t)j * ldz + c] = v;
             }
         }
-#pragma unroll
-        for (int t = 0; t < kSubChunk; ++t) zc[t] = zn[t];
+        cur = nxt;
     }
 #pragma unroll
     for (int r = 0; r < D; ++r) win[r] = 0.0;              // win[r] = y[j + 1 + r] before step j
-#pragma unroll
-    for (int t = 0; t < kSubChunk; ++t) zc[t] = (NE - 1 - t >= 0) ? Z[(size_t)(NE - 1 - t) * ldz + c] : 0.0;
+    sub_load_bwd<D>(cur, NE - 1, NE, L, rd, Z, ldz, c);
     for (int j0 = NE - 1; j0 >= 0; j0 -= kSubChunk) {
-        double zn[kSubChunk];
-#pragma unroll
-        for (int t = 0; t < kSubChunk; ++t) {
-            const int j = j0 - kSubChunk - t;
-            zn[t] = (j >= 0) ? Z[(size_t)j * ldz + c] : 0.0;
-        }
+        sub_load_bwd<D>(nxt, j0 - kSubChunk, NE, L, rd, Z, ldz, c);
 #pragma unroll
         for (int t = 0; t < kSubChunk; ++t) {
             const int j = j0 - t;
             if (j >= 0) {
-                double s = zc[t];
+                double s = cur.z[t];
 #pragma unroll
-                for (int r = D; r >= 1; --r)
-                    if (j + r < NE) s -= L[(j + r) * (D + 1) + r] * win[r - 1];
-                const double v = s * rd[j];
+                for (int r = D; r >= 1; --r) s -= cur.l[t][r - 1] * win[r - 1];
+                const double v = s * cur.rd[t];
 #pragma unroll
                 for (int r = D - 1; r > 0; --r) win[r] = win[r - 1];
                 win[0] = v;
                 Z[(size_t)j * ldz + c] = v;
             }
         }
-#pragma unroll
-        for (int t = 0; t < kSubChunk; ++t) zc[t] = zn[t];
+        cur = nxt;
     }
 }
 
