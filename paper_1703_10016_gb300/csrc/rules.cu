@@ -2,6 +2,7 @@
 #include <cmath>
 #include <mutex>
 #include <set>
+#include <type_traits>
 
 #include "bspline_dev.cuh"
 #include "igs_internal.h"
@@ -439,6 +440,216 @@ __global__ void k_gsolve(int NE, int d, int ncol, const double* __restrict__ L, 
     }
 }
 
+// ------------------------------------------- partitioned solve with G = L L^T
+// Many-right-hand-side-free form of the two banded substitutions for a few
+// dense right-hand sides (the boundary rows of W^s): rows are split into P
+// blocks of kPart rows (the last block takes the remainder, so every block
+// has at least d rows).  Forward, block p: L_pp y_p = mu_p - L_p,p-1 y_p-1,
+// where L_p,p-1 reaches only the last d entries t_p-1 of y_p-1, so
+//     y_p = u_p - sum_k t_p-1[k] V_p[k],   u_p = L_pp^{-1} mu_p,
+//     V_p[k] = L_pp^{-1} (column m-k of L_p,p-1)   (k = 1..d, "spikes").
+// The spikes depend on L only; the local solves run in parallel over blocks;
+// only the d interface values per block are carried sequentially.  Backward
+// likewise with L^T and the first d entries of the next block.  Algebraically
+// this is the block form of the same substitutions (no truncation).
+constexpr int kPart = 64;
+
+__host__ __device__ inline int part_count(int NE) { return NE / kPart; }       // >= 1 when NE >= kPart
+__device__ __forceinline__ int part_len(int NE, int P, int p) { return p == P - 1 ? NE - p * kPart : kPart; }
+
+// V[(p*D + k-1)*2kPart + i] = V_p[k][i] (forward), W likewise (backward, k = 0..D-1)
+template <int D>
+__global__ void k_spikes(int NE, const double* __restrict__ L, const double* __restrict__ rd, double* __restrict__ V,
+                         double* __restrict__ W) {
+    const int P = part_count(NE);
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 2 * P * D) return;
+    const bool fwd = q < P * D;
+    const int p = (fwd ? q : q - P * D) / D, k = (fwd ? q : q - P * D) % D;
+    const int r0 = p * kPart, len = part_len(NE, P, p);
+    double* out = (fwd ? V : W) + (size_t)(p * D + k) * 2 * kPart;
+    double win[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) win[r] = 0.0;
+    if (fwd) {
+        if (p == 0) return;
+        // column (r0 - 1 - k) of L restricted to rows of block p: L[r0+i][r0-1-k], band offset i+1+k
+        for (int i = 0; i < len; ++i) {
+            const int j = r0 + i;
+            double s = (i + 1 + k <= D) ? L[j * (D + 1) + i + 1 + k] : 0.0;
+#pragma unroll
+            for (int r = D; r >= 1; --r)
+                if (i - r >= 0) s -= L[j * (D + 1) + r] * win[r - 1];
+            const double v = s * rd[j];
+#pragma unroll
+            for (int r = D - 1; r > 0; --r) win[r] = win[r - 1];
+            win[0] = v;
+            out[i] = v;
+        }
+    } else {
+        if (p == P - 1) return;
+        // row (r0 + len + k) of L restricted to columns of block p, transposed:
+        // rhs_i = L[r0+len+k][r0+i], band offset len+k-i
+        for (int i = len - 1; i >= 0; --i) {
+            const int j = r0 + i, off = len + k - i;
+            double s = (off <= D) ? L[(r0 + len + k) * (D + 1) + off] : 0.0;
+#pragma unroll
+            for (int r = D; r >= 1; --r)
+                if (i + r < len) s -= L[(j + r) * (D + 1) + r] * win[r - 1];
+            const double v = s * rd[j];
+#pragma unroll
+            for (int r = D - 1; r > 0; --r) win[r] = win[r - 1];
+            win[0] = v;
+            out[i] = v;
+        }
+    }
+}
+
+// Local substitutions in place, one thread per (block, column): forward
+// L_pp u_p = mu_p (dir 0) or backward L_pp^T u_p = y_p (dir 1), no coupling.
+template <int D>
+__global__ void k_part_local(int NE, int ncol, int dir, const double* __restrict__ L, const double* __restrict__ rd,
+                             double* __restrict__ Z, int ldz) {
+    const int P = part_count(NE);
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P * ncol) return;
+    const int p = q / ncol, c = q % ncol;
+    const int r0 = p * kPart, len = part_len(NE, P, p);
+    double win[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) win[r] = 0.0;
+    if (dir == 0) {
+        for (int i = 0; i < len; ++i) {
+            const int j = r0 + i;
+            double s = Z[(size_t)j * ldz + c];
+#pragma unroll
+            for (int r = D; r >= 1; --r)
+                if (i - r >= 0) s -= L[j * (D + 1) + r] * win[r - 1];
+            const double v = s * rd[j];
+#pragma unroll
+            for (int r = D - 1; r > 0; --r) win[r] = win[r - 1];
+            win[0] = v;
+            Z[(size_t)j * ldz + c] = v;
+        }
+    } else {
+        for (int i = len - 1; i >= 0; --i) {
+            const int j = r0 + i;
+            double s = Z[(size_t)j * ldz + c];
+#pragma unroll
+            for (int r = D; r >= 1; --r)
+                if (i + r < len) s -= L[(j + r) * (D + 1) + r] * win[r - 1];
+            const double v = s * rd[j];
+#pragma unroll
+            for (int r = D - 1; r > 0; --r) win[r] = win[r - 1];
+            win[0] = v;
+            Z[(size_t)j * ldz + c] = v;
+        }
+    }
+}
+
+// Interface values, one warp, lane (c, k) for columns c0 <= c < c0 + nc and
+// k < D (nc * D <= 32).  Forward: t_p[k] = y_p[len_p-1-k] = u_p[len_p-1-k] -
+// sum_k' V_p[k'][len_p-1-k] t_p-1[k'] for p = 1..P-1 (t_0 from u_0); the
+// values of t_p-1 come from the lanes of the same column by shuffles.
+// Backward: s_p[k] = z_p[k] = u_p[k] - sum_k' W_p[k'][k] s_p+1[k'] for
+// p = P-2..0.  T[(p*ncol + c)*D + k] receives the carried values.
+template <int D>
+__global__ void k_part_iface(int NE, int ncol, int c0, int nc, int dir, const double* __restrict__ Z, int ldz,
+                             const double* __restrict__ VW, double* __restrict__ T) {
+    const int P = part_count(NE);
+    const int lane = threadIdx.x;
+    const bool act = lane < nc * D;
+    const int c = c0 + (act ? lane / D : 0), k = act ? lane % D : 0;
+    const int base = lane - k;                                 // lane of (c, 0)
+    if (dir == 0) {
+        double t = act ? Z[(size_t)(kPart - 1 - k) * ldz + c] : 0.0;
+        if (act) T[(size_t)(0 * ncol + c) * D + k] = t;
+        for (int p = 1; p < P; ++p) {
+            const int r0 = p * kPart, len = part_len(NE, P, p);
+            const int i = len - 1 - k;
+            double s = act ? Z[(size_t)(r0 + i) * ldz + c] : 0.0;
+            double vk[D];
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) vk[kk] = act ? VW[(size_t)(p * D + kk) * 2 * kPart + i] : 0.0;
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) {
+                // t_p-1[kk + 1 in 1-based] = y_p-1[m - 1 - kk]: spike kk couples entry m-1-kk
+                const double tk = __shfl_sync(0xffffffffu, t, base + kk);
+                s -= vk[kk] * tk;
+            }
+            t = s;
+            if (act) T[(size_t)(p * ncol + c) * D + k] = t;
+        }
+    } else {
+        const int rl = (P - 1) * kPart;
+        double t = act ? Z[(size_t)(rl + k) * ldz + c] : 0.0;
+        if (act) T[(size_t)((P - 1) * ncol + c) * D + k] = t;
+        for (int p = P - 2; p >= 0; --p) {
+            const int r0 = p * kPart;
+            double s = act ? Z[(size_t)(r0 + k) * ldz + c] : 0.0;
+            double wk[D];
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) wk[kk] = act ? VW[(size_t)(p * D + kk) * 2 * kPart + k] : 0.0;
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) {
+                const double tk = __shfl_sync(0xffffffffu, t, base + kk);
+                s -= wk[kk] * tk;
+            }
+            t = s;
+            if (act) T[(size_t)(p * ncol + c) * D + k] = t;
+        }
+    }
+}
+
+// Corrections: forward y_p = u_p - sum_k V_p[k] t_p-1[k] (p >= 1); backward
+// z_p = u_p - sum_k W_p[k] s_p+1[k] (p <= P-2).  One thread per (row, column).
+template <int D>
+__global__ void k_part_correct(int NE, int ncol, int dir, const double* __restrict__ VW, const double* __restrict__ T,
+                               double* __restrict__ Z, int ldz) {
+    const int P = part_count(NE);
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)NE * ncol) return;
+    const int j = (int)(q / ncol), c = (int)(q % ncol);
+    const int p = min(j / kPart, P - 1), i = j - p * kPart;
+    const int pn = dir == 0 ? p - 1 : p + 1;                   // block whose interface values couple in
+    if (pn < 0 || pn >= P) return;
+    double s = Z[(size_t)j * ldz + c];
+#pragma unroll
+    for (int k = 0; k < D; ++k) s -= VW[(size_t)(p * D + k) * 2 * kPart + i] * T[(size_t)(pn * ncol + c) * D + k];
+    Z[(size_t)j * ldz + c] = s;
+}
+
+// z = G^{-1} z for ncol columns of Z (ldz), partitioned (NE >= 2 kPart).
+static void part_gsolve(igs_prob p, cudaStream_t s, int NE, int d, int ncol, const double* L, const double* rd,
+                        double* Z, int ldz, int& launches) {
+    const int P = part_count(NE);
+    double* V = (double*)dev_alloc(p, sizeof(double) * (size_t)P * d * 2 * kPart);
+    double* W = (double*)dev_alloc(p, sizeof(double) * (size_t)P * d * 2 * kPart);
+    double* T = (double*)dev_alloc(p, sizeof(double) * (size_t)P * ncol * d);
+    auto run = [&](auto dtag) {
+        constexpr int D = decltype(dtag)::value;
+        k_spikes<D><<<(2 * P * D + 127) / 128, 128, 0, s>>>(NE, L, rd, V, W);
+        for (int dir = 0; dir < 2; ++dir) {
+            const double* VW = dir == 0 ? V : W;
+            k_part_local<D><<<(P * ncol + 127) / 128, 128, 0, s>>>(NE, ncol, dir, L, rd, Z, ldz);
+            for (int c0 = 0; c0 < ncol; c0 += 32 / D)
+                k_part_iface<D><<<1, 32, 0, s>>>(NE, ncol, c0, std::min(ncol - c0, 32 / D), dir, Z, ldz, VW, T);
+            k_part_correct<D><<<(unsigned)(((size_t)NE * ncol + 255) / 256), 256, 0, s>>>(NE, ncol, dir, VW, T, Z, ldz);
+        }
+        launches += 5 + 2 * ((ncol + 32 / D - 1) / (32 / D));
+    };
+    switch (d) {
+        case 2: run(std::integral_constant<int, 2>()); break;
+        case 3: run(std::integral_constant<int, 3>()); break;
+        case 4: run(std::integral_constant<int, 4>()); break;
+        default: run(std::integral_constant<int, 5>()); break;
+    }
+    IGS_CUDA(cudaGetLastError());
+    dev_free(p, V);
+    dev_free(p, W);
+    dev_free(p, T);
+}
+
 // Reciprocals of the Cholesky diagonal: the substitutions multiply instead of
 // dividing (an FP64 division is a long dependent sequence on this GPU).
 __global__ void k_recip_diag(int NE, int d, const double* __restrict__ L, double* __restrict__ rd) {
@@ -822,11 +1033,16 @@ void rules_build(igs_prob p) {
         double* d_Zr = (double*)dev_alloc(p, sizeof(double) * (size_t)NE * R);
         k_mu_tab<<<dim3((NE + 127) / 128, R), 128, 0, s>>>(NE, M, d, den, dmin, p->d_pos, d_rows, p->d_piece, d_Et,
                                                           d_Zr, R);
-        k_gsolve<<<1, R, 0, s>>>(NE, d, R, d_L, d_rd, d_Zr, R);
+        if (NE >= 2 * kPart) {
+            part_gsolve(p, s, NE, d, R, d_L, d_rd, d_Zr, R, launches);
+        } else {
+            k_gsolve<<<1, R, 0, s>>>(NE, d, R, d_L, d_rd, d_Zr, R);
+            ++launches;
+        }
         p->d_WsRow = (double*)dev_alloc(p, sizeof(double) * (size_t)2 * R * Nq);
         k_wrows<<<dim3((Nq + 255) / 256, R), 256, 0, s>>>(Nq, d, R, p->d_fspan, p->d_Bf, d_Zr, p->d_WsRow);
         k_mirror<<<dim3((Nq + 255) / 256, R), 256, 0, s>>>(Nq, R, R, p->d_WsRow, p->d_WsRow);
-        launches += 4;
+        launches += 3;
         // boundary columns at both ends and the Toeplitz sequences
         p->d_WsT = (double*)dev_alloc(p, sizeof(double) * (size_t)2 * B * Nq);
         k_mirror<<<dim3((Nq + 255) / 256, 2 * B), 256, 0, s>>>(Nq, B, 0, d_Wc, p->d_WsT);
