@@ -1019,153 +1019,204 @@ __global__ void __launch_bounds__(256) k_split_panel(int n, const float* __restr
     }
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+
+// Persistent, warp-specialised form of the outer-block update (MIXED tier,
+// n >= 4096): one CTA per SM walks its share of the 128 x 64 lower-triangle
+// tiles (column tiles tj_off .. ntc-1; in column tile tj the row tiles
+// tj/2 .. ntr-1) in column order.  Warp 0 issues the bulk copies of the split
+// operand images into kTcpStages 48 KB stages, warp 1 issues the 3xTF32 MMAs
+// into one of two TMEM accumulators, warps 4-7 read the other accumulator
+// back (one tile row per lane) and apply C -= D, so a tile's epilogue runs
+// under the next tile's copies and MMAs.  Every wait is bounded: on a timeout
+// (or after another role's timeout) the kernel sets *flag |= 2 and skips the
+// rest.
+constexpr int kTcpStages = 3;
+constexpr uint32_t kTcpStageFloats = 2 * tc::kM * kKC + 2 * tc::kN * kKC;
+constexpr size_t tcp_smem_bytes() { return (size_t)kTcpStages * kTcpStageFloats * 4 + 128; }
+
+// Tile t of the walk (t non-decreasing between calls).
+struct TcpIter {
+    int tj, ti, t;
+    __device__ void init(int tj_off) { tj = tj_off; ti = tj_off / 2; t = 0; }
+    __device__ void seek(int target, int ntr) {
+        while (target - t >= ntr - ti) { t += ntr - ti; ++tj; ti = tj / 2; }
+        ti += target - t;
+        t = target;
+    }
+};
+
+// Bounded mbarrier wait: gives up after 2^24 polls or one second, or as soon
+// as another role of the CTA has given up.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort) {
+    const unsigned long long t0 = global_ns();
     for (long it = 0; it < (1L << 24); ++it) {
         uint32_t r;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(r) : "r"(bar), "r"(parity) : "memory");
         if (r) return true;
+        if (*abort) return false;
+        if ((it & 255) == 255 && global_ns() - t0 > kSpinNs) return false;
     }
     return false;
 }
 
-// Trailing update by a whole outer column block (MIXED tier, n >= 4096):
-// F[i][j] -= sum_{l < kbo} F[i][K0+l] F[j][K0+l], lower triangle of rows and
-// columns >= base = K0 + kbo, 128 x 64 output tiles, column tiles tj_off +
-// blockIdx.x.  Operands come from the split images by bulk copies into two
-// shared-memory stages of 32-column chunks (chunk kc+1 loads while chunk kc
-// multiplies; 96 KB, two CTAs per SM); one
-// thread issues copies and MMAs (3xTF32 into one TMEM accumulator), all
-// threads run the epilogue.  Waits are bounded: on a timeout the kernel sets
-// *flag |= 2 and skips the update.
-__global__ void __launch_bounds__(256) k_syrk_tcb(int n, float* __restrict__ F, const float* __restrict__ img, int K0,
-                                                  int kbo, int G2, int tj_off, int* __restrict__ flag) {
+__global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ F, const float* __restrict__ img,
+                                                     int K0, int kbo, int G2, int tj_off, int ntc, int ntr, int ntiles,
+                                                     int* __restrict__ flag) {
     using namespace tc;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float* stages = (float*)smem_raw;
+    uint64_t* bars = (uint64_t*)(stages + (size_t)kTcpStages * kTcpStageFloats);
+    uint64_t* full = bars;                         // [kTcpStages]
+    uint64_t* empty = bars + kTcpStages;           // [kTcpStages]
+    uint64_t* accf = bars + 2 * kTcpStages;        // [2]
+    uint64_t* acce = bars + 2 * kTcpStages + 2;    // [2]
+    uint32_t* s_taddr = (uint32_t*)(bars + 2 * kTcpStages + 4);
+    volatile int* s_abort = (volatile int*)(s_taddr + 1);
     const int base = K0 + kbo;
-    const int ti = blockIdx.y, tj = tj_off + blockIdx.x;
-    const int i0 = base + ti * (int)kM, j0 = base + tj * (int)kN;
-    if (j0 > i0 + (int)kM - 1 || j0 >= n) return;              // no lower-triangle entry in this tile
-    constexpr uint32_t kStageFloats = 2 * kM * kKC + 2 * kN * kKC;   // Ahi, Alo, Bhi, Blo
-    constexpr uint32_t kStageBytes = kStageFloats * 4;
-    float* stage0 = (float*)smem_raw;
-    uint64_t* bars = (uint64_t*)(stage0 + 2 * kStageFloats);   // full[2], empty[2]
-    uint32_t* s_taddr = (uint32_t*)(bars + 4);
-    int* s_bad = (int*)(s_taddr + 1);
+    const int nch = (kbo + kKC - 1) / kKC;
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(su32(s_taddr)), "r"(kN));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(su32(s_taddr)), "r"(2 * kN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int b = 0; b < 4; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(bars + b)), "r"(1));
+        for (int s = 0; s < kTcpStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(full + s)), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(empty + s)), "r"(1));
+        }
+        for (int a = 0; a < 2; ++a) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(accf + a)), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(acce + a)), "r"(4));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
-        *s_bad = 0;
+        *s_abort = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t taddr = *s_taddr;
-    const int nch = (kbo + kKC - 1) / kKC;
-    if (tid == 0) {
-        auto issue = [&](int kc, int st) {
-            float* sA = stage0 + (size_t)st * kStageFloats;
-            const uint32_t full = su32(bars + st);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(full), "r"(kStageBytes) : "memory");
-            const float* srcs[4] = {img + ((size_t)(kc * 2 + 0) * G2 + 2 * ti) * kImgFloats,
-                                    img + ((size_t)(kc * 2 + 1) * G2 + 2 * ti) * kImgFloats,
-                                    img + ((size_t)(kc * 2 + 0) * G2 + tj) * kImgFloats,
-                                    img + ((size_t)(kc * 2 + 1) * G2 + tj) * kImgFloats};
-            float* dsts[4] = {sA, sA + kM * kKC, sA + 2 * kM * kKC, sA + 2 * kM * kKC + kN * kKC};
-            const uint32_t sizes[4] = {kM * kKC * 4, kM * kKC * 4, kN * kKC * 4, kN * kKC * 4};
+    auto abort = [&]() {
+        if (!*s_abort) atomicOr(flag, 2);
+        *s_abort = 1;
+    };
+
+    if (warp == 0 && lane == 0) {
+        // producer: bulk copies of each tile's K chunks into the stages
+        TcpIter it;
+        it.init(tj_off);
+        long g = 0;
+        for (int t = blockIdx.x; t < ntiles && !*s_abort; t += gridDim.x) {
+            it.seek(t, ntr);
+            for (int kc = 0; kc < nch; ++kc, ++g) {
+                const int s = (int)(g % kTcpStages);
+                const long use = g / kTcpStages;
+                if (use >= 1 && !mbar_wait_or_abort(su32(empty + s), (uint32_t)((use - 1) & 1), s_abort)) { abort(); break; }
+                float* sA = stages + (size_t)s * kTcpStageFloats;
+                const uint32_t fb = su32(full + s);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"(kTcpStageFloats * 4) : "memory");
+                const float* srcs[4] = {img + ((size_t)(kc * 2 + 0) * G2 + 2 * it.ti) * kImgFloats,
+                                        img + ((size_t)(kc * 2 + 1) * G2 + 2 * it.ti) * kImgFloats,
+                                        img + ((size_t)(kc * 2 + 0) * G2 + it.tj) * kImgFloats,
+                                        img + ((size_t)(kc * 2 + 1) * G2 + it.tj) * kImgFloats};
+                float* dsts[4] = {sA, sA + kM * kKC, sA + 2 * kM * kKC, sA + 2 * kM * kKC + kN * kKC};
+                const uint32_t sizes[4] = {kM * kKC * 4, kM * kKC * 4, kN * kKC * 4, kN * kKC * 4};
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             :: "r"(su32(dsts[q])), "l"(srcs[q]), "r"(sizes[q]), "r"(full) : "memory");
-        };
-        bool ok = true;
-        for (int kc = 0; kc < nch && kc < 2; ++kc) issue(kc, kc);
+                for (int q = 0; q < 4; ++q)
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 :: "r"(su32(dsts[q])), "l"(srcs[q]), "r"(sizes[q]), "r"(fb) : "memory");
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: accumulator lt & 1 for the tile with local index lt
         const uint32_t lbo = 128, sbo = (kKC / 4) * 128;
-        for (int kc = 0; kc < nch && ok; ++kc) {
-            const int st = kc & 1;
-            const uint32_t ph = (uint32_t)((kc >> 1) & 1);
-            if (!mbar_wait(su32(bars + st), ph)) { ok = false; break; }
+        long g = 0;
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles && !*s_abort; t += gridDim.x, ++lt) {
+            const int a = lt & 1, use = lt / 2;
+            if (use >= 1 && !mbar_wait_or_abort(su32(acce + a), (uint32_t)((use - 1) & 1), s_abort)) { abort(); break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const float* sA = stage0 + (size_t)st * kStageFloats;
-            const uint32_t aH = su32(sA), aL = su32(sA + kM * kKC), bH = su32(sA + 2 * kM * kKC),
-                           bL = su32(sA + 2 * kM * kKC + kN * kKC);
-            for (uint32_t ks = 0; ks < kKC / 8; ++ks) {
-                const uint32_t koff = ks * 256;                    // K = 8: two core matrices
-                const uint64_t ah = sdesc(aH + koff, lbo, sbo), al = sdesc(aL + koff, lbo, sbo);
-                const uint64_t bh = sdesc(bH + koff, lbo, sbo), bl = sdesc(bL + koff, lbo, sbo);
-                mma(taddr, ah, bh, (kc > 0 || ks > 0) ? 1u : 0u);
-                mma(taddr, ah, bl, 1u);
-                mma(taddr, al, bh, 1u);
+            const uint32_t d = taddr + (uint32_t)(a * kN);
+            bool ok = true;
+            for (int kc = 0; kc < nch; ++kc, ++g) {
+                const int s = (int)(g % kTcpStages);
+                if (!mbar_wait_or_abort(su32(full + s), (uint32_t)((g / kTcpStages) & 1), s_abort)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const float* sA = stages + (size_t)s * kTcpStageFloats;
+                const uint32_t aH = su32(sA), aL = su32(sA + kM * kKC), bH = su32(sA + 2 * kM * kKC),
+                               bL = su32(sA + 2 * kM * kKC + kN * kKC);
+                for (uint32_t ks = 0; ks < kKC / 8; ++ks) {
+                    const uint32_t koff = ks * 256;
+                    const uint64_t ah = sdesc(aH + koff, lbo, sbo), al = sdesc(aL + koff, lbo, sbo);
+                    const uint64_t bh = sdesc(bH + koff, lbo, sbo), bl = sdesc(bL + koff, lbo, sbo);
+                    mma(d, ah, bh, (kc > 0 || ks > 0) ? 1u : 0u);
+                    mma(d, ah, bl, 1u);
+                    mma(d, al, bh, 1u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(su32(empty + s)) : "memory");
             }
+            if (!ok) { abort(); break; }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(su32(bars + 2 + st)) : "memory");
-            if (kc + 2 < nch) {
-                if (!mbar_wait(su32(bars + 2 + st), ph)) { ok = false; break; }
-                issue(kc + 2, st);
+                         :: "r"(su32(accf + a)) : "memory");
+        }
+    } else if (warp >= 4) {
+        // epilogue: lane = tile row (warp - 4) * 32 + lane, 64 columns from TMEM
+        const int rw = warp - 4;
+        TcpIter it;
+        it.init(tj_off);
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+            const int a = lt & 1, use = lt / 2;
+            bool ok = mbar_wait_or_abort(su32(accf + a), (uint32_t)(use & 1), s_abort);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) abort();
+                break;
             }
-        }
-        if (ok) {                                                  // the last commit covers every MMA
-            const int kl = nch - 1;
-            ok = mbar_wait(su32(bars + 2 + (kl & 1)), (uint32_t)((kl >> 1) & 1));
-        }
-        if (!ok) {
-            *s_bad = 1;
-            atomicOr(flag, 2);
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            it.seek(t, ntr);
+            const int i0 = base + it.ti * (int)kM, j0 = base + it.tj * (int)kN;
+            float dv[kN];
+#pragma unroll
+            for (int c0 = 0; c0 < (int)kN; c0 += 16) {
+                uint32_t r[16];
+                const uint32_t addr = taddr + ((uint32_t)(rw * 32) << 16) + (uint32_t)(a * kN + c0);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                             : "r"(addr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int q = 0; q < 16; ++q) dv[c0 + q] = __uint_as_float(r[q]);
+            }
+            // the accumulator is free for the tile after next
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(su32(acce + a)) : "memory");
+            const int i = i0 + rw * 32 + lane;
+            if (i < n) {
+                float* row = F + (size_t)i * n + j0;
+                if ((n & 3) == 0 && j0 + (int)kN - 1 <= i) {
+#pragma unroll
+                    for (int c = 0; c < (int)kN; c += 4) {
+                        float4 v = *(const float4*)(row + c);
+                        v.x -= dv[c]; v.y -= dv[c + 1]; v.z -= dv[c + 2]; v.w -= dv[c + 3];
+                        *(float4*)(row + c) = v;
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < (int)kN; ++c)
+                        if (j0 + c <= i && j0 + c < n) row[c] -= dv[c];
+                }
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const bool done = *s_bad == 0;
-    // accumulator -> shared (stage 0, no longer read by the tensor cores)
-    float (*D)[kN + 1] = (float (*)[kN + 1])smem_raw;
-    if (done) {
-        const int rbase = (warp % 4) * 32, cbase = (warp / 4) * 32;
-#pragma unroll
-        for (int c0 = 0; c0 < 32; c0 += 16) {
-            uint32_t r[16];
-            const uint32_t a = taddr + ((uint32_t)rbase << 16) + (uint32_t)(cbase + c0);
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                         : "r"(a));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-            for (int q = 0; q < 16; ++q) D[rbase + lane][cbase + c0 + q] = __uint_as_float(r[q]);
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(kN));
-    if (!done) return;
-    constexpr int kRows = (int)kM / 8;
-    float cv[kRows][2];
-#pragma unroll
-    for (int t = 0; t < kRows; ++t) {
-        const int i = i0 + warp + 8 * t;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int j = j0 + lane + 32 * h;
-            cv[t][h] = (i < n && j <= i) ? F[(size_t)i * n + j] : 0.0f;
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < kRows; ++t) {
-        const int rl = warp + 8 * t, i = i0 + rl;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = lane + 32 * h, j = j0 + c;
-            if (i < n && j <= i) F[(size_t)i * n + j] = cv[t][h] - D[rl][c];
-        }
-    }
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(2 * kN));
 }
-
-constexpr size_t tcb_smem_bytes() { return 2 * (size_t)(2 * tc::kM * kKC + 2 * tc::kN * kKC) * 4 + 64; }
 
 // Launch with programmatic stream serialisation (see pdl_wait).
 template <typename... KArgs, typename... Args>
@@ -1268,7 +1319,17 @@ static void tcb_launch(int n, float* F, const float* img, int K0, int kbo, int t
     const int rem = n - K0 - kbo;
     const int ntr = (rem + (int)tc::kM - 1) / (int)tc::kM;
     if (tcols <= 0 || ntr <= 0) return;
-    k_syrk_tcb<<<dim3(tcols, ntr), 256, tcb_smem_bytes(), s>>>(n, F, img, K0, kbo, 2 * ntr, tj_off, flag);
+    const int ntc = tj_off + tcols;
+    int ntiles = 0;
+    for (int tj = tj_off; tj < ntc; ++tj) ntiles += ntr - tj / 2;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        IGS_CUDA(cudaGetDevice(&dev));
+        IGS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int grid = std::max(1, std::min(ntiles, sms));
+    k_syrk_tcp<<<grid, 256, tcp_smem_bytes(), s>>>(n, F, img, K0, kbo, 2 * ntr, tj_off, ntc, ntr, ntiles, flag);
 }
 
 static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evP, cudaEvent_t evB,
@@ -1347,7 +1408,7 @@ static void factor(igs_prob p, cudaStream_t s) {
     ensure_dyn_smem((const void*)k_panel<T>, (size_t)panel_smem<T>());
     ensure_dyn_smem((const void*)k_syrk<T>, (size_t)syrk_smem<T>());
     ensure_dyn_smem((const void*)k_syrk_tc, tc::smem_bytes());
-    ensure_dyn_smem((const void*)k_syrk_tcb, tcb_smem_bytes());
+    ensure_dyn_smem((const void*)k_syrk_tcp, tcp_smem_bytes());
     const bool blocked = std::is_same<T, float>::value && n >= kBlockedMinN;
     if (!p->factor_exec) {
         // capture the fixed launch sequence once, on two private streams
