@@ -1021,25 +1021,35 @@ __global__ void __launch_bounds__(256) k_split_panel(int n, const float* __restr
 
 
 // Persistent, warp-specialised form of the outer-block update (MIXED tier,
-// n >= 4096): one CTA per SM walks its share of the 128 x 64 lower-triangle
+// n >= 4096): one CTA per SM walks its share of the 128 x 128 lower-triangle
 // tiles (column tiles tj_off .. ntc-1; in column tile tj the row tiles
-// tj/2 .. ntr-1) in column order.  Warp 0 issues the bulk copies of the split
-// operand images into kTcpStages 48 KB stages, warp 1 issues the 3xTF32 MMAs
-// into one of two TMEM accumulators, warps 4-7 read the other accumulator
-// back (one tile row per lane) and apply C -= D, so a tile's epilogue runs
-// under the next tile's copies and MMAs.  Every wait is bounded: on a timeout
-// (or after another role's timeout) the kernel sets *flag |= 2 and skips the
-// rest.
+// tj .. ntr-1) in column order.  Warp 0 issues the bulk copies of the split
+// operand images into kTcpStages 64 KB stages, warp 1 issues the 3xTF32 MMAs
+// (N = 128) into one of two TMEM accumulators, warps 4-7 read the other
+// accumulator back (one tile row per lane, two halves of 64 columns) and
+// apply C -= D, so a tile's epilogue runs under the next tile's copies and
+// MMAs.  Every wait is bounded: on a timeout (or after another role's
+// timeout) the kernel sets *flag |= 2 and skips the rest.
 constexpr int kTcpStages = 3;
-constexpr uint32_t kTcpStageFloats = 2 * tc::kM * kKC + 2 * tc::kN * kKC;
+constexpr uint32_t kTN = 128;                                  // tile columns (MMA N)
+constexpr uint32_t kTcpStageFloats = 2 * tc::kM * kKC + 2 * kTN * kKC;
 constexpr size_t tcp_smem_bytes() { return (size_t)kTcpStages * kTcpStageFloats * 4 + 128; }
+// D F32, A and B TF32, both K-major, N = kTN, M = 128
+__host__ __device__ constexpr uint32_t tcp_idesc() {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((kTN >> 3) << 17) | ((tc::kM >> 4) << 24);
+}
+__device__ __forceinline__ void tcp_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d), "l"(a), "l"(b), "r"(tcp_idesc()), "r"(accumulate));
+}
 
-// Tile t of the walk (t non-decreasing between calls).
+// Tile t of the walk (t non-decreasing between calls); square tiles, so the
+// first row tile of column tile tj is tj.
 struct TcpIter {
     int tj, ti, t;
-    __device__ void init(int tj_off) { tj = tj_off; ti = tj_off / 2; t = 0; }
+    __device__ void init(int tj_off) { tj = tj_off; ti = tj_off; t = 0; }
     __device__ void seek(int target, int ntr) {
-        while (target - t >= ntr - ti) { t += ntr - ti; ++tj; ti = tj / 2; }
+        while (target - t >= ntr - ti) { t += ntr - ti; ++tj; ti = tj; }
         ti += target - t;
         t = target;
     }
@@ -1077,7 +1087,7 @@ __global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ 
     const int nch = (kbo + kKC - 1) / kKC;
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(su32(s_taddr)), "r"(2 * kN));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(su32(s_taddr)), "r"(2 * kTN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -1117,10 +1127,10 @@ __global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ 
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"(kTcpStageFloats * 4) : "memory");
                 const float* srcs[4] = {img + ((size_t)(kc * 2 + 0) * G2 + 2 * it.ti) * kImgFloats,
                                         img + ((size_t)(kc * 2 + 1) * G2 + 2 * it.ti) * kImgFloats,
-                                        img + ((size_t)(kc * 2 + 0) * G2 + it.tj) * kImgFloats,
-                                        img + ((size_t)(kc * 2 + 1) * G2 + it.tj) * kImgFloats};
-                float* dsts[4] = {sA, sA + kM * kKC, sA + 2 * kM * kKC, sA + 2 * kM * kKC + kN * kKC};
-                const uint32_t sizes[4] = {kM * kKC * 4, kM * kKC * 4, kN * kKC * 4, kN * kKC * 4};
+                                        img + ((size_t)(kc * 2 + 0) * G2 + 2 * it.tj) * kImgFloats,
+                                        img + ((size_t)(kc * 2 + 1) * G2 + 2 * it.tj) * kImgFloats};
+                float* dsts[4] = {sA, sA + kM * kKC, sA + 2 * kM * kKC, sA + 2 * kM * kKC + kTN * kKC};
+                const uint32_t sizes[4] = {kM * kKC * 4, kM * kKC * 4, kTN * kKC * 4, kTN * kKC * 4};
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -1136,7 +1146,7 @@ __global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ 
             const int a = lt & 1, use = lt / 2;
             if (use >= 1 && !mbar_wait_or_abort(su32(acce + a), (uint32_t)((use - 1) & 1), s_abort)) { abort(); break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t d = taddr + (uint32_t)(a * kN);
+            const uint32_t d = taddr + (uint32_t)(a * kTN);
             bool ok = true;
             for (int kc = 0; kc < nch; ++kc, ++g) {
                 const int s = (int)(g % kTcpStages);
@@ -1144,14 +1154,14 @@ __global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ 
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const float* sA = stages + (size_t)s * kTcpStageFloats;
                 const uint32_t aH = su32(sA), aL = su32(sA + kM * kKC), bH = su32(sA + 2 * kM * kKC),
-                               bL = su32(sA + 2 * kM * kKC + kN * kKC);
+                               bL = su32(sA + 2 * kM * kKC + kTN * kKC);
                 for (uint32_t ks = 0; ks < kKC / 8; ++ks) {
                     const uint32_t koff = ks * 256;
                     const uint64_t ah = sdesc(aH + koff, lbo, sbo), al = sdesc(aL + koff, lbo, sbo);
                     const uint64_t bh = sdesc(bH + koff, lbo, sbo), bl = sdesc(bL + koff, lbo, sbo);
-                    mma(d, ah, bh, (kc > 0 || ks > 0) ? 1u : 0u);
-                    mma(d, ah, bl, 1u);
-                    mma(d, al, bh, 1u);
+                    tcp_mma(d, ah, bh, (kc > 0 || ks > 0) ? 1u : 0u);
+                    tcp_mma(d, ah, bl, 1u);
+                    tcp_mma(d, al, bh, 1u);
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              :: "r"(su32(empty + s)) : "memory");
@@ -1176,38 +1186,43 @@ __global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ 
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             it.seek(t, ntr);
-            const int i0 = base + it.ti * (int)kM, j0 = base + it.tj * (int)kN;
-            float dv[kN];
-#pragma unroll
-            for (int c0 = 0; c0 < (int)kN; c0 += 16) {
-                uint32_t r[16];
-                const uint32_t addr = taddr + ((uint32_t)(rw * 32) << 16) + (uint32_t)(a * kN + c0);
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                             : "r"(addr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                for (int q = 0; q < 16; ++q) dv[c0 + q] = __uint_as_float(r[q]);
-            }
-            // the accumulator is free for the tile after next
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(su32(acce + a)) : "memory");
+            const int i0 = base + it.ti * (int)kM, j0 = base + it.tj * (int)kTN;
             const int i = i0 + rw * 32 + lane;
-            if (i < n) {
-                float* row = F + (size_t)i * n + j0;
-                if ((n & 3) == 0 && j0 + (int)kN - 1 <= i) {
+            for (int h = 0; h < 2; ++h) {
+                float dv[64];
 #pragma unroll
-                    for (int c = 0; c < (int)kN; c += 4) {
-                        float4 v = *(const float4*)(row + c);
-                        v.x -= dv[c]; v.y -= dv[c + 1]; v.z -= dv[c + 2]; v.w -= dv[c + 3];
-                        *(float4*)(row + c) = v;
+                for (int c0 = 0; c0 < 64; c0 += 16) {
+                    uint32_t r[16];
+                    const uint32_t addr = taddr + ((uint32_t)(rw * 32) << 16) + (uint32_t)(a * kTN + h * 64 + c0);
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                                 : "r"(addr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) dv[c0 + q] = __uint_as_float(r[q]);
+                }
+                if (h == 1) {
+                    // the accumulator is free for the tile after next
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    __syncwarp();
+                    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(su32(acce + a)) : "memory");
+                }
+                const int jh = j0 + h * 64;
+                if (i < n && jh <= i) {
+                    float* row = F + (size_t)i * n + jh;
+                    if ((n & 3) == 0 && jh + 63 <= i) {
+#pragma unroll
+                        for (int c = 0; c < 64; c += 4) {
+                            float4 v = *(const float4*)(row + c);
+                            v.x -= dv[c]; v.y -= dv[c + 1]; v.z -= dv[c + 2]; v.w -= dv[c + 3];
+                            *(float4*)(row + c) = v;
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 64; ++c)
+                            if (jh + c <= i && jh + c < n) row[c] -= dv[c];
                     }
-                } else {
-#pragma unroll
-                    for (int c = 0; c < (int)kN; ++c)
-                        if (j0 + c <= i && j0 + c < n) row[c] -= dv[c];
                 }
             }
         }
@@ -1215,7 +1230,7 @@ __global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ 
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(2 * kN));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(2 * kTN));
 }
 
 // Launch with programmatic stream serialisation (see pdl_wait).
@@ -1321,7 +1336,7 @@ static void tcb_launch(int n, float* F, const float* img, int K0, int kbo, int t
     if (tcols <= 0 || ntr <= 0) return;
     const int ntc = tj_off + tcols;
     int ntiles = 0;
-    for (int tj = tj_off; tj < ntc; ++tj) ntiles += ntr - tj / 2;
+    for (int tj = tj_off; tj < ntc; ++tj) ntiles += ntr - tj;
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -1353,11 +1368,11 @@ static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, c
         }
         const int rem = n - K0 - kbo;
         if (rem <= 0) continue;
-        const int ntc = (rem + (int)tc::kN - 1) / (int)tc::kN;
+        const int ntc = (rem + (int)kTN - 1) / (int)kTN;             // 128-column tiles
         const int G2 = 2 * ((rem + (int)tc::kM - 1) / (int)tc::kM);
         float* img = p->d_timg + (size_t)((K0 / kOB) & 1) * tcb_image_floats(n);
         k_split_panel<<<dim3(G2, (kbo + kKC - 1) / kKC), 256, 0, s0>>>(n, F, K0, kbo, K0 + kbo, G2, img);
-        const int first = std::min(ntc, kOB / (int)tc::kN);          // the next outer block's column tiles
+        const int first = std::min(ntc, kOB / (int)kTN);             // the next outer block's column tiles
         if (ntc > first) IGS_CUDA(cudaEventRecord(evP, s0));
         if (pending) {
             IGS_CUDA(cudaStreamWaitEvent(s0, evB, 0));
