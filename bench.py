@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=180.0)
+    ap.add_argument("--serve-distinct", type=int, default=0,
+                    help="draw every request from a pool of this many (curve, n, p) problems (0: all distinct)")
+    ap.add_argument("--serve-cache-gb", type=float, default=16.0,
+                    help="device memory the server keeps for resident problems (rules, matrix, factor)")
     ap.add_argument("--batch-count", type=int, default=1024)
     ap.add_argument("--fp64-sample", type=int, default=64)
     return ap.parse_args()
@@ -435,7 +439,13 @@ def run_serve(args, rank, world, local_rank):
     from paper_1703_10016_gb300 import workloads as wl
     torch.cuda.set_device(local_rank)
     arrivals = wl.serve_arrivals(args.serve_rate, args.serve_seconds, seed=5)
-    srv = igs.igs_server_create(local_rank, slots=args.serve_slots, mem_budget=int(args.serve_budget_gb * 1e9))
+    if args.serve_distinct > 0:
+        # a recurring workload: the same problems come back with new data
+        pool = [pr for _, pr, _ in arrivals[:args.serve_distinct]]
+        pick = np.random.default_rng(6).integers(0, len(pool), size=len(arrivals))
+        arrivals = [(ta, pool[k], nrhs) for (ta, _, nrhs), k in zip(arrivals, pick)]
+    srv = igs.igs_server_create(local_rank, slots=args.serve_slots, mem_budget=int(args.serve_budget_gb * 1e9),
+                                cache_budget=int(args.serve_cache_gb * 1e9))
     # warm-up: a few small requests (module loading, first graph builds)
     warm = [igs.igs_server_submit(srv, wl.star_curve(), 3, 128, 2, igs.IGS_MIXED, 1, _serve_data)
             for _ in range(max(1, args.warmup))]
@@ -457,6 +467,7 @@ def run_serve(args, rank, world, local_rank):
     wall = time.perf_counter() - t0
     clocks = clk.stop()
     lat, queue, run, fails, entries, solves, bytes_max = [], [], [], 0, 0, 0, 0
+    reuse = {"rules": 0, "factor": 0}
     fail_kinds = {}
     for t, pr, nrhs in tickets:
         st = igs.igs_server_wait(srv, t)
@@ -469,6 +480,10 @@ def run_serve(args, rank, world, local_rank):
                 fail_kinds[key] = fail_kinds.get(key, 0) + 1
             continue
         _, res, st = igs.igs_server_result(srv, t, st["n"], nrhs)
+        if st["reuse"] == igs.IGS_REUSE_RULES:
+            reuse["rules"] += 1
+        elif st["reuse"] == igs.IGS_REUSE_FACTOR:
+            reuse["factor"] += 1
         lat.append(st["latency_ms"])
         queue.append(st["queue_ms"])
         run.append(st["run_ms"])
@@ -507,10 +522,12 @@ def run_serve(args, rank, world, local_rank):
         "warmup": len(warm), "ms_per_step": 1e3 * wall / max(len(tickets), 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s (seed 5): random "
-                               "stars, n log-uniform [128,16384], p in {2,3,4}, N_ref=2, 1..8 data sets",
+                               "stars, n log-uniform [128,16384], p in {2,3,4}, N_ref=2, 1..8 data sets"
+                               + (f"; drawn from {args.serve_distinct} recurring problems" if args.serve_distinct else ""),
                    "slots": args.serve_slots, "mem_budget_gb": args.serve_budget_gb,
+                   "resident_cache_gb": args.serve_cache_gb,
                    "parallelism": f"replicas x{world}"},
-        "requests": len(tickets), "completed": solves, "failed": fails, "failures": dict(list(fail_kinds.items())[:8]),
+        "requests": len(tickets), "completed": solves, "failed": fails, "reused": reuse, "failures": dict(list(fail_kinds.items())[:8]),
         "wall_s": wall,
         "offered_rate": args.serve_rate, "achieved_rate": solves / wall,
         "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "mean": statistics.mean(lat) if lat else None},

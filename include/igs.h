@@ -269,11 +269,25 @@ int igs_batch_get_config(igs_batch batch, igs_batch_config* cfg);
  * `mem_budget`; a request that could never fit is refused at submission.
  * Each request's result does not depend on what runs beside it.
  *
+ * Resident problems: the weighted rules depend only on the discretisation
+ * (degree, n_elems, n_ref, precision and the curve's parameter interval), not
+ * on the curve (Sect. 4), and a factorisation is valid until the matrix
+ * changes.  With cache_budget > 0 each slot keeps the problems of its recent
+ * requests (rules, matrix, factor) on the device, up to cache_budget bytes
+ * over all slots (least recently used first out).  A request whose
+ * discretisation matches a kept problem reuses its rules (the curve is swapped
+ * in as by igs_set_geometry); if the curve is also the same, bit for bit, it
+ * reuses the assembled matrix and its factor and only builds the right-hand
+ * sides and solves.  Kept problems count against mem_budget; an idle slot
+ * gives its kept problems up when the oldest queued request does not fit.
+ * The reuse changes no arithmetic: results equal those of a fresh request.
+ *
  * igs_data_fn: called once per request on a server thread with the request's
  *   right-hand-side points xy[count*2] (HOST, FP64, as igs_rhs_points); fills
  *   uD[k*count + q] for the nrhs data sets and returns 0 (nonzero fails the
  *   request with INVALID_ARG).
- * igs_server_create: device, opts (slots 1..64, mem_budget > 0 bytes).
+ * igs_server_create: device, opts (slots 1..64, mem_budget > 0 bytes,
+ *   cache_budget >= 0 bytes of resident problems, 0: none).
  *   Errors: INVALID_ARG, CUDA.
  * igs_server_submit: copies the request (curve arrays included) and returns a
  *   ticket at once.  Errors: INVALID_ARG (malformed), ADMISSION_REFUSED (its
@@ -309,6 +323,7 @@ typedef struct igs_request {
 typedef struct igs_server_opts {
     int32_t slots;
     int64_t mem_budget;
+    int64_t cache_budget;       /* device bytes of resident problems kept between requests (0: none) */
 } igs_server_opts;
 #define IGS_REQ_QUEUED  0
 #define IGS_REQ_RUNNING 1
@@ -322,7 +337,12 @@ typedef struct igs_request_stats {
     double queue_ms;            /* submission -> admission */
     double run_ms;              /* admission -> done */
     double latency_ms;          /* submission -> done */
+    int32_t reuse;              /* IGS_REUSE_*: what the request took from a resident problem */
+    int32_t reserved;
 } igs_request_stats;
+#define IGS_REUSE_NONE   0      /* rules built for the request */
+#define IGS_REUSE_RULES  1      /* rules of a resident problem, curve swapped in */
+#define IGS_REUSE_FACTOR 2      /* same curve: rules, matrix and factor reused */
 int igs_server_create(int device, const igs_server_opts* opts, igs_server* out);
 int igs_server_submit(igs_server server, const igs_request* req, int64_t* ticket);
 int igs_server_wait(igs_server server, int64_t ticket, int32_t timeout_ms, igs_request_stats* st);

@@ -6,6 +6,9 @@
 // is not overtaken), runs it through the library's own entry points, stores
 // the result and frees its memory share.  Requests on different slots overlap
 // on the device; each one's arithmetic is the same as when it runs alone.
+// With a cache budget, each slot keeps the problems of its recent requests
+// (rules, matrix, factor) resident and reuses them for requests on the same
+// discretisation (rules, curve swapped in) or the same curve (factor too).
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -26,10 +29,28 @@ struct Ticket {
     std::vector<double> knots, ctrl, w;
     int64_t est = 0;
     Clock::time_point t_submit, t_admit, t_done;
-    int status = IGS_REQ_QUEUED, error = IGS_OK, slot = -1, n = 0, ir = 0;
+    int status = IGS_REQ_QUEUED, error = IGS_OK, slot = -1, n = 0, ir = 0, reuse = IGS_REUSE_NONE;
     std::string msg;
     std::vector<double> alpha, resid;
 };
+
+// A resident problem of one slot: its discretisation key, the curve it holds
+// (degree, closed, knots, control points, weights, for an exact match), the
+// device bytes it keeps and its last use.
+struct Resident {
+    std::vector<double> key, curve;
+    igs_geom g = nullptr;
+    igs_prob p = nullptr;
+    int64_t bytes = 0;
+    uint64_t last = 0;
+};
+
+void drop(Resident& r) {
+    if (r.p) igs_destroy_problem(r.p);
+    if (r.g) igs_destroy_geometry(r.g);
+    r.p = nullptr;
+    r.g = nullptr;
+}
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();
@@ -70,25 +91,97 @@ struct igs_server_s {
     bool stop = false;
     std::vector<igs_ctx> ctxs;
     std::vector<std::thread> workers;
+    std::vector<std::vector<Resident>> kept;   // per slot, guarded by mu (only the slot's thread uses the problems)
+    int64_t kept_bytes = 0;
+    uint64_t clock = 0;
 };
 
 namespace {
 
-void run_request(igs_ctx ctx, Ticket& t) {
+// Take the slot's resident problem for `key` out of its list (nullptr-free
+// Resident if none).
+Resident take_resident(igs_server s, int slot, const std::vector<double>& key) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto& v = s->kept[slot];
+    for (size_t k = 0; k < v.size(); ++k)
+        if (v[k].key == key) {
+            Resident r = std::move(v[k]);
+            v.erase(v.begin() + (long)k);
+            s->kept_bytes -= r.bytes;
+            return r;
+        }
+    return Resident{};
+}
+
+// Keep a problem resident after its request; trims the slot's least recently
+// used problems while all slots together keep more than the cache budget.
+void keep_resident(igs_server s, int slot, Resident r) {
+    std::vector<Resident> out;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        r.last = ++s->clock;
+        s->kept_bytes += r.bytes;
+        s->kept[slot].push_back(std::move(r));
+        auto& v = s->kept[slot];
+        while (s->kept_bytes > s->opts.cache_budget && !v.empty()) {
+            size_t lru = 0;
+            for (size_t k = 1; k < v.size(); ++k)
+                if (v[k].last < v[lru].last) lru = k;
+            s->kept_bytes -= v[lru].bytes;
+            out.push_back(std::move(v[lru]));
+            v.erase(v.begin() + (long)lru);
+        }
+    }
+    for (Resident& q : out) drop(q);
+}
+
+void run_request(igs_server s, int slot, Ticket& t) {
+    igs_ctx ctx = s->ctxs[slot];
     const igs_request& r = t.req;
+    Resident res;
     igs_geom g = nullptr;
-    igs_prob p = nullptr;
     auto fail = [&](int rc, const std::string& m) {
         t.error = rc;
         t.msg = m;
     };
     int rc = igs_create_geometry(ctx, &g, r.geom_degree, t.knots.data(), (int)t.knots.size(), t.ctrl.data(),
                                  t.w.empty() ? nullptr : t.w.data(), r.n_ctrl, r.closed);
-    if (rc == IGS_OK) rc = igs_create_problem(g, &p, r.degree, r.n_elems, r.n_ref, r.precision);
+    std::vector<double> key, curve;
+    if (rc == IGS_OK) {
+        key = {(double)r.degree, (double)r.n_elems, (double)r.n_ref, (double)r.precision, (double)r.closed, g->a, g->b};
+        curve = {(double)r.geom_degree, (double)r.closed, (double)t.knots.size(), (double)r.n_ctrl};
+        curve.insert(curve.end(), t.knots.begin(), t.knots.end());
+        curve.insert(curve.end(), t.ctrl.begin(), t.ctrl.end());
+        curve.insert(curve.end(), t.w.begin(), t.w.end());
+        if (s->opts.cache_budget > 0) res = take_resident(s, slot, key);
+        if (res.p && res.curve == curve) {
+            // same curve: matrix and factor are still valid
+            igs_destroy_geometry(g);
+            g = nullptr;
+            t.reuse = IGS_REUSE_FACTOR;
+        } else if (res.p) {
+            rc = igs_set_geometry(res.p, g);
+            if (rc == IGS_OK) {
+                igs_destroy_geometry(res.g);
+                res.g = g;
+                g = nullptr;
+                res.curve = curve;
+                t.reuse = IGS_REUSE_RULES;
+                rc = igs_assemble(res.p, nullptr, 0, IGS_MEM_HOST, IGS_F64);
+            }
+        } else {
+            res.key = key;
+            res.curve = curve;
+            res.g = g;
+            g = nullptr;
+            rc = igs_create_problem(res.g, &res.p, r.degree, r.n_elems, r.n_ref, r.precision);
+            if (rc == IGS_OK) rc = igs_build_weighted_rules(res.p);
+            if (rc == IGS_OK) rc = igs_assemble(res.p, nullptr, 0, IGS_MEM_HOST, IGS_F64);
+        }
+    }
+    igs_prob p = res.p;
     igs_info info{};
     if (rc == IGS_OK) rc = igs_problem_info(p, &info);
-    if (rc == IGS_OK) rc = igs_build_weighted_rules(p);
-    if (rc == IGS_OK) rc = igs_assemble(p, nullptr, 0, IGS_MEM_HOST, IGS_F64);
     int64_t count = 0;
     std::vector<double> xy, uD;
     if (rc == IGS_OK) rc = igs_rhs_points(p, nullptr, 0, &count);
@@ -113,8 +206,14 @@ void run_request(igs_ctx ctx, Ticket& t) {
             if (rc != IGS_OK) fail(rc, igs_last_error());
         }
     }
-    if (p) igs_destroy_problem(p);
     if (g) igs_destroy_geometry(g);
+    if (t.error == IGS_OK && p && s->opts.cache_budget > 0 && igs_problem_info(p, &info) == IGS_OK &&
+        info.device_bytes <= s->opts.cache_budget) {
+        res.bytes = info.device_bytes;
+        keep_resident(s, slot, std::move(res));
+    } else {
+        drop(res);
+    }
 }
 
 void worker(igs_server s, int slot) {
@@ -122,27 +221,47 @@ void worker(igs_server s, int slot) {
     for (;;) {
         int64_t id = 0;
         Ticket* t = nullptr;
+        Resident spill;
         {
             std::unique_lock<std::mutex> lk(s->mu);
+            auto fits = [&] {
+                const Ticket& head = *s->tickets.at(s->queue.front());
+                return s->mem_in_use + s->kept_bytes + head.est <= s->opts.mem_budget;
+            };
             s->cv_work.wait(lk, [&] {
                 if (s->stop) return true;
                 if (s->queue.empty()) return false;
-                const Ticket& head = *s->tickets.at(s->queue.front());
-                return s->mem_in_use + head.est <= s->opts.mem_budget;
+                return fits() || !s->kept[slot].empty();
             });
             if (s->stop && s->queue.empty()) return;
             if (s->queue.empty()) continue;
-            id = s->queue.front();
-            s->queue.pop_front();
-            t = s->tickets.at(id).get();
-            s->mem_in_use += t->est;
-            t->status = IGS_REQ_RUNNING;
-            t->slot = slot;
-            t->t_admit = Clock::now();
+            if (!fits()) {
+                // the oldest request waits for memory: give up this slot's oldest resident problem
+                auto& v = s->kept[slot];
+                size_t lru = 0;
+                for (size_t k = 1; k < v.size(); ++k)
+                    if (v[k].last < v[lru].last) lru = k;
+                s->kept_bytes -= v[lru].bytes;
+                spill = std::move(v[lru]);
+                v.erase(v.begin() + (long)lru);
+            } else {
+                id = s->queue.front();
+                s->queue.pop_front();
+                t = s->tickets.at(id).get();
+                s->mem_in_use += t->est;
+                t->status = IGS_REQ_RUNNING;
+                t->slot = slot;
+                t->t_admit = Clock::now();
+            }
+        }
+        if (!t) {
+            drop(spill);
+            s->cv_work.notify_all();
+            continue;
         }
         // the next queued request may fit as well
         s->cv_work.notify_all();
-        run_request(s->ctxs[slot], *t);
+        run_request(s, slot, *t);
         {
             std::lock_guard<std::mutex> lk(s->mu);
             t->t_done = Clock::now();
@@ -164,6 +283,8 @@ void fill_stats(const Ticket& t, igs_request_stats* st) {
     st->ir_iterations = t.ir;
     st->slot = t.slot;
     st->device_bytes = t.est;
+    st->reuse = t.reuse;
+    st->reserved = 0;
     const bool admitted = t.status != IGS_REQ_QUEUED;
     const bool finished = t.status == IGS_REQ_DONE || t.status == IGS_REQ_FAILED;
     st->queue_ms = admitted ? ms_between(t.t_submit, t.t_admit) : ms_between(t.t_submit, Clock::now());
@@ -180,6 +301,7 @@ int igs_server_create(int device, const igs_server_opts* opts, igs_server* out) 
     REQUIRE(opts && out, IGS_E_INVALID_ARG, "opts and out must be set");
     REQUIRE(opts->slots >= 1 && opts->slots <= 64, IGS_E_INVALID_ARG, "slots must be in [1, 64]");
     REQUIRE(opts->mem_budget > 0, IGS_E_INVALID_ARG, "mem_budget must be positive");
+    REQUIRE(opts->cache_budget >= 0, IGS_E_INVALID_ARG, "cache_budget must not be negative");
     auto s = std::make_unique<igs_server_s>();
     s->device = device;
     s->opts = *opts;
@@ -192,6 +314,7 @@ int igs_server_create(int device, const igs_server_opts* opts, igs_server* out) 
         }
         s->ctxs.push_back(c);
     }
+    s->kept.resize(opts->slots);
     igs_server raw = s.release();
     for (int k = 0; k < opts->slots; ++k) raw->workers.emplace_back(worker, raw, k);
     *out = raw;
@@ -290,6 +413,8 @@ int igs_server_destroy(igs_server s) {
     }
     s->cv_work.notify_all();
     for (std::thread& w : s->workers) w.join();
+    for (auto& v : s->kept)
+        for (Resident& r : v) drop(r);
     for (igs_ctx c : s->ctxs) igs_destroy(c);
     delete s;
     API_END

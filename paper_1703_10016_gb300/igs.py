@@ -40,6 +40,7 @@ EXPORTED = [
     "igs_server_destroy", "igs_selftest_wait",
 ]
 IGS_REQ_QUEUED, IGS_REQ_RUNNING, IGS_REQ_DONE, IGS_REQ_FAILED = 0, 1, 2, 3
+IGS_REUSE_NONE, IGS_REUSE_RULES, IGS_REUSE_FACTOR = 0, 1, 2
 IGS_ORDER_NATURAL, IGS_ORDER_INTERLEAVED, IGS_ORDER_LARGEST_FIRST = 0, 1, 2
 
 
@@ -77,13 +78,14 @@ class igs_request(C.Structure):
 
 
 class igs_server_opts(C.Structure):
-    _fields_ = [("slots", C.c_int32), ("mem_budget", C.c_int64)]
+    _fields_ = [("slots", C.c_int32), ("mem_budget", C.c_int64), ("cache_budget", C.c_int64)]
 
 
 class igs_request_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("error", C.c_int32), ("n", C.c_int32), ("nrhs", C.c_int32),
                 ("ir_iterations", C.c_int32), ("slot", C.c_int32), ("device_bytes", C.c_int64),
-                ("queue_ms", C.c_double), ("run_ms", C.c_double), ("latency_ms", C.c_double)]
+                ("queue_ms", C.c_double), ("run_ms", C.c_double), ("latency_ms", C.c_double),
+                ("reuse", C.c_int32), ("reserved", C.c_int32)]
 
 
 def _load() -> C.CDLL:
@@ -364,9 +366,10 @@ def _stats_dict(st: igs_request_stats) -> dict:
     return {k: getattr(st, k) for k, _ in igs_request_stats._fields_}
 
 
-def igs_server_create(device: int = 0, slots: int = 4, mem_budget: int = 180 * 10**9) -> C.c_void_p:
+def igs_server_create(device: int = 0, slots: int = 4, mem_budget: int = 180 * 10**9,
+                      cache_budget: int = 0) -> C.c_void_p:
     h = C.c_void_p()
-    opts = igs_server_opts(int(slots), int(mem_budget))
+    opts = igs_server_opts(int(slots), int(mem_budget), int(cache_budget))
     _check(_lib.igs_server_create(int(device), C.byref(opts), C.byref(h)), "igs_server_create")
     return h
 

@@ -125,3 +125,46 @@ def test_many_mid_size_requests_on_eight_slots():
             assert np.max(np.abs(alpha - ref)) <= 1e-8 * np.max(np.abs(ref))
     finally:
         g.igs_server_destroy(s)
+
+
+def test_resident_problems_are_reused_and_change_no_result():
+    """With a cache budget a slot keeps its last problems: the same
+    discretisation on another curve reuses the rules (curve swapped in), the
+    same curve reuses the matrix and factor too; results equal the solo runs."""
+    g = lib()
+    rng = np.random.default_rng(33)
+    c1, c2 = wl.random_star(rng), wl.random_star(rng)
+    s = g.igs_server_create(0, slots=1, mem_budget=4 * 10**9, cache_budget=2 * 10**9)
+    try:
+        plan = [(c1, 2, g.IGS_REUSE_NONE), (c1, 3, g.IGS_REUSE_FACTOR), (c2, 1, g.IGS_REUSE_RULES),
+                (c2, 2, g.IGS_REUSE_FACTOR), (c1, 1, g.IGS_REUSE_RULES)]
+        for curve, nrhs, want in plan:
+            t = g.igs_server_submit(s, curve, 3, 160, 2, g.IGS_MIXED, nrhs, _data)
+            st = g.igs_server_wait(s, t)
+            assert st["status"] == g.IGS_REQ_DONE, st
+            alpha, res, st = g.igs_server_result(s, t, st["n"], nrhs)
+            assert st["reuse"] == want, (st["reuse"], want)
+            ref, _ = _solo(g, curve, 3, 160, 2, g.IGS_MIXED, nrhs)
+            assert np.all(res <= 1e-10)
+            np.testing.assert_allclose(alpha.reshape(nrhs, -1), ref, rtol=0, atol=1e-9 * np.max(np.abs(ref)))
+        # another discretisation is built fresh
+        t = g.igs_server_submit(s, c1, 3, 96, 2, g.IGS_MIXED, 1, _data)
+        st = g.igs_server_wait(s, t)
+        _, _, st = g.igs_server_result(s, t, st["n"], 1)
+        assert st["reuse"] == g.IGS_REUSE_NONE
+    finally:
+        g.igs_server_destroy(s)
+
+
+def test_no_cache_budget_means_no_reuse():
+    g = lib()
+    c = wl.star_curve()
+    s = g.igs_server_create(0, slots=1, mem_budget=4 * 10**9)
+    try:
+        for _ in range(2):
+            t = g.igs_server_submit(s, c, 3, 96, 2, g.IGS_MIXED, 1, _data)
+            st = g.igs_server_wait(s, t)
+            _, _, st = g.igs_server_result(s, t, st["n"], 1)
+            assert st["reuse"] == g.IGS_REUSE_NONE
+    finally:
+        g.igs_server_destroy(s)
