@@ -803,6 +803,30 @@ __global__ void __launch_bounds__(128) k_yc(int NE, int M, int d, int cap, const
 }
 
 // Wc[c][m] = W^s[m][cols[c]] = sum_{e in range(c)} sum_k E_{m,e,k} Yc[c][e][k].
+// The element row of the table for element q+1 is loaded while element q is
+// contracted (the FP64 pipe, not the L2 latency, sets the pace).
+template <int D>
+__device__ __forceinline__ double wcols_sum(const double* __restrict__ E, int cnt, int den,
+                                            const double* __restrict__ sY) {
+    constexpr int D1 = D + 1;
+    double cur[D1], nxt[D1];
+#pragma unroll
+    for (int k = 0; k < D1; ++k) cur[k] = E[k];
+    double acc = 0.0;
+    for (int q = 0; q < cnt; ++q) {
+        E -= (size_t)den * D1;
+        if (q + 1 < cnt) {
+#pragma unroll
+            for (int k = 0; k < D1; ++k) nxt[k] = E[k];
+        }
+#pragma unroll
+        for (int k = 0; k < D1; ++k) acc += cur[k] * sY[q * D1 + k];
+#pragma unroll
+        for (int k = 0; k < D1; ++k) cur[k] = nxt[k];
+    }
+    return acc;
+}
+
 __global__ void __launch_bounds__(256) k_wcols(int Nq, int d, int den, int dmin, int cap, const int* __restrict__ pos,
                                                const double* __restrict__ Et, const int* __restrict__ erange,
                                                const double* __restrict__ Yc, double* __restrict__ Wc) {
@@ -814,10 +838,18 @@ __global__ void __launch_bounds__(256) k_wcols(int Nq, int d, int den, int dmin,
     __syncthreads();
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= Nq) return;
+    if (cnt <= 0) {
+        Wc[(size_t)c * Nq + m] = 0.0;
+        return;
+    }
     const double* E = Et + (size_t)(pos[m] - elo * den - dmin) * D1;
-    double acc = 0.0;
-    for (int q = 0; q < cnt; ++q, E -= (size_t)den * D1)
-        for (int k = 0; k < D1; ++k) acc += E[k] * sY[q * D1 + k];
+    double acc;
+    switch (d) {
+        case 2: acc = wcols_sum<2>(E, cnt, den, sY); break;
+        case 3: acc = wcols_sum<3>(E, cnt, den, sY); break;
+        case 4: acc = wcols_sum<4>(E, cnt, den, sY); break;
+        default: acc = wcols_sum<5>(E, cnt, den, sY); break;
+    }
     Wc[(size_t)c * Nq + m] = acc;
 }
 
