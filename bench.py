@@ -63,6 +63,20 @@ def parse():
     return ap.parse_args()
 
 
+def all_reduce_value(x: float, op: str = "max") -> float:
+    """Max or sum of a per-rank number over the ranks of the job (the number
+    itself when the job has one rank); NCCL jobs reduce on the device, gloo
+    jobs on the host."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -187,11 +201,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         ck = clocks.stop() if name == "mixed" else None
-        total_ms = sum(times)
-        if world > 1:
-            tt = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(tt.item())
+        total_ms = all_reduce_value(sum(times), "max")         # slowest rank sets the job time
         A = torch.empty((n, n), dtype=torch.float64, device=dev)
         igs.igs_assemble(prob, A)
         results[name] = dict(times=times, total_ms=total_ms, wall=wall, launches=launches, phases=phases,
@@ -357,11 +367,7 @@ def run_batch(args, rank, world, local_rank):
     clk.start()
     times = [igs.igs_batch_assemble(b) for _ in range(args.steps)]
     clocks = clk.stop()
-    step_ms = statistics.mean(times)
-    if world > 1:
-        t = torch.tensor([step_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = all_reduce_value(statistics.mean(times), "max")
     # single-problem loop, MIXED (same kernels one launch per problem)
     torch.cuda.synchronize()
     loop_ms = 0.0
@@ -493,6 +499,10 @@ def run_serve(args, rank, world, local_rank):
     igs.igs_server_destroy(srv)
     lat_s = sorted(lat)
     pct = lambda q: lat_s[min(len(lat_s) - 1, int(math.ceil(q * len(lat_s))) - 1)] if lat_s else None
+    # whole job: every rank serves its own replica of the arrival stream
+    job_wall = all_reduce_value(wall, "max")
+    job_solves = all_reduce_value(solves, "sum")
+    job_entries = all_reduce_value(entries, "sum")
     # serial FP64 loop on a seeded sample of the same requests (direct API, one at a time)
     rng = np.random.default_rng(9)
     sample = sorted(rng.choice(len(arrivals), size=min(8, len(arrivals)), replace=False).tolist())
@@ -518,7 +528,7 @@ def run_serve(args, rank, world, local_rank):
     fp_rate = len(sample) / (fp_ms * 1e-3)
     return {
         "metric": "solves/s (served assemble+solve requests, MIXED tier, <=1e-6 rel. error)",
-        "value": world * solves / wall, "unit": "solves/s", "n_gpus": world, "steps": len(tickets),
+        "value": job_solves / job_wall, "unit": "solves/s", "n_gpus": world, "steps": len(tickets),
         "warmup": len(warm), "ms_per_step": 1e3 * wall / max(len(tickets), 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s (seed 5): random "
@@ -533,7 +543,7 @@ def run_serve(args, rank, world, local_rank):
         "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "mean": statistics.mean(lat) if lat else None},
         "queue_ms": {"p50": statistics.median(queue) if queue else None, "max": max(queue) if queue else None},
         "run_ms": {"p50": statistics.median(run) if run else None, "max": max(run) if run else None},
-        "entries_per_s": entries / wall, "max_request_bytes": bytes_max,
+        "entries_per_s": job_entries / job_wall, "max_request_bytes": bytes_max,
         "serial_fp64_loop": {"value": fp_rate, "unit": "solves/s", "sample": len(sample), "ms": fp_ms,
                              "entries_per_s": fp_entries / (fp_ms * 1e-3)},
         "speedup_vs_serial_fp64": (solves / wall) / fp_rate,
