@@ -63,6 +63,16 @@ def parse():
     return ap.parse_args()
 
 
+def measured_peak(key: str, fallback: float) -> tuple[float, str]:
+    """A peak from MEASURED_PEAKS.json at the repository root (written on the
+    GPU pool), else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key]), "measured"
+    except (OSError, KeyError, ValueError):
+        return fallback, "fallback"
+
+
 def all_reduce_value(x: float, op: str = "max") -> float:
     """Max or sum of a per-rank number over the ranks of the job (the number
     itself when the job has one rank); NCCL jobs reduce on the device, gloo
@@ -280,6 +290,12 @@ def run_ours(args, rank, world, local_rank):
                               "peak": SM_COUNT * 16 * SM_MAX_MHZ * 1e6 / 1e12, "unit": "Tops/s",
                               "frac": (2.0 * nq * nq / (asm_ms * 1e-3)) / (SM_COUNT * 16 * SM_MAX_MHZ * 1e6),
                               "peak_basis": "152 SMs x 16 MUFU lanes x 2070 MHz"}},
+        # the factorisation as a whole against the TF32 tensor peak (half the bf16 one):
+        # at small n the panel chain is latency-bound and this fraction is small
+        "factor_rate": (lambda pk: {"flop": n ** 3 / 3, "achieved_tflops": n ** 3 / 3 / (phase_mean["factor"] * 1e-3) / 1e12,
+                                    "tf32_peak_tflops": pk[0] / 2, "peak_source": pk[1],
+                                    "frac": n ** 3 / 3 / (phase_mean["factor"] * 1e-3) / 1e12 / (pk[0] / 2)})(
+            measured_peak("bf16_tflops_sustained", 1700.0)),
         "gpu_launches": int(sum(mixed["launches"])),
         "clocks": mixed["clocks"],
     }
