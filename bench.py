@@ -64,8 +64,8 @@ def parse():
 
 
 def measured_peak(key: str, fallback: float) -> tuple[float, str]:
-    """A peak from MEASURED_PEAKS.json at the repository root (written on the
-    GPU pool), else the stated fallback."""
+    """A peak from MEASURED_PEAKS.json at the repository root (measured copy
+    bandwidth and GEMM throughput of this GPU model), else the stated fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             return float(json.load(fh)[key]), "measured"
