@@ -1417,6 +1417,47 @@ static int factor_launches(int n) {
     return c;
 }
 
+// Capture the factorisation's fixed launch sequence into p->factor_exec, on
+// two private streams.
+template <typename T>
+static void capture_factor(igs_prob p, bool blocked) {
+    // capture the fixed launch sequence once, on two private streams
+    cudaStream_t cs = nullptr, cs1 = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    auto release = [&]() {
+        for (cudaEvent_t& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (cs1) cudaStreamDestroy(cs1);
+        if (cs) cudaStreamDestroy(cs);
+    };
+    cudaGraph_t graph = nullptr;
+    try {
+        IGS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        IGS_CUDA(cudaStreamCreateWithFlags(&cs1, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : ev) IGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        IGS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        try {
+            if (blocked) issue_factor_blocked(p, cs, cs1, ev[0], ev[1], ev[2]);
+            else issue_factor<T>(p, cs, cs1, ev[0], ev[1], ev[2]);
+        } catch (...) {
+            cudaStreamEndCapture(cs, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        IGS_CUDA(cudaStreamEndCapture(cs, &graph));
+    } catch (...) {
+        release();
+        throw;
+    }
+    cudaError_t e = cudaGraphInstantiate(&p->factor_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    release();
+    if (e != cudaSuccess) {
+        p->factor_exec = nullptr;
+        throw Error(IGS_E_CUDA, cuda_msg(e, "cudaGraphInstantiate", __FILE__, __LINE__));
+    }
+}
+
 template <typename T>
 static void factor(igs_prob p, cudaStream_t s) {
     const int n = p->plan.n;
@@ -1425,44 +1466,32 @@ static void factor(igs_prob p, cudaStream_t s) {
     ensure_dyn_smem((const void*)k_syrk_tc, tc::smem_bytes());
     ensure_dyn_smem((const void*)k_syrk_tcp, tcp_smem_bytes());
     const bool blocked = std::is_same<T, float>::value && n >= kBlockedMinN;
-    if (!p->factor_exec) {
-        // capture the fixed launch sequence once, on two private streams
-        cudaStream_t cs = nullptr, cs1 = nullptr;
+    if (!p->factor_exec && p->factor_runs == 0) {
+        // first factorisation of this problem: issue the launch sequence directly
+        // (a problem factored once, such as a served request, does not pay for a
+        // graph capture); the graph is captured when the problem is factored again
+        cudaStream_t s1 = nullptr;
         cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
         auto release = [&]() {
             for (cudaEvent_t& e : ev)
                 if (e) cudaEventDestroy(e);
-            if (cs1) cudaStreamDestroy(cs1);
-            if (cs) cudaStreamDestroy(cs);
+            if (s1) cudaStreamDestroy(s1);
         };
-        cudaGraph_t graph = nullptr;
         try {
-            IGS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-            IGS_CUDA(cudaStreamCreateWithFlags(&cs1, cudaStreamNonBlocking));
+            IGS_CUDA(cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking));
             for (cudaEvent_t& e : ev) IGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-            IGS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            try {
-                if (blocked) issue_factor_blocked(p, cs, cs1, ev[0], ev[1], ev[2]);
-                else issue_factor<T>(p, cs, cs1, ev[0], ev[1], ev[2]);
-            } catch (...) {
-                cudaStreamEndCapture(cs, &graph);
-                if (graph) cudaGraphDestroy(graph);
-                throw;
-            }
-            IGS_CUDA(cudaStreamEndCapture(cs, &graph));
+            if (blocked) issue_factor_blocked(p, s, s1, ev[0], ev[1], ev[2]);
+            else issue_factor<T>(p, s, s1, ev[0], ev[1], ev[2]);
         } catch (...) {
             release();
             throw;
         }
-        cudaError_t e = cudaGraphInstantiate(&p->factor_exec, graph, 0);
-        cudaGraphDestroy(graph);
         release();
-        if (e != cudaSuccess) {
-            p->factor_exec = nullptr;
-            throw Error(IGS_E_CUDA, cuda_msg(e, "cudaGraphInstantiate", __FILE__, __LINE__));
-        }
+    } else {
+        if (!p->factor_exec) capture_factor<T>(p, blocked);
+        IGS_CUDA(cudaGraphLaunch(p->factor_exec, s));
     }
-    IGS_CUDA(cudaGraphLaunch(p->factor_exec, s));
+    p->factor_runs++;
     p->launches += blocked ? factor_launches_blocked(n) : factor_launches(n);
     int flag = 0;
     IGS_CUDA(cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
