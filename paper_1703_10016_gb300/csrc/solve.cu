@@ -1565,6 +1565,15 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
         launch_resid(n, nrhs, p->d_As64, d_alpha, d_beta, d_r, d_norm, s);
         p->launches += 5;
         IGS_CUDA(cudaGetLastError());
+        if (it == 0 && max_it > 1) {
+            // an FP32 factor never meets the tolerance after one step: go on to the
+            // second without a round trip to the host (the next step reads the
+            // residual and its norm on the device)
+            ++it;
+            src = d_r;
+            scale = d_norm;
+            continue;
+        }
         IGS_CUDA(cudaMemcpyAsync(hn.data(), d_norm, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, s));
         int tflag = 0;
         IGS_CUDA(cudaMemcpyAsync(&tflag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
