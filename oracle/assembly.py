@@ -22,6 +22,11 @@
   oracle solves with (A + A^T)/2 by Cholesky (LAPACK potrf/potrs).
 * Errors (Sect. 6): E_M = max error on 500 uniform points of I, E_R = relative
   L^2(I) error.
+* Representation formula (Sect. 2): with the density q_h = sum_j alpha_j B_j,
+      u(x) = -(1/2 pi) int ln|x - y| q_h dgamma + (1/2 pi) int dln|x - y|/dn_y u_D dgamma
+  for x inside a closed curve (direct method), and only the first term for an
+  open arc (indirect method, density phi_h), both by the composite Gauss rule
+  of the right-hand side (G_RHS points per refined element).
 """
 from __future__ import annotations
 
@@ -151,6 +156,48 @@ def solve(A: np.ndarray, beta: np.ndarray) -> np.ndarray:
     As = 0.5 * (A + A.T)
     c = sla.cho_factor(As, lower=True)
     return sla.cho_solve(c, beta)
+
+
+# ----------------------------------------------------------------------------
+# Representation formula (post-processing)
+# ----------------------------------------------------------------------------
+def density_at(disc: Discretization, alpha, s) -> np.ndarray:
+    """q_h(s) = sum_j alpha_j B_j(s) for each data set: (nrhs, len(s))."""
+    alpha = np.asarray(alpha, np.float64).reshape(-1, disc.n)
+    return alpha @ disc.test_basis(s)[0]
+
+
+def potential_sum(x, f_t, f1_t, w, q, uD=None) -> np.ndarray:
+    """Quadrature form of the representation formula (Sect. 2) at points x
+    (2, P), from the rule (t_g, w_g): f_t = f(t_g), f1_t = f'(t_g), densities
+    q (nrhs, Ng) and, for a closed curve, u_D (nrhs, Ng) at t_g:
+      u(x) = -(1/2 pi) sum_g w_g J(t_g) ln|x - f(t_g)| q_g
+             + (1/2 pi) sum_g w_g Kbar(x, t_g) u_D(t_g).
+    Returns (nrhs, P)."""
+    J = np.hypot(f1_t[0], f1_t[1])
+    dx = f_t[0][None, :] - x[0][:, None]                 # (P, Ng)
+    dy = f_t[1][None, :] - x[1][:, None]
+    logr = 0.5 * np.log(dx * dx + dy * dy)
+    u = -(logr @ (w * J * q).T) / (2.0 * np.pi)
+    if uD is not None:
+        Kb = kernel_Kbar(x, f_t, f1_t)                   # (P, Ng)
+        u = u + (Kb @ (w * uD).T) / (2.0 * np.pi)
+    return u.T
+
+
+def eval_potential(curve, n_elems: int, degree: int, n_ref: int, alpha, uD_gauss, points) -> np.ndarray:
+    """u at `points` (P, 2) from the solution alpha (nrhs, n) and, for a
+    closed curve, u_D at the right-hand side's Gauss points (nrhs, Ng).
+    Valid away from the curve (a few refined elements or more)."""
+    disc = make_discretization(curve, n_elems, degree, n_ref)
+    tg, wg = disc.fine_gauss(G_RHS)
+    ft, f1t, _ = geometry_at(curve, tg)
+    q = density_at(disc, alpha, tg)
+    uD = None
+    if disc.closed:
+        uD = np.asarray(uD_gauss, np.float64).reshape(-1, len(tg))
+    x = np.asarray(points, np.float64).reshape(-1, 2).T
+    return potential_sum(x, ft, f1t, wg, q, uD)
 
 
 def outward_normal(f1):
