@@ -210,6 +210,26 @@ int igs_build_rhs_noalloc(igs_prob prob, const double* uD, int nrhs, double* bet
  * Errors: STATE (not assembled / no rhs), NOT_SPD, NOT_CONVERGED, CUDA. */
 int igs_solve(igs_prob prob, const double* beta, int nrhs, double* alpha_out, double* resid_out, int mem);
 
+/* Representation formula (Sect. 2): the potential u at `count` points x_p
+ * off the curve from a solved density.  Closed curve (direct method):
+ *   u(x) = -(1/2 pi) int ln|x - y| q(y) dgamma_y + (1/2 pi) int d/dn_y ln|x - y| u_D(y) dgamma_y,
+ * q = sum_j alpha_j B_j; open arc (indirect method): only the first term, with
+ * the density phi = sum_j alpha_j B_j.  Both integrals use the composite Gauss
+ * rule of igs_build_rhs (igs_rhs_points), in FP64 in every tier; the rule is
+ * not adapted to a near-singular integrand, so a point closer to the curve
+ * than a few refined elements gets a less accurate value, and a point on a
+ * Gauss point of the curve a non-finite one.
+ *   alpha: `mem` memory, nrhs x n (the layout of igs_solve's alpha_out).
+ *   uD:    `mem` memory, nrhs x n_rhs_pts (the layout of igs_build_rhs);
+ *          only the values at the Gauss points are read.  Required for a
+ *          closed curve, ignored (may be NULL) for an open arc.
+ *   xy:    `mem` memory, count x 2 (x_p = (xy[2p], xy[2p+1])).
+ *   u_out: `mem` memory, nrhs x count (data set k at u_out[k*count]).
+ * Needs no rules, matrix or factor.  Errors: INVALID_ARG (NULL pointer, nrhs
+ * outside [1, 8], count < 0, missing uD for a closed curve), NO_MEMORY, CUDA. */
+int igs_eval_potential(igs_prob prob, const double* alpha, const double* uD, int nrhs, const double* xy,
+                       int64_t count, double* u_out, int mem);
+
 /* Download the assembled A (eq. IK1e2 plus IK1e2_bis, Sect. 5) without
  * assembling again, e.g. after igs_batch_assemble.  Arguments as for
  * igs_assemble's A_out, ld, mem, dtype.  Errors: INVALID_ARG, STATE (not

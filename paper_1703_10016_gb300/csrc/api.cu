@@ -435,6 +435,53 @@ int igs_build_rhs(igs_prob p, const double* uD, int nrhs, double* beta_out, int 
     API_END
 }
 
+int igs_eval_potential(igs_prob p, const double* alpha, const double* uD, int nrhs, const double* xy, int64_t count,
+                       double* u_out, int mem) {
+    API_BEGIN
+    REQUIRE(p && alpha && (count == 0 || (xy && u_out)), IGS_E_INVALID_ARG, "NULL argument");
+    REQUIRE(nrhs >= 1 && nrhs <= 8, IGS_E_INVALID_ARG, "nrhs must be in [1, 8]");
+    REQUIRE(count >= 0, IGS_E_INVALID_ARG, "count must be >= 0");
+    REQUIRE(mem == IGS_MEM_HOST || mem == IGS_MEM_DEVICE, IGS_E_INVALID_ARG, "bad mem kind");
+    REQUIRE(!p->plan.closed || uD, IGS_E_INVALID_ARG, "a closed curve needs u_D at the right-hand side points");
+    if (count == 0) return IGS_OK;
+    IGS_CUDA(cudaSetDevice(p->geom->ctx->device));
+    cudaStream_t s = p->geom->ctx->stream;
+    p->launches = 0;
+    rhs_prepare(p);
+    const Plan& P = p->plan;
+    const size_t na = (size_t)nrhs * P.n, nu = p->plan.closed ? (size_t)nrhs * (P.Nq + p->Ng) : 0;
+    const double *d_alpha = alpha, *d_uD = p->plan.closed ? uD : nullptr, *d_xy = xy;
+    double* d_u = u_out;
+    double* tmp = nullptr;
+    if (mem == IGS_MEM_HOST) {
+        const size_t tot = na + nu + 2 * (size_t)count + (size_t)nrhs * count;
+        tmp = (double*)dev_alloc(p, sizeof(double) * tot);
+        double* t_alpha = tmp;
+        double* t_uD = t_alpha + na;
+        double* t_xy = t_uD + nu;
+        d_u = t_xy + 2 * (size_t)count;
+        IGS_CUDA(cudaMemcpyAsync(t_alpha, alpha, sizeof(double) * na, cudaMemcpyHostToDevice, s));
+        if (nu) IGS_CUDA(cudaMemcpyAsync(t_uD, uD, sizeof(double) * nu, cudaMemcpyHostToDevice, s));
+        IGS_CUDA(cudaMemcpyAsync(t_xy, xy, sizeof(double) * 2 * (size_t)count, cudaMemcpyHostToDevice, s));
+        d_alpha = t_alpha;
+        d_uD = nu ? t_uD : nullptr;
+        d_xy = t_xy;
+    }
+    try {
+        potential_eval(p, d_alpha, d_uD, nrhs, d_xy, count, d_u);
+        if (tmp) {
+            IGS_CUDA(cudaMemcpyAsync(u_out, d_u, sizeof(double) * (size_t)nrhs * count, cudaMemcpyDeviceToHost, s));
+            IGS_CUDA(cudaStreamSynchronize(s));
+        }
+    } catch (...) {
+        if (tmp) { cudaStreamSynchronize(s); dev_free(p, tmp); }
+        throw;
+    }
+    if (tmp) dev_free(p, tmp);
+    p->timing.kernel_launches = p->launches;
+    API_END
+}
+
 int igs_build_rhs_noalloc(igs_prob p, const double* uD, int nrhs, double* beta_out) {
     API_BEGIN
     REQUIRE(p && uD && beta_out, IGS_E_INVALID_ARG, "NULL argument");

@@ -184,6 +184,8 @@ void assemble_matrix(igs_prob p);
 void rhs_prepare(igs_prob p);
 void rhs_build(igs_prob p, const double* d_uD, int nrhs);
 void rhs_build_noalloc(igs_prob p, const double* d_uD, int nrhs, double* d_beta);
+void potential_eval(igs_prob p, const double* d_alpha, const double* d_uD, int nrhs, const double* d_xy,
+                    int64_t count, double* d_u);
 void solve_system(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double* resid);
 int wait_selftest(int device, double budget_s);   // 1: the bounded wait gave up
 }  // namespace igs

@@ -32,7 +32,7 @@ EXPORTED = [
     "igs_create", "igs_destroy", "igs_last_error", "igs_create_geometry", "igs_destroy_geometry",
     "igs_create_problem", "igs_destroy_problem", "igs_set_geometry", "igs_problem_info", "igs_problem_timing",
     "igs_build_weighted_rules", "igs_assemble", "igs_rhs_points", "igs_build_rhs", "igs_build_rhs_noalloc",
-    "igs_solve",
+    "igs_solve", "igs_eval_potential",
     "igs_get_rules", "igs_get_node_geometry",
     "igs_get_matrix", "igs_batch_create", "igs_batch_destroy", "igs_batch_assemble", "igs_batch_tune", "igs_batch_set_config",
     "igs_batch_get_config",
@@ -110,6 +110,7 @@ def _load() -> C.CDLL:
         "igs_build_rhs": [vp, vp, i32, vp, i32],
         "igs_build_rhs_noalloc": [vp, vp, i32, vp],
         "igs_solve": [vp, vp, i32, vp, vp, i32],
+        "igs_eval_potential": [vp, vp, vp, i32, vp, i64, vp, i32],
         "igs_get_rules": [vp, vp, vp, vp, vp],
         "igs_get_node_geometry": [vp, vp, vp],
         "igs_get_matrix": [vp, vp, i64, i32, i32],
@@ -291,6 +292,32 @@ def igs_solve(prob, beta=None, nrhs: int = 1, alpha_out=None, mem: int = IGS_MEM
     res = np.empty(nrhs, dtype=np.float64)
     _check(_lib.igs_solve(prob, _ptr(beta), int(nrhs), _ptr(alpha_out), _ptr(res), int(mem)), "igs_solve")
     return alpha_out, res
+
+
+def igs_eval_potential(prob, alpha, uD, xy, u_out=None):
+    """u at the points xy (count x 2) by the representation formula.
+    alpha: (nrhs, n); uD: (nrhs, n_rhs_pts) values at igs_rhs_points (None for
+    an open arc).  Host arrays, or CUDA tensors (device memory; u_out, if
+    given, a CUDA tensor nrhs x count).  Returns u (nrhs, count)."""
+    if hasattr(alpha, "is_cuda") and alpha.is_cuda:
+        import torch
+        a = alpha if alpha.dim() == 2 else alpha[None, :]
+        nrhs, count = int(a.shape[0]), int(xy.shape[0])
+        if u_out is None:
+            u_out = torch.empty((nrhs, count), dtype=torch.float64, device=a.device)
+        _check(_lib.igs_eval_potential(prob, _ptr(a), _ptr(uD), nrhs, _ptr(xy), count, _ptr(u_out), IGS_MEM_DEVICE),
+               "igs_eval_potential")
+        return u_out
+    a = _f64(alpha)
+    if a.ndim == 1:
+        a = a[None, :]
+    nrhs = a.shape[0]
+    u = None if uD is None else _f64(uD).reshape(nrhs, -1)
+    x = _f64(xy).reshape(-1, 2)
+    out = np.empty((nrhs, x.shape[0]), dtype=np.float64)
+    _check(_lib.igs_eval_potential(prob, _ptr(a), _ptr(u), nrhs, _ptr(x), x.shape[0], _ptr(out), IGS_MEM_HOST),
+           "igs_eval_potential")
+    return out
 
 
 def igs_get_rules(prob, with_ws: bool = False):
