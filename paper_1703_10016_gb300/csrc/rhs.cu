@@ -8,7 +8,8 @@
 // The double-layer potentials v_k(eta_m) = sum_g w_g Kbar(eta_m, t_g) u_k(t_g) are
 // an N_quad x N_GQ kernel sum.  The Gauss range is split in kSplit slices, one
 // grid row each, so that every node has kSplit partial sums (reduced in a fixed
-// order by k_beta: results do not depend on scheduling).  MIXED tier: FP32 with
+// order, by k_double_layer_near in the MIXED tier and by k_beta in the FP64
+// tier: results do not depend on scheduling).  MIXED tier: FP32 with
 // float-float coordinate differences for every pair.  At the Gauss points of
 // the node's refined element and its two neighbours the numerator
 // (f(t)-f(s)).n(t) is second-order small and the FP32 value is poor, so
@@ -53,16 +54,25 @@ __device__ __forceinline__ float kb32_pair(float gxh, float gxl, float gyh, floa
 
 // MIXED far field: partial sums over Gauss slice blockIdx.y, FP32, every pair
 // (the near pairs are replaced by k_double_layer_near).  Gauss data in shared
-// memory as 16-byte coordinate records and 8-byte (a, b) records.
+// memory as 16-byte coordinate records and 8-byte (a, b) records.  A block
+// holds kFarNodes nodes and kFarParts threads per node: part p of a node sums
+// the chunk's Gauss points q = p (mod kFarParts) (one warp = 32 nodes of one
+// part, so every shared-memory read is a broadcast), and the parts are added
+// in a fixed order at the end.
+constexpr int kFarNodes = 64, kFarParts = 4;
+
 template <int NR>
-__global__ void __launch_bounds__(256) k_double_layer_f(int Nq, int Ng, const double* __restrict__ geo,
-                                                        const double* __restrict__ rgeo,
-                                                        const double* __restrict__ rw, const double* __restrict__ uD,
-                                                        int ldu, int off, double* __restrict__ part) {
+__global__ void __launch_bounds__(kFarNodes * kFarParts) k_double_layer_f(int Nq, int Ng, const double* __restrict__ geo,
+                                                                          const double* __restrict__ rgeo,
+                                                                          const double* __restrict__ rw,
+                                                                          const double* __restrict__ uD, int ldu, int off,
+                                                                          double* __restrict__ part) {
     __shared__ float4 sg[kRhsChunk];
     __shared__ float2 sab[kRhsChunk];
     __shared__ float su[NR][kRhsChunk];
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ float red[kFarParts][NR][kFarNodes];
+    const int node = threadIdx.x % kFarNodes, prt = threadIdx.x / kFarNodes;
+    const int m = blockIdx.x * kFarNodes + node;
     const bool live = m < Nq;
     float xh = 0, xl = 0, yh = 0, yl = 0;
     if (live) {
@@ -91,7 +101,7 @@ __global__ void __launch_bounds__(256) k_double_layer_f(int Nq, int Ng, const do
         __syncthreads();
         if (live) {
 #pragma unroll 4
-            for (int q = 0; q < cn; ++q) {
+            for (int q = prt; q < cn; q += kFarParts) {
                 const float4 c = sg[q];
                 const float2 ab = sab[q];
                 const float kb = kb32_pair(c.x, c.y, c.z, c.w, ab.x, ab.y, xh, xl, yh, yl);
@@ -100,9 +110,17 @@ __global__ void __launch_bounds__(256) k_double_layer_f(int Nq, int Ng, const do
             }
         }
     }
-    if (live) {
 #pragma unroll
-        for (int k = 0; k < NR; ++k) part[((size_t)blockIdx.y * NR + k) * Nq + m] = (double)acc[k];
+    for (int k = 0; k < NR; ++k) red[prt][k][node] = acc[k];
+    __syncthreads();
+    if (live && prt == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            float v = red[0][k][node];
+#pragma unroll
+            for (int q = 1; q < kFarParts; ++q) v += red[q][k][node];
+            part[((size_t)blockIdx.y * NR + k) * Nq + m] = (double)v;
+        }
     }
 }
 
@@ -151,67 +169,94 @@ __global__ void __launch_bounds__(256) k_double_layer_d(int Nq, int Ng, const do
 // MIXED near field: Gauss points of the node's element and its two neighbours.
 // Adds their FP64 contributions and removes the FP32 ones the far-field kernel
 // summed (same bits from kb32_pair; the product of two floats is exact in FP64).
+// kNearLanes consecutive lanes share a node (pairs j = lane, lane + kNearLanes,
+// ... of the 3 kGaussRhs near pairs), reduced by a fixed shuffle tree; the
+// first lane adds the kSplit far-field partial sums (in slice order) and
+// writes the node's whole potential v_k(eta_m) into `out`.
+constexpr int kNearLanes = 4;
+
 __global__ void k_double_layer_near(int Nq, int Ng, int M, int nrhs, const double* __restrict__ geo,
                                     const int* __restrict__ fspan, const double* __restrict__ rgeo,
                                     const double* __restrict__ rw, const double* __restrict__ uD, int ldu, int off,
-                                    double* __restrict__ part) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= Nq) return;
-    const double xm = geo[m], ym = geo[Nq + m];
+                                    const double* __restrict__ far, double* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = t / kNearLanes, lane = t % kNearLanes;
+    const bool live = m < Nq;
+    const int mm = live ? m : Nq - 1;
+    const double xm = geo[mm], ym = geo[Nq + mm];
     float xh, xl, yh, yl;
     split2(xm, xh, xl);
     split2(ym, yh, yl);
-    const int em = fspan[m];
+    const int em = fspan[mm];
     double acc[kMaxRhs];
-    for (int k = 0; k < nrhs; ++k) acc[k] = 0.0;
-    for (int de = -1; de <= 1; ++de) {
-        int e = em + de;
+    for (int k = 0; k < kMaxRhs; ++k) acc[k] = 0.0;
+    for (int j = lane; j < 3 * kGaussRhs; j += kNearLanes) {
+        int e = em + j / kGaussRhs - 1;
         if (e < 0) e += M;
         if (e >= M) e -= M;
-        for (int q = 0; q < kGaussRhs; ++q) {
-            const int g = e * kGaussRhs + q;
-            const double dx = rgeo[g] - xm, dy = rgeo[Ng + g] - ym;
-            const double kb = (dx * rgeo[3 * Ng + g] - dy * rgeo[2 * Ng + g]) / (dx * dx + dy * dy);
-            float gxh, gxl, gyh, gyl;
-            split2(rgeo[g], gxh, gxl);
-            split2(rgeo[Ng + g], gyh, gyl);
-            const float kb32 = kb32_pair(gxh, gxl, gyh, gyl, (float)rgeo[3 * Ng + g], (float)(-rgeo[2 * Ng + g]), xh,
-                                         xl, yh, yl);
-            const double w = rw[g];
-            for (int k = 0; k < nrhs; ++k) {
-                const double u = uD[(size_t)k * ldu + off + g];
-                acc[k] += kb * w * u - (double)kb32 * (double)(float)(w * u);
-            }
+        const int g = e * kGaussRhs + j % kGaussRhs;
+        const double dx = rgeo[g] - xm, dy = rgeo[Ng + g] - ym;
+        const double kb = (dx * rgeo[3 * Ng + g] - dy * rgeo[2 * Ng + g]) / (dx * dx + dy * dy);
+        float gxh, gxl, gyh, gyl;
+        split2(rgeo[g], gxh, gxl);
+        split2(rgeo[Ng + g], gyh, gyl);
+        const float kb32 = kb32_pair(gxh, gxl, gyh, gyl, (float)rgeo[3 * Ng + g], (float)(-rgeo[2 * Ng + g]), xh,
+                                     xl, yh, yl);
+        const double w = rw[g];
+        for (int k = 0; k < nrhs; ++k) {
+            const double u = uD[(size_t)k * ldu + off + g];
+            acc[k] += kb * w * u - (double)kb32 * (double)(float)(w * u);
         }
     }
-    for (int k = 0; k < nrhs; ++k) part[(size_t)k * Nq + m] = acc[k];
+    for (int k = 0; k < nrhs; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int o = 1; o < kNearLanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (live && lane == 0) {
+            double tot = 0.0;
+            for (int sl = 0; sl < kSplit; ++sl) tot += far[((size_t)sl * nrhs + k) * Nq + m];
+            out[(size_t)k * Nq + m] = tot + v;
+        }
+    }
 }
 
 // beta[k][i] from the row weights P[m][r] = J_m w^(jfirst+r)_m over N^(i);
-// v_k(eta_m) is the sum of the np partial slots (fixed order).
+// v_k(eta_m) is the sum of the np partial slots (fixed order).  kBetaLanes
+// consecutive lanes share a row (nodes lo + lane, lo + lane + kBetaLanes, ...),
+// reduced by a fixed shuffle tree.
+constexpr int kBetaLanes = 8;
+
 __global__ void k_beta(int n, int Nq, int d, int nrhs, int closed, const int* __restrict__ lo, const int* __restrict__ hi,
                        const int* __restrict__ jfirst, const double* __restrict__ W, const double* __restrict__ geo,
                        const double* __restrict__ uD, int ldu, const double* __restrict__ part, int np,
                        double* __restrict__ beta) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / kBetaLanes, lane = t % kBetaLanes;
     const int k = blockIdx.y;
-    if (i >= n || k >= nrhs) return;
+    const bool live = i < n && k < nrhs;
     double b1 = 0.0, b2 = 0.0;
-    for (int u = lo[i]; u <= hi[i]; ++u) {
-        int m = u % Nq;
-        if (m < 0) m += Nq;
-        const int iu = (u < 0) ? i + n : i;
-        const int r = iu - jfirst[m];
-        if (r < 0 || r > d) continue;
-        const double p = geo[4 * Nq + m] * W[m * (d + 1) + r];
-        b1 += p * uD[(size_t)k * ldu + m];
-        if (closed) {
-            double v = 0.0;
-            for (int s = 0; s < np; ++s) v += part[((size_t)s * nrhs + k) * Nq + m];
-            b2 += p * v;
+    if (live) {
+        for (int u = lo[i] + lane; u <= hi[i]; u += kBetaLanes) {
+            int m = u % Nq;
+            if (m < 0) m += Nq;
+            const int iu = (u < 0) ? i + n : i;
+            const int r = iu - jfirst[m];
+            if (r < 0 || r > d) continue;
+            const double p = geo[4 * Nq + m] * W[m * (d + 1) + r];
+            b1 += p * uD[(size_t)k * ldu + m];
+            if (closed) {
+                double v = 0.0;
+                for (int s = 0; s < np; ++s) v += part[((size_t)s * nrhs + k) * Nq + m];
+                b2 += p * v;
+            }
         }
     }
-    beta[(size_t)k * n + i] = closed ? 0.5 * b1 - b2 / (2.0 * kPi) : b1;
+#pragma unroll
+    for (int o = 1; o < kBetaLanes; o <<= 1) {
+        b1 += __shfl_xor_sync(0xffffffffu, b1, o);
+        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+    }
+    if (live && lane == 0) beta[(size_t)k * n + i] = closed ? 0.5 * b1 - b2 / (2.0 * kPi) : b1;
 }
 
 void rhs_prepare(igs_prob p) {
@@ -262,13 +307,12 @@ template <int NR>
 static void launch_far(igs_prob p, const double* d_uD, int ldu, double* part) {
     const Plan& P = p->plan;
     cudaStream_t s = p->geom->ctx->stream;
-    dim3 grid((P.Nq + 255) / 256, kSplit);
     if (p->precision == IGS_MIXED)
-        k_double_layer_f<NR><<<grid, 256, 0, s>>>(P.Nq, p->Ng, p->d_geo, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq,
-                                                  part);
+        k_double_layer_f<NR><<<dim3((P.Nq + kFarNodes - 1) / kFarNodes, kSplit), kFarNodes * kFarParts, 0, s>>>(
+            P.Nq, p->Ng, p->d_geo, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, part);
     else
-        k_double_layer_d<NR><<<grid, 256, 0, s>>>(P.Nq, p->Ng, p->d_geo, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq,
-                                                  part);
+        k_double_layer_d<NR><<<dim3((P.Nq + 255) / 256, kSplit), 256, 0, s>>>(P.Nq, p->Ng, p->d_geo, p->d_rhs_geo,
+                                                                            p->d_rhs_w, d_uD, ldu, P.Nq, part);
     IGS_CUDA(cudaGetLastError());
 }
 
@@ -277,7 +321,8 @@ static void rhs_compute(igs_prob p, const double* d_uD, int nrhs, double* d_beta
     const Plan& P = p->plan;
     cudaStream_t s = p->geom->ctx->stream;
     const int ldu = P.Nq + p->Ng;
-    const int np = rhs_slots(p);
+    int np = rhs_slots(p);
+    const double* vsum = scratch;
     if (P.closed) {
         switch (nrhs) {
             case 1: launch_far<1>(p, d_uD, ldu, scratch); break;
@@ -291,16 +336,21 @@ static void rhs_compute(igs_prob p, const double* d_uD, int nrhs, double* d_beta
         }
         p->launches++;
         if (p->precision == IGS_MIXED) {
-            k_double_layer_near<<<(P.Nq + 127) / 128, 128, 0, s>>>(P.Nq, p->Ng, P.M, nrhs, p->d_geo, p->d_fspan,
-                                                                   p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq,
-                                                                   scratch + (size_t)kSplit * nrhs * P.Nq);
+            // the near kernel writes the whole potential (far slices + near correction) into the last slot
+            double* whole = scratch + (size_t)kSplit * nrhs * P.Nq;
+            const int nt = P.Nq * kNearLanes;
+            k_double_layer_near<<<(nt + 127) / 128, 128, 0, s>>>(P.Nq, p->Ng, P.M, nrhs, p->d_geo, p->d_fspan,
+                                                                 p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, scratch,
+                                                                 whole);
             IGS_CUDA(cudaGetLastError());
             p->launches++;
+            vsum = whole;
+            np = 1;
         }
     }
-    dim3 grid((P.n + 127) / 128, nrhs);
+    dim3 grid((P.n * kBetaLanes + 127) / 128, nrhs);
     k_beta<<<grid, 128, 0, s>>>(P.n, P.Nq, P.d, nrhs, P.closed, p->d_lo, p->d_hi, p->d_jfirst, p->d_W, p->d_geo, d_uD,
-                                ldu, scratch, np, d_beta);
+                                ldu, vsum, np, d_beta);
     IGS_CUDA(cudaGetLastError());
     p->launches++;
 }
