@@ -148,6 +148,28 @@ def build_rhs(curve, n_elems: int, degree: int, n_ref: int, uD_nodes, uD_gauss) 
     return 0.5 * b1 - b2 / (2.0 * np.pi)
 
 
+def build_rhs_rows(curve, n_elems: int, degree: int, n_ref: int, rows, uD_nodes, uD_gauss) -> np.ndarray:
+    """Entries `rows` of beta (len(rows) x nrhs) by the same sums as build_rhs,
+    restricted to the nodes N^(i) where P[n, i] can be non-zero (sampled
+    parity checks at large size)."""
+    disc = make_discretization(curve, n_elems, degree, n_ref)
+    W = rules.regular_rules(disc)
+    rows = np.asarray(rows)
+    need = np.unique(np.concatenate([disc.support_nodes(i) for i in rows]))
+    f, f1, J = geometry_at(curve, disc.eta[need])
+    P = J[:, None] * W[need][:, rows]                    # (len(need), len(rows))
+    uD_nodes = np.asarray(uD_nodes, np.float64).reshape(disc.Nq, -1)
+    b1 = P.T @ uD_nodes[need]
+    if not disc.closed:
+        return b1
+    tg, wg = disc.fine_gauss(G_RHS)
+    ft, f1t, _ = geometry_at(curve, tg)
+    Kb = kernel_Kbar(f, ft, f1t)                         # (len(need), Ng)
+    uD_gauss = np.asarray(uD_gauss, np.float64).reshape(len(tg), -1)
+    b2 = P.T @ (Kb @ (wg[:, None] * uD_gauss))
+    return 0.5 * b1 - b2 / (2.0 * np.pi)
+
+
 # ----------------------------------------------------------------------------
 # Solve and errors
 # ----------------------------------------------------------------------------

@@ -188,6 +188,36 @@ def test_full_size_star_sampled_rows(ctx, tier, tol):
         p.close()
 
 
+_FULL_SIZE_REF = {}
+
+
+@pytest.mark.parametrize("tier,tol", [("FP64", 1e-12), ("MIXED", 1e-6)])
+def test_full_size_star_rhs_and_solve(ctx, tier, tol):
+    """n = 2048, p = 3 star with u = log|x - (2, 1)| (the benchmark's request):
+    sampled entries of beta against the oracle's row-sampled sums, and the
+    refined solution satisfies the FP64 system of the assembled matrix."""
+    curve = wl.star_curve()
+    n, d, nref = 2048, 3, 2
+    rows = np.array([0, 1, 700, 1024, 2046, 2047])
+    p = Prob(ctx, curve, n, d, nref, getattr(lib(), "IGS_" + tier))
+    try:
+        A = p.assemble()
+        xy = lib().igs_rhs_points(p.prob)
+        u = wl.Harmonic("log").value(xy[:, 0], xy[:, 1])
+        beta = lib().igs_build_rhs(p.prob, u[None, :])[0]
+        Nq = p.info.n_quad
+        if "rhs2048" not in _FULL_SIZE_REF:
+            _FULL_SIZE_REF["rhs2048"] = oa.build_rhs_rows(curve, n, d, nref, rows, u[:Nq], u[Nq:])[:, 0]
+        ref = _FULL_SIZE_REF["rhs2048"]
+        assert np.max(np.abs(beta[rows] - ref)) <= tol * np.max(np.abs(ref))
+        alpha, res = lib().igs_solve(p.prob)
+        assert res[0] <= 1e-10
+        As = 0.5 * (A + A.T)
+        assert np.linalg.norm(As @ alpha[0] - beta) <= 1e-9 * np.linalg.norm(beta)
+    finally:
+        p.close()
+
+
 def test_invalid_arguments(ctx):
     g = lib()
     c = wl.star_curve()

@@ -145,3 +145,16 @@ def test_assemble_rows_matches_full():
     rows = np.array([0, 5, 23])
     part = oa.assemble_rows(c, 24, 3, 2, rows)
     np.testing.assert_allclose(part["A"], full["A"][rows], rtol=1e-13, atol=1e-16)
+
+
+def test_build_rhs_rows_matches_full():
+    """The row-sampled right-hand side equals the full one (closed and open)."""
+    for c, n, d in ((wl.star_curve(), 24, 3), (wl.parabola_arc(), 12, 2)):
+        eta, tg, _ = oa.rhs_points(c, n, d, 2)
+        h = wl.Harmonic("log")
+        un = h.value(*bspline.curve_eval(c, eta, 0)[0])[:, None]
+        ug = h.value(*bspline.curve_eval(c, tg, 0)[0])[:, None]
+        full = oa.build_rhs(c, n, d, 2, un, ug)
+        rows = np.array([0, 3, full.shape[0] - 1])
+        part = oa.build_rhs_rows(c, n, d, 2, rows, un, ug)
+        np.testing.assert_allclose(part, full[rows], rtol=1e-13, atol=1e-16)
