@@ -19,7 +19,10 @@ Modules
   rules          Algorithm 1 (regular weighted rules), modified moments (eq. mod_mom_gen),
                  Algorithm 2 (singular weighted rules)
   assembly       I_K1 (eq. IK1e2), I_K2 (eq. IK1e2_bis), right-hand side (Sect. 5),
-                 Cholesky solve and the error measures E_R, E_M (Sect. 6)
+                 Cholesky solve and the error measures E_R, E_M (Sect. 6),
+                 representation formula (Sect. 2)
+  collocation    collocation form of the single-layer equation with the same rules
+                 (Sect. 7 remark), LU solve
 
 Pins: every function is checked in ``tests/test_oracle_*.py`` against
 quantities the paper or mathematics fixes (exactness, closed forms, adaptive
@@ -27,4 +30,4 @@ quadrature, circle eigenvalues, manufactured solutions, Table 2 condition
 numbers).  Functions without such a pin say "parity unpinned" in their
 docstring; at present there are none.
 """
-from . import bspline, discretization, rules, assembly  # noqa: F401
+from . import bspline, discretization, rules, assembly, collocation  # noqa: F401
