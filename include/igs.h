@@ -52,6 +52,7 @@ extern "C" {
 #define IGS_E_TIMEOUT           -6   /* a bounded device wait gave up             */
 #define IGS_E_ADMISSION_REFUSED -7   /* request does not fit the memory budget    */
 #define IGS_E_STATE             -8   /* call out of order (e.g. solve before assemble) */
+#define IGS_E_SINGULAR          -9   /* LU met a zero or non-finite pivot         */
 
 /* precision tiers */
 #define IGS_FP64   0   /* every step in FP64                                                    */
@@ -229,6 +230,27 @@ int igs_solve(igs_prob prob, const double* beta, int nrhs, double* alpha_out, do
  * outside [1, 8], count < 0, missing uD for a closed curve), NO_MEMORY, CUDA. */
 int igs_eval_potential(igs_prob prob, const double* alpha, const double* uD, int nrhs, const double* xy,
                        int64_t count, double* u_out, int mem);
+
+/* Collocation form of the single-layer equation (the remark of Sect. 7: the
+ * same quadrature rules serve collocation BEM), closed curves only.  The
+ * pointwise form of eq. seconda_BIE is imposed at one node m_i per unknown:
+ *   Ac[i][j] = -(1/2 pi) (C0 P + W^s Q)[m_i][j]   (the inner sums of eqs. IK1e2, IK1e2_bis),
+ *   beta_c[k][i] = u_D,k(eta_m_i)/2 - v_k(eta_m_i)/(2 pi),
+ * v_k the double-layer potential at the nodes (the b2 inner rule of Sect. 5),
+ * and Ac alpha = beta_c is solved by LU with partial pivoting.  m_i is the
+ * node nearest the centre of the support of B_i (its Greville abscissa),
+ * measured periodically, ties to the smaller node index.  Matrix, LU and
+ * substitutions in FP64 in every tier; v_k follows the problem's tier.  The
+ * LU is unblocked (2n launches): meant for n up to a few thousand.
+ *   uD:        `mem` memory, nrhs x n_rhs_pts (the layout of igs_build_rhs).
+ *   alpha_out: `mem` memory, nrhs x n.
+ *   Ac_out:    NULL or `mem` memory, n x n row-major FP64 (before the LU).
+ *   nodes_out: NULL or HOST array of n collocation node indices m_i.
+ * Builds the rules and node geometry if missing; leaves the Galerkin matrix,
+ * factor and right-hand side alone.  Errors: INVALID_ARG (open arc, n > 16384,
+ * nrhs outside [1, 8], NULL uD/alpha_out), SINGULAR, NO_MEMORY, CUDA. */
+int igs_collocation(igs_prob prob, const double* uD, int nrhs, double* alpha_out, double* Ac_out, int32_t* nodes_out,
+                    int mem);
 
 /* Download the assembled A (eq. IK1e2 plus IK1e2_bis, Sect. 5) without
  * assembling again, e.g. after igs_batch_assemble.  Arguments as for

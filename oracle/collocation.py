@@ -48,10 +48,13 @@ def collocation_nodes(disc: Discretization) -> np.ndarray:
     return m
 
 
-def collocation_matrix(curve, n_elems: int, degree: int, n_ref: int = 2):
-    """(Ac, m): the n x n collocation matrix and the collocation nodes."""
+def collocation_matrix(curve, n_elems: int, degree: int, n_ref: int = 2, rows=None):
+    """(Ac, m): the n x n collocation matrix (or its rows `rows`) and the
+    collocation nodes of those rows."""
     disc = make_discretization(curve, n_elems, degree, n_ref)
     m = collocation_nodes(disc)
+    if rows is not None:
+        m = m[np.asarray(rows)]
     W = rules.regular_rules(disc)
     Ws = rules.singular_rules(disc, m)                           # rows w^{eta_m}
     f, f1, J = geometry_at(curve, disc.eta)

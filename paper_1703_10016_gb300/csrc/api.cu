@@ -482,6 +482,44 @@ int igs_eval_potential(igs_prob p, const double* alpha, const double* uD, int nr
     API_END
 }
 
+int igs_collocation(igs_prob p, const double* uD, int nrhs, double* alpha_out, double* Ac_out, int32_t* nodes_out,
+                    int mem) {
+    API_BEGIN
+    REQUIRE(p && uD && alpha_out, IGS_E_INVALID_ARG, "NULL argument");
+    REQUIRE(nrhs >= 1 && nrhs <= 8, IGS_E_INVALID_ARG, "nrhs must be in [1, 8]");
+    REQUIRE(mem == IGS_MEM_HOST || mem == IGS_MEM_DEVICE, IGS_E_INVALID_ARG, "bad mem kind");
+    REQUIRE(p->plan.closed, IGS_E_INVALID_ARG, "collocation is implemented for closed curves only");
+    IGS_CUDA(cudaSetDevice(p->geom->ctx->device));
+    cudaStream_t s = p->geom->ctx->stream;
+    p->launches = 0;
+    ensure_geometry(p);
+    rhs_prepare(p);
+    const Plan& P = p->plan;
+    const size_t nu = (size_t)nrhs * (P.Nq + p->Ng), na = (size_t)nrhs * P.n;
+    const double* d_uD = uD;
+    double* d_alpha = alpha_out;
+    double* tmp = nullptr;
+    if (mem == IGS_MEM_HOST) {
+        tmp = (double*)dev_alloc(p, sizeof(double) * (nu + na));
+        IGS_CUDA(cudaMemcpyAsync(tmp, uD, sizeof(double) * nu, cudaMemcpyHostToDevice, s));
+        d_uD = tmp;
+        d_alpha = tmp + nu;
+    }
+    try {
+        collocation_solve(p, d_uD, nrhs, d_alpha, Ac_out, mem, nodes_out);
+        if (tmp) {
+            IGS_CUDA(cudaMemcpyAsync(alpha_out, d_alpha, sizeof(double) * na, cudaMemcpyDeviceToHost, s));
+            IGS_CUDA(cudaStreamSynchronize(s));
+        }
+    } catch (...) {
+        if (tmp) { cudaStreamSynchronize(s); dev_free(p, tmp); }
+        throw;
+    }
+    if (tmp) dev_free(p, tmp);
+    p->timing.kernel_launches = p->launches;
+    API_END
+}
+
 int igs_build_rhs_noalloc(igs_prob p, const double* uD, int nrhs, double* beta_out) {
     API_BEGIN
     REQUIRE(p && uD && beta_out, IGS_E_INVALID_ARG, "NULL argument");

@@ -184,6 +184,10 @@ void assemble_matrix(igs_prob p);
 void rhs_prepare(igs_prob p);
 void rhs_build(igs_prob p, const double* d_uD, int nrhs);
 void rhs_build_noalloc(igs_prob p, const double* d_uD, int nrhs, double* d_beta);
+int rhs_slots(const igs_prob p);   // partial-sum slots (each nrhs x N_quad doubles) of the node potentials
+void rhs_node_potentials(igs_prob p, const double* d_uD, int nrhs, double* scratch, const double** vsum, int* np);
+void collocation_solve(igs_prob p, const double* d_uD, int nrhs, double* d_alpha, double* Ac_out, int ac_mem,
+                       int* nodes_out);
 void potential_eval(igs_prob p, const double* d_alpha, const double* d_uD, int nrhs, const double* d_xy,
                     int64_t count, double* d_u);
 void solve_system(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double* resid);

@@ -298,7 +298,7 @@ void rhs_prepare(igs_prob p) {
 }
 
 // Number of partial-sum slots (each nrhs x N_quad doubles) the kernels need.
-static int rhs_slots(const igs_prob p) {
+int rhs_slots(const igs_prob p) {
     if (!p->plan.closed) return 0;
     return kSplit + (p->precision == IGS_MIXED ? 1 : 0);
 }
@@ -316,38 +316,48 @@ static void launch_far(igs_prob p, const double* d_uD, int ldu, double* part) {
     IGS_CUDA(cudaGetLastError());
 }
 
+// Double-layer potentials v_k(eta_m) at the nodes of a closed curve, as
+// partial sums in `scratch` (rhs_slots x nrhs x N_quad doubles): v_k(eta_m) is
+// the sum over s < *np of vsum[(s nrhs + k) N_quad + m], in that order.
+void rhs_node_potentials(igs_prob p, const double* d_uD, int nrhs, double* scratch, const double** vsum, int* np) {
+    const Plan& P = p->plan;
+    cudaStream_t s = p->geom->ctx->stream;
+    const int ldu = P.Nq + p->Ng;
+    *np = rhs_slots(p);
+    *vsum = scratch;
+    switch (nrhs) {
+        case 1: launch_far<1>(p, d_uD, ldu, scratch); break;
+        case 2: launch_far<2>(p, d_uD, ldu, scratch); break;
+        case 3: launch_far<3>(p, d_uD, ldu, scratch); break;
+        case 4: launch_far<4>(p, d_uD, ldu, scratch); break;
+        case 5: launch_far<5>(p, d_uD, ldu, scratch); break;
+        case 6: launch_far<6>(p, d_uD, ldu, scratch); break;
+        case 7: launch_far<7>(p, d_uD, ldu, scratch); break;
+        default: launch_far<8>(p, d_uD, ldu, scratch); break;
+    }
+    p->launches++;
+    if (p->precision == IGS_MIXED) {
+        // the near kernel writes the whole potential (far slices + near correction) into the last slot
+        double* whole = scratch + (size_t)kSplit * nrhs * P.Nq;
+        const int nt = P.Nq * kNearLanes;
+        k_double_layer_near<<<(nt + 127) / 128, 128, 0, s>>>(P.Nq, p->Ng, P.M, nrhs, p->d_geo, p->d_fspan,
+                                                             p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, scratch,
+                                                             whole);
+        IGS_CUDA(cudaGetLastError());
+        p->launches++;
+        *vsum = whole;
+        *np = 1;
+    }
+}
+
 // beta for nrhs data sets into d_beta, partial sums in `scratch` (rhs_slots x nrhs x N_quad doubles).
 static void rhs_compute(igs_prob p, const double* d_uD, int nrhs, double* d_beta, double* scratch) {
     const Plan& P = p->plan;
     cudaStream_t s = p->geom->ctx->stream;
     const int ldu = P.Nq + p->Ng;
-    int np = rhs_slots(p);
+    int np = 0;
     const double* vsum = scratch;
-    if (P.closed) {
-        switch (nrhs) {
-            case 1: launch_far<1>(p, d_uD, ldu, scratch); break;
-            case 2: launch_far<2>(p, d_uD, ldu, scratch); break;
-            case 3: launch_far<3>(p, d_uD, ldu, scratch); break;
-            case 4: launch_far<4>(p, d_uD, ldu, scratch); break;
-            case 5: launch_far<5>(p, d_uD, ldu, scratch); break;
-            case 6: launch_far<6>(p, d_uD, ldu, scratch); break;
-            case 7: launch_far<7>(p, d_uD, ldu, scratch); break;
-            default: launch_far<8>(p, d_uD, ldu, scratch); break;
-        }
-        p->launches++;
-        if (p->precision == IGS_MIXED) {
-            // the near kernel writes the whole potential (far slices + near correction) into the last slot
-            double* whole = scratch + (size_t)kSplit * nrhs * P.Nq;
-            const int nt = P.Nq * kNearLanes;
-            k_double_layer_near<<<(nt + 127) / 128, 128, 0, s>>>(P.Nq, p->Ng, P.M, nrhs, p->d_geo, p->d_fspan,
-                                                                 p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, scratch,
-                                                                 whole);
-            IGS_CUDA(cudaGetLastError());
-            p->launches++;
-            vsum = whole;
-            np = 1;
-        }
-    }
+    if (P.closed) rhs_node_potentials(p, d_uD, nrhs, scratch, &vsum, &np);
     dim3 grid((P.n * kBetaLanes + 127) / 128, nrhs);
     k_beta<<<grid, 128, 0, s>>>(P.n, P.Nq, P.d, nrhs, P.closed, p->d_lo, p->d_hi, p->d_jfirst, p->d_W, p->d_geo, d_uD,
                                 ldu, vsum, np, d_beta);

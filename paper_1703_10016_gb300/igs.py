@@ -24,6 +24,7 @@ IGS_E_NOT_CONVERGED = -5
 IGS_E_TIMEOUT = -6
 IGS_E_ADMISSION_REFUSED = -7
 IGS_E_STATE = -8
+IGS_E_SINGULAR = -9
 IGS_FP64, IGS_MIXED = 0, 1
 IGS_MEM_HOST, IGS_MEM_DEVICE = 0, 1
 IGS_F64, IGS_F32 = 0, 1
@@ -32,7 +33,7 @@ EXPORTED = [
     "igs_create", "igs_destroy", "igs_last_error", "igs_create_geometry", "igs_destroy_geometry",
     "igs_create_problem", "igs_destroy_problem", "igs_set_geometry", "igs_problem_info", "igs_problem_timing",
     "igs_build_weighted_rules", "igs_assemble", "igs_rhs_points", "igs_build_rhs", "igs_build_rhs_noalloc",
-    "igs_solve", "igs_eval_potential",
+    "igs_solve", "igs_eval_potential", "igs_collocation",
     "igs_get_rules", "igs_get_node_geometry",
     "igs_get_matrix", "igs_batch_create", "igs_batch_destroy", "igs_batch_assemble", "igs_batch_tune", "igs_batch_set_config",
     "igs_batch_get_config",
@@ -111,6 +112,7 @@ def _load() -> C.CDLL:
         "igs_build_rhs_noalloc": [vp, vp, i32, vp],
         "igs_solve": [vp, vp, i32, vp, vp, i32],
         "igs_eval_potential": [vp, vp, vp, i32, vp, i64, vp, i32],
+        "igs_collocation": [vp, vp, i32, vp, vp, vp, i32],
         "igs_get_rules": [vp, vp, vp, vp, vp],
         "igs_get_node_geometry": [vp, vp, vp],
         "igs_get_matrix": [vp, vp, i64, i32, i32],
@@ -318,6 +320,23 @@ def igs_eval_potential(prob, alpha, uD, xy, u_out=None):
     _check(_lib.igs_eval_potential(prob, _ptr(a), _ptr(u), nrhs, _ptr(x), x.shape[0], _ptr(out), IGS_MEM_HOST),
            "igs_eval_potential")
     return out
+
+
+def igs_collocation(prob, uD, return_matrix: bool = False):
+    """Collocation solution alpha (nrhs, n) from u_D (nrhs, n_rhs_pts) at
+    igs_rhs_points (host arrays).  Returns alpha, or (alpha, Ac, nodes) with
+    the n x n collocation matrix and the collocation node indices."""
+    u = _f64(uD)
+    if u.ndim == 1:
+        u = u[None, :]
+    nrhs = u.shape[0]
+    n = igs_problem_info(prob).n
+    alpha = np.empty((nrhs, n), dtype=np.float64)
+    Ac = np.empty((n, n), dtype=np.float64) if return_matrix else None
+    nodes = np.empty(n, dtype=np.int32) if return_matrix else None
+    _check(_lib.igs_collocation(prob, _ptr(u), nrhs, _ptr(alpha), _ptr(Ac), _ptr(nodes), IGS_MEM_HOST),
+           "igs_collocation")
+    return (alpha, Ac, nodes) if return_matrix else alpha
 
 
 def igs_get_rules(prob, with_ws: bool = False):

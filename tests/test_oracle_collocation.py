@@ -119,3 +119,12 @@ def test_planted_collocation_mistake_is_caught(monkeypatch, mutation):
         except AssertionError:
             caught.append(pin.__name__)
     assert caught
+
+
+def test_matrix_rows_match_full():
+    c = wl.star_curve()
+    full, m = oc.collocation_matrix(c, 24, 3, 2)
+    rows = np.array([0, 7, 23])
+    part, mr = oc.collocation_matrix(c, 24, 3, 2, rows)
+    assert np.array_equal(mr, m[rows])
+    np.testing.assert_allclose(part, full[rows], rtol=1e-13, atol=1e-16)
