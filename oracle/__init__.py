@@ -23,6 +23,8 @@ Modules
                  representation formula (Sect. 2)
   collocation    collocation form of the single-layer equation with the same rules
                  (Sect. 7 remark), LU solve
+  sampled        single entries A[i, j] from local pieces of the same definitions
+                 (parity at sizes where the dense arrays do not fit)
 
 Pins: every function is checked in ``tests/test_oracle_*.py`` against
 quantities the paper or mathematics fixes (exactness, closed forms, adaptive
@@ -30,4 +32,4 @@ quadrature, circle eigenvalues, manufactured solutions, Table 2 condition
 numbers).  Functions without such a pin say "parity unpinned" in their
 docstring; at present there are none.
 """
-from . import bspline, discretization, rules, assembly, collocation  # noqa: F401
+from . import bspline, discretization, rules, assembly, collocation, sampled  # noqa: F401
