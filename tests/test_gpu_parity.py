@@ -223,6 +223,30 @@ def test_full_size_star_rhs_and_solve(ctx, tier, tol):
         p.close()
 
 
+@pytest.mark.parametrize("tier,tol", [("FP64", 1e-12), ("MIXED", 1e-6)])
+def test_c3_size_sampled_entries(ctx, tier, tol):
+    """n = 16384, p = 4, N_ref = 2 star (the precision workload): entries
+    sampled on and near the diagonal, at the seam corners, in the far field
+    and at the ragged end, against the oracle's one-entry assembly."""
+    from oracle.sampled import EntrySampler
+    curve = wl.star_curve()
+    n, d, nref = 16384, 4, 2
+    pairs = [(0, 0), (0, 1), (0, 5), (0, n - 1), (n - 1, 0), (n - 1, n - 1), (n - 2, n - 1), (4096, 4096),
+             (4096, 4100), (4096, 4160), (8191, 12000), (100, 9000), (16000, 16383), (5, 8192)]
+    if "c3" not in _FULL_SIZE_REF:
+        S = EntrySampler(curve, n, d, nref)
+        _FULL_SIZE_REF["c3"] = np.array([S.entry(i, j) for i, j in pairs])
+    ref = _FULL_SIZE_REF["c3"]
+    p = Prob(ctx, curve, n, d, nref, getattr(lib(), "IGS_" + tier))
+    try:
+        A = p.assemble(np.float32 if tier == "MIXED" else np.float64)
+        got = np.array([float(A[i, j]) for i, j in pairs])
+        del A
+        assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), (tier, np.abs(got - ref) / np.abs(ref))
+    finally:
+        p.close()
+
+
 def test_invalid_arguments(ctx):
     g = lib()
     c = wl.star_curve()
