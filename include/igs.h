@@ -252,6 +252,17 @@ int igs_eval_potential(igs_prob prob, const double* alpha, const double* uD, int
 int igs_collocation(igs_prob prob, const double* uD, int nrhs, double* alpha_out, double* Ac_out, int32_t* nodes_out,
                     int mem);
 
+/* Right-hand side and solve in one call: the same result as igs_build_rhs
+ * followed by igs_solve(prob, NULL, ...), bit for bit.  The right-hand side
+ * (Sect. 5) is computed on an auxiliary stream of the problem while the
+ * factorisation (eq. sistlin) runs on the context stream, so the two
+ * overlap when the problem is not yet factored.
+ *   uD:        `mem` memory, nrhs x n_rhs_pts (the layout of igs_build_rhs).
+ *   alpha_out: `mem` memory, nrhs x n.  resid_out: NULL or HOST, nrhs values.
+ * The right-hand side is kept in the problem as after igs_build_rhs.
+ * Errors: INVALID_ARG, STATE (not assembled), NOT_SPD, NOT_CONVERGED, TIMEOUT, CUDA. */
+int igs_solve_data(igs_prob prob, const double* uD, int nrhs, double* alpha_out, double* resid_out, int mem);
+
 /* Download the assembled A (eq. IK1e2 plus IK1e2_bis, Sect. 5) without
  * assembling again, e.g. after igs_batch_assemble.  Arguments as for
  * igs_assemble's A_out, ld, mem, dtype.  Errors: INVALID_ARG, STATE (not

@@ -272,6 +272,11 @@ int igs_destroy_problem(igs_prob p) {
                      p->d_flag, p->d_geo, p->d_nodes,
                      p->d_P, p->d_Q, p->d_A, p->d_F, p->d_As64, p->d_diagL, p->d_diagLinv, p->d_tflags, p->d_tpub, p->d_timg,
                      p->d_beta, p->d_rhs_geo, p->d_rhs_w, p->d_rhs_t};
+    if (p->aux_stream) {
+        cudaStreamSynchronize(p->aux_stream);
+        cudaStreamDestroy(p->aux_stream);
+        p->aux_stream = nullptr;
+    }
     for (void* q : ptrs) dev_free_raw(p, q);
     if (p->factor_exec) cudaGraphExecDestroy(p->factor_exec);
     cudaStreamSynchronize(p->geom->ctx->stream);
@@ -516,6 +521,44 @@ int igs_collocation(igs_prob p, const double* uD, int nrhs, double* alpha_out, d
         throw;
     }
     if (tmp) dev_free(p, tmp);
+    p->timing.kernel_launches = p->launches;
+    API_END
+}
+
+int igs_solve_data(igs_prob p, const double* uD, int nrhs, double* alpha_out, double* resid_out, int mem) {
+    API_BEGIN
+    REQUIRE(p && uD && alpha_out, IGS_E_INVALID_ARG, "NULL argument");
+    REQUIRE(nrhs >= 1 && nrhs <= 8, IGS_E_INVALID_ARG, "nrhs must be in [1, 8]");
+    REQUIRE(mem == IGS_MEM_HOST || mem == IGS_MEM_DEVICE, IGS_E_INVALID_ARG, "bad mem kind");
+    REQUIRE(p->assembled, IGS_E_STATE, "assemble before solve");
+    IGS_CUDA(cudaSetDevice(p->geom->ctx->device));
+    cudaStream_t s = p->geom->ctx->stream;
+    p->launches = 0;
+    rhs_prepare(p);
+    const Plan& P = p->plan;
+    const size_t nu = (size_t)nrhs * (P.Nq + p->Ng), na = (size_t)nrhs * P.n;
+    const double* d_uD = uD;
+    double* d_alpha = alpha_out;
+    double* tmp = nullptr;
+    if (mem == IGS_MEM_HOST) {
+        tmp = (double*)dev_alloc(p, sizeof(double) * (nu + na));
+        IGS_CUDA(cudaMemcpyAsync(tmp, uD, sizeof(double) * nu, cudaMemcpyHostToDevice, s));
+        d_uD = tmp;
+        d_alpha = tmp + nu;
+    }
+    std::vector<double> res(nrhs, 0.0);
+    try {
+        solve_with_data(p, d_uD, nrhs, d_alpha, res.data());
+        if (tmp) {
+            IGS_CUDA(cudaMemcpyAsync(alpha_out, d_alpha, sizeof(double) * na, cudaMemcpyDeviceToHost, s));
+            IGS_CUDA(cudaStreamSynchronize(s));
+        }
+    } catch (...) {
+        if (tmp) { cudaStreamSynchronize(s); dev_free(p, tmp); }
+        throw;
+    }
+    if (tmp) dev_free(p, tmp);
+    if (resid_out) std::copy(res.begin(), res.end(), resid_out);
     p->timing.kernel_launches = p->launches;
     API_END
 }

@@ -230,7 +230,7 @@ void collocation_solve(igs_prob p, const double* d_uD, int nrhs, double* d_alpha
                                      ac_mem == IGS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
         const double* vsum = nullptr;
         int np = 0;
-        rhs_node_potentials(p, d_uD, nrhs, scratch, &vsum, &np);
+        rhs_node_potentials(p, d_uD, nrhs, scratch, &vsum, &np, s);
         k_colloc_rhs<<<dim3((n + 127) / 128, nrhs), 128, 0, s>>>(n, Nq, nrhs, d_cn, d_uD, Nq + p->Ng, vsum, np, beta);
         IGS_CUDA(cudaGetLastError());
         for (int k = 0; k < n; ++k) {

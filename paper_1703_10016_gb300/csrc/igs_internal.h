@@ -135,6 +135,7 @@ struct igs_prob_s {
     unsigned long long* d_tpub = nullptr;  // [8][n] published FP32 solution words (value, epoch)
     float* d_timg = nullptr;      // two outer blocks of split factor columns (MIXED tier, n >= 4096)
     int tepoch = 0;               // flag value of the current triangular solve
+    cudaStream_t aux_stream = nullptr;   // right-hand side beside the factorisation (igs_solve_data)
     bool coop_ok = false;         // cooperative launch available
     double* d_As64 = nullptr;     // (A+A^T)/2 in FP64 for residuals (MIXED)
     int rhs_n = 0;
@@ -185,7 +186,10 @@ void rhs_prepare(igs_prob p);
 void rhs_build(igs_prob p, const double* d_uD, int nrhs);
 void rhs_build_noalloc(igs_prob p, const double* d_uD, int nrhs, double* d_beta);
 int rhs_slots(const igs_prob p);   // partial-sum slots (each nrhs x N_quad doubles) of the node potentials
-void rhs_node_potentials(igs_prob p, const double* d_uD, int nrhs, double* scratch, const double** vsum, int* np);
+void rhs_node_potentials(igs_prob p, const double* d_uD, int nrhs, double* scratch, const double** vsum, int* np,
+                         cudaStream_t s);
+void rhs_compute(igs_prob p, const double* d_uD, int nrhs, double* d_beta, double* scratch, cudaStream_t s);
+void solve_with_data(igs_prob p, const double* d_uD, int nrhs, double* d_alpha, double* resid);
 void collocation_solve(igs_prob p, const double* d_uD, int nrhs, double* d_alpha, double* Ac_out, int ac_mem,
                        int* nodes_out);
 void potential_eval(igs_prob p, const double* d_alpha, const double* d_uD, int nrhs, const double* d_xy,

@@ -304,9 +304,8 @@ int rhs_slots(const igs_prob p) {
 }
 
 template <int NR>
-static void launch_far(igs_prob p, const double* d_uD, int ldu, double* part) {
+static void launch_far(igs_prob p, const double* d_uD, int ldu, double* part, cudaStream_t s) {
     const Plan& P = p->plan;
-    cudaStream_t s = p->geom->ctx->stream;
     if (p->precision == IGS_MIXED)
         k_double_layer_f<NR><<<dim3((P.Nq + kFarNodes - 1) / kFarNodes, kSplit), kFarNodes * kFarParts, 0, s>>>(
             P.Nq, p->Ng, p->d_geo, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, part);
@@ -319,21 +318,21 @@ static void launch_far(igs_prob p, const double* d_uD, int ldu, double* part) {
 // Double-layer potentials v_k(eta_m) at the nodes of a closed curve, as
 // partial sums in `scratch` (rhs_slots x nrhs x N_quad doubles): v_k(eta_m) is
 // the sum over s < *np of vsum[(s nrhs + k) N_quad + m], in that order.
-void rhs_node_potentials(igs_prob p, const double* d_uD, int nrhs, double* scratch, const double** vsum, int* np) {
+void rhs_node_potentials(igs_prob p, const double* d_uD, int nrhs, double* scratch, const double** vsum, int* np,
+                         cudaStream_t s) {
     const Plan& P = p->plan;
-    cudaStream_t s = p->geom->ctx->stream;
     const int ldu = P.Nq + p->Ng;
     *np = rhs_slots(p);
     *vsum = scratch;
     switch (nrhs) {
-        case 1: launch_far<1>(p, d_uD, ldu, scratch); break;
-        case 2: launch_far<2>(p, d_uD, ldu, scratch); break;
-        case 3: launch_far<3>(p, d_uD, ldu, scratch); break;
-        case 4: launch_far<4>(p, d_uD, ldu, scratch); break;
-        case 5: launch_far<5>(p, d_uD, ldu, scratch); break;
-        case 6: launch_far<6>(p, d_uD, ldu, scratch); break;
-        case 7: launch_far<7>(p, d_uD, ldu, scratch); break;
-        default: launch_far<8>(p, d_uD, ldu, scratch); break;
+        case 1: launch_far<1>(p, d_uD, ldu, scratch, s); break;
+        case 2: launch_far<2>(p, d_uD, ldu, scratch, s); break;
+        case 3: launch_far<3>(p, d_uD, ldu, scratch, s); break;
+        case 4: launch_far<4>(p, d_uD, ldu, scratch, s); break;
+        case 5: launch_far<5>(p, d_uD, ldu, scratch, s); break;
+        case 6: launch_far<6>(p, d_uD, ldu, scratch, s); break;
+        case 7: launch_far<7>(p, d_uD, ldu, scratch, s); break;
+        default: launch_far<8>(p, d_uD, ldu, scratch, s); break;
     }
     p->launches++;
     if (p->precision == IGS_MIXED) {
@@ -350,14 +349,14 @@ void rhs_node_potentials(igs_prob p, const double* d_uD, int nrhs, double* scrat
     }
 }
 
-// beta for nrhs data sets into d_beta, partial sums in `scratch` (rhs_slots x nrhs x N_quad doubles).
-static void rhs_compute(igs_prob p, const double* d_uD, int nrhs, double* d_beta, double* scratch) {
+// beta for nrhs data sets into d_beta, partial sums in `scratch` (rhs_slots x nrhs x N_quad doubles),
+// every kernel on stream s.
+void rhs_compute(igs_prob p, const double* d_uD, int nrhs, double* d_beta, double* scratch, cudaStream_t s) {
     const Plan& P = p->plan;
-    cudaStream_t s = p->geom->ctx->stream;
     const int ldu = P.Nq + p->Ng;
     int np = 0;
     const double* vsum = scratch;
-    if (P.closed) rhs_node_potentials(p, d_uD, nrhs, scratch, &vsum, &np);
+    if (P.closed) rhs_node_potentials(p, d_uD, nrhs, scratch, &vsum, &np, s);
     dim3 grid((P.n * kBetaLanes + 127) / 128, nrhs);
     k_beta<<<grid, 128, 0, s>>>(P.n, P.Nq, P.d, nrhs, P.closed, p->d_lo, p->d_hi, p->d_jfirst, p->d_W, p->d_geo, d_uD,
                                 ldu, vsum, np, d_beta);
@@ -375,7 +374,7 @@ void rhs_build(igs_prob p, const double* d_uD, int nrhs) {
     if (p->d_beta && p->rhs_n < nrhs) dev_free(p, p->d_beta);
     if (!p->d_beta) p->d_beta = (double*)dev_alloc(p, sizeof(double) * (size_t)kMaxRhs * P.n);
     p->rhs_n = nrhs;
-    rhs_compute(p, d_uD, nrhs, p->d_beta, scratch);
+    rhs_compute(p, d_uD, nrhs, p->d_beta, scratch, s);
     if (scratch) {
         IGS_CUDA(cudaStreamSynchronize(s));
         dev_free(p, scratch);
@@ -427,7 +426,7 @@ void rhs_build_noalloc(igs_prob p, const double* d_uD, int nrhs, double* d_beta)
                                            " scratch doubles (9 x n_quad x nrhs), more than the fixed " +
                                            std::to_string(kNoAllocScratchDoubles));
     double* scratch = scratch_address(p->geom->ctx->device);
-    rhs_compute(p, d_uD, nrhs, d_beta, scratch);
+    rhs_compute(p, d_uD, nrhs, d_beta, scratch, p->geom->ctx->stream);
 }
 
 }  // namespace igs

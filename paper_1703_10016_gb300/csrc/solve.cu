@@ -1645,4 +1645,61 @@ void solve_system(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double*
     cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
 }
 
+// Right-hand side and solve in one call: the right-hand side kernels run on
+// the problem's auxiliary stream beside the factorisation on the context
+// stream (the two are independent: the factor reads A, the right-hand side
+// the rules, the node geometry and u_D), and the refinement waits for both.
+// Buffers are allocated on the context stream before the fork; the scratch is
+// freed on it after the join.
+void solve_with_data(igs_prob p, const double* d_uD, int nrhs, double* d_alpha, double* resid) {
+    cudaStream_t s = p->geom->ctx->stream;
+    const Plan& P = p->plan;
+    if (nrhs < 1 || nrhs > 8) throw Error(IGS_E_INVALID_ARG, "nrhs must be in [1, 8]");
+    if (!p->aux_stream) IGS_CUDA(cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking));
+    cudaStream_t sr = p->aux_stream;
+    if (!p->d_beta) p->d_beta = (double*)dev_alloc(p, sizeof(double) * (size_t)8 * P.n);
+    p->rhs_n = nrhs;
+    const int np = rhs_slots(p);
+    double* scratch = np > 0 ? (double*)dev_alloc(p, sizeof(double) * (size_t)np * nrhs * P.Nq) : nullptr;
+    cudaEvent_t ev[6] = {};
+    bool forked = false;
+    try {
+        for (cudaEvent_t& e : ev) IGS_CUDA(cudaEventCreate(&e));
+        IGS_CUDA(cudaEventRecord(ev[0], s));                 // fork: buffers and u_D are ready
+        IGS_CUDA(cudaStreamWaitEvent(sr, ev[0], 0));
+        forked = true;
+        IGS_CUDA(cudaEventRecord(ev[1], sr));
+        rhs_compute(p, d_uD, nrhs, p->d_beta, scratch, sr);
+        IGS_CUDA(cudaEventRecord(ev[2], sr));                // join
+        IGS_CUDA(cudaEventRecord(ev[3], s));
+        const bool mixed = p->precision == IGS_MIXED;
+        if (!p->factored) {
+            if (mixed) prepare_factor<float>(p, s);
+            else prepare_factor<double>(p, s);
+        }
+        IGS_CUDA(cudaEventRecord(ev[4], s));
+        IGS_CUDA(cudaStreamWaitEvent(s, ev[2], 0));
+        if (mixed) refine<float>(p, p->d_beta, nrhs, d_alpha, resid, s, 30, 1e-10);
+        else refine<double>(p, p->d_beta, nrhs, d_alpha, resid, s, 1, 1e-10);
+        IGS_CUDA(cudaEventRecord(ev[5], s));
+        IGS_CUDA(cudaEventSynchronize(ev[5]));
+        float r_ms = 0, f_ms = 0, s_ms = 0;
+        cudaEventElapsedTime(&r_ms, ev[1], ev[2]);
+        cudaEventElapsedTime(&f_ms, ev[3], ev[4]);
+        cudaEventElapsedTime(&s_ms, ev[4], ev[5]);
+        p->timing.rhs_ms = r_ms;
+        p->timing.factor_ms = f_ms;
+        p->timing.solve_ms = s_ms;
+    } catch (...) {
+        if (forked) cudaStreamSynchronize(sr);
+        cudaStreamSynchronize(s);
+        for (cudaEvent_t& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (scratch) dev_free(p, scratch);
+        throw;
+    }
+    for (cudaEvent_t& e : ev) cudaEventDestroy(e);
+    if (scratch) dev_free(p, scratch);
+}
+
 }  // namespace igs

@@ -33,7 +33,7 @@ EXPORTED = [
     "igs_create", "igs_destroy", "igs_last_error", "igs_create_geometry", "igs_destroy_geometry",
     "igs_create_problem", "igs_destroy_problem", "igs_set_geometry", "igs_problem_info", "igs_problem_timing",
     "igs_build_weighted_rules", "igs_assemble", "igs_rhs_points", "igs_build_rhs", "igs_build_rhs_noalloc",
-    "igs_solve", "igs_eval_potential", "igs_collocation",
+    "igs_solve", "igs_solve_data", "igs_eval_potential", "igs_collocation",
     "igs_get_rules", "igs_get_node_geometry",
     "igs_get_matrix", "igs_batch_create", "igs_batch_destroy", "igs_batch_assemble", "igs_batch_tune", "igs_batch_set_config",
     "igs_batch_get_config",
@@ -111,6 +111,7 @@ def _load() -> C.CDLL:
         "igs_build_rhs": [vp, vp, i32, vp, i32],
         "igs_build_rhs_noalloc": [vp, vp, i32, vp],
         "igs_solve": [vp, vp, i32, vp, vp, i32],
+        "igs_solve_data": [vp, vp, i32, vp, vp, i32],
         "igs_eval_potential": [vp, vp, vp, i32, vp, i64, vp, i32],
         "igs_collocation": [vp, vp, i32, vp, vp, vp, i32],
         "igs_get_rules": [vp, vp, vp, vp, vp],
@@ -294,6 +295,30 @@ def igs_solve(prob, beta=None, nrhs: int = 1, alpha_out=None, mem: int = IGS_MEM
     res = np.empty(nrhs, dtype=np.float64)
     _check(_lib.igs_solve(prob, _ptr(beta), int(nrhs), _ptr(alpha_out), _ptr(res), int(mem)), "igs_solve")
     return alpha_out, res
+
+
+def igs_solve_data(prob, uD, alpha_out=None):
+    """Right-hand side from u_D (nrhs, n_rhs_pts) and solve, overlapped on the
+    GPU; returns (alpha, residuals).  Host arrays, or CUDA tensors (device
+    memory; alpha_out, if given, a CUDA tensor nrhs x n)."""
+    n = igs_problem_info(prob).n
+    if hasattr(uD, "is_cuda") and uD.is_cuda:
+        u = uD if uD.dim() == 2 else uD[None, :]
+        nrhs = int(u.shape[0])
+        if alpha_out is None:
+            import torch
+            alpha_out = torch.empty((nrhs, n), dtype=torch.float64, device=u.device)
+        res = np.empty(nrhs, dtype=np.float64)
+        _check(_lib.igs_solve_data(prob, _ptr(u), nrhs, _ptr(alpha_out), _ptr(res), IGS_MEM_DEVICE), "igs_solve_data")
+        return alpha_out, res
+    u = _f64(uD)
+    if u.ndim == 1:
+        u = u[None, :]
+    nrhs = u.shape[0]
+    alpha = np.empty((nrhs, n), dtype=np.float64)
+    res = np.empty(nrhs, dtype=np.float64)
+    _check(_lib.igs_solve_data(prob, _ptr(u), nrhs, _ptr(alpha), _ptr(res), IGS_MEM_HOST), "igs_solve_data")
+    return alpha, res
 
 
 def igs_eval_potential(prob, alpha, uD, xy, u_out=None):
