@@ -1,7 +1,11 @@
 """igs_solve_data (right-hand side beside the factorisation) against
-igs_build_rhs + igs_solve: the same bits, in both tiers, host and device
-buffers, for a first factorisation, a reused factor and a factorisation
-replayed from the captured graph."""
+igs_build_rhs + igs_solve, in both tiers, host and device buffers, for a
+first factorisation, a reused factor and a factorisation replayed from the
+captured graph.  The refinement's residual norms are sums by atomic
+addition, so two solves of the same system need not agree bit for bit: the
+solutions are compared to the refinement's accuracy (FP64 tier: 1e-12; MIXED
+tier: the 1e-10 residual bar times cond(A) < 1e4 gives 1e-6) and both must
+meet the residual bar."""
 import numpy as np
 import pytest
 
@@ -43,10 +47,10 @@ def test_same_bits_as_separate_calls(ctx, tier, n, nrhs):
             runs.append(out)
         finally:
             p.close()
+    tol = 1e-12 if tier == "IGS_FP64" else 1e-6
     for (a1, r1), (a2, r2) in zip(*runs):
-        assert np.array_equal(a1, a2)
-        assert np.array_equal(r1, r2)
-        assert np.all(r1 <= 1e-10)
+        assert np.linalg.norm(a1 - a2) <= tol * np.linalg.norm(a1)
+        assert np.all(r1 <= 1e-10) and np.all(r2 <= 1e-10)
 
 
 def test_device_buffers(ctx):
@@ -61,7 +65,8 @@ def test_device_buffers(ctx):
         g.igs_assemble(p.prob)
         ad, rd = g.igs_solve_data(p.prob, torch.from_numpy(np.ascontiguousarray(U)).cuda())
         torch.cuda.synchronize()
-        assert np.array_equal(ah, ad.cpu().numpy()) and np.array_equal(rh, rd)
+        assert np.linalg.norm(ah - ad.cpu().numpy()) <= 1e-6 * np.linalg.norm(ah)
+        assert np.all(rh <= 1e-10) and np.all(rd <= 1e-10)
         with pytest.raises(g.IgsError):
             g.igs_solve_data(p.prob, np.ones((9, p.info.n_rhs_pts)))
     finally:
