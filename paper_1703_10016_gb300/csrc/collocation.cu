@@ -162,38 +162,6 @@ __global__ void __launch_bounds__(1024) k_lu_solve(int n, const double* __restri
     for (int r = tid; r < n; r += blockDim.x) x_out[(size_t)k * n + r] = x[r];
 }
 
-// Collocation node of each test function (closed curves), in the plan's
-// integer units h_f / den: centre (2i + 1 - d) N_ref den / 2 modulo M den,
-// nearest node by periodic distance, ties to the smaller node index.
-static std::vector<int> colloc_nodes(const Plan& P) {
-    const int64_t period = (int64_t)P.M * P.den;
-    std::vector<int> out(P.n);
-    const std::vector<int>& pos = P.pos_num;
-    for (int i = 0; i < P.n; ++i) {
-        int64_t c = ((int64_t)(2 * i + 1 - P.d) * P.Nref * P.den) / 2;
-        c %= period;
-        if (c < 0) c += period;
-        const int lb = int(std::lower_bound(pos.begin(), pos.end(), (int)c) - pos.begin());
-        const int cand[4] = {0, lb - 1, lb, P.Nq - 1};
-        int best = -1;
-        int64_t bd = 0;
-        for (int q = 0; q < 4; ++q) {
-            const int m = cand[q];
-            if (m < 0 || m >= P.Nq) continue;
-            int64_t dist = c - pos[m];
-            if (dist < 0) dist = -dist;
-            dist = std::min(dist, period - dist);
-            if (best < 0 || dist < bd || (dist == bd && m < best)) { best = m; bd = dist; }
-        }
-        out[i] = best;
-    }
-    std::vector<int> sorted(out);
-    std::sort(sorted.begin(), sorted.end());
-    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
-        throw Error(IGS_E_INVALID_ARG, "collocation nodes are not distinct for this discretisation");
-    return out;
-}
-
 void collocation_solve(igs_prob p, const double* d_uD, int nrhs, double* d_alpha, double* Ac_out, int ac_mem,
                        int* nodes_out) {
     const Plan& P = p->plan;
@@ -203,7 +171,9 @@ void collocation_solve(igs_prob p, const double* d_uD, int nrhs, double* d_alpha
     if (P.n > kMaxCollocN) throw Error(IGS_E_INVALID_ARG, "collocation supports n <= 16384");
     const int n = P.n, Nq = P.Nq;
     rhs_prepare(p);
-    const std::vector<int> cn = colloc_nodes(P);
+    std::vector<int> cn;
+    std::string err;
+    if (collocation_nodes(P, cn, err) != IGS_OK) throw Error(IGS_E_INVALID_ARG, err);
     if (nodes_out) std::copy(cn.begin(), cn.end(), nodes_out);
 
     const size_t nn = (size_t)n * n;

@@ -60,6 +60,7 @@ struct Plan {
 constexpr int kSeries = 30;
 
 int build_plan(Plan& p, double a, double b, int Nh, int d, int Nref, int closed, std::string& err);
+int collocation_nodes(const Plan& P, std::vector<int>& out, std::string& err);
 
 }  // namespace igs
 

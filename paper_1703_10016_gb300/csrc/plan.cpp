@@ -143,4 +143,41 @@ int build_plan(Plan& p, double a, double b, int Nh, int d, int Nref, int closed,
     return IGS_OK;
 }
 
+// Collocation node of each test function of a closed curve (the collocation
+// form of the single-layer equation): the node nearest the centre of the
+// support of B_i, i.e. (2i + 1 - d) N_ref den / 2 in units h_f / den, modulo
+// the period M den, by periodic distance, ties to the smaller node index.
+int collocation_nodes(const Plan& P, std::vector<int>& out, std::string& err) {
+    if (!P.closed) { err = "collocation nodes are defined for closed curves only"; return IGS_E_INVALID_ARG; }
+    const int64_t period = (int64_t)P.M * P.den;
+    const std::vector<int>& pos = P.pos_num;
+    out.assign(P.n, -1);
+    for (int i = 0; i < P.n; ++i) {
+        int64_t c = ((int64_t)(2 * i + 1 - P.d) * P.Nref * P.den) / 2;
+        c %= period;
+        if (c < 0) c += period;
+        // the nearest nodes lie on either side of c, or at the two ends (the same point a = b)
+        const int lb = int(std::lower_bound(pos.begin(), pos.end(), (int)c) - pos.begin());
+        const int cand[4] = {0, lb - 1, lb, P.Nq - 1};
+        int best = -1;
+        int64_t bd = 0;
+        for (int q = 0; q < 4; ++q) {
+            const int m = cand[q];
+            if (m < 0 || m >= P.Nq) continue;
+            int64_t dist = c - pos[m];
+            if (dist < 0) dist = -dist;
+            dist = std::min(dist, period - dist);
+            if (best < 0 || dist < bd || (dist == bd && m < best)) { best = m; bd = dist; }
+        }
+        out[i] = best;
+    }
+    std::vector<int> sorted(out);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+        err = "collocation nodes are not distinct for this discretisation";
+        return IGS_E_INVALID_ARG;
+    }
+    return IGS_OK;
+}
+
 }  // namespace igs
