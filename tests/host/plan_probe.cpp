@@ -1,6 +1,7 @@
 // Host-logic probe for the CPU tests: prints the planner's integer description
-// of one discretisation (node positions, the node ranges N^(i) of Sect. 4.1 and,
-// for a closed curve, the collocation nodes).  Links only the planner; no GPU
+// of one discretisation (node positions, the node bands, the node ranges N^(i)
+// and the exactness ranges J^(i) of Sect. 4.1 and, for a closed curve, the
+// collocation nodes).  Links only the planner; no GPU
 // is touched.  Usage: plan_probe n_elems degree n_ref closed
 #include <cstdio>
 #include <cstdlib>
@@ -28,6 +29,12 @@ int main(int argc, char** argv) {
     row("pos", P.pos_num);
     row("lo", P.lo);
     row("hi", P.hi);
+    row("jfirst", P.jfirst);
+    row("member", P.member);
+    row("jlo1", P.jlo1);
+    row("jhi1", P.jhi1);
+    row("jlo2", P.jlo2);
+    row("jhi2", P.jhi2);
     if (closed) {
         std::vector<int> c;
         if (igs::collocation_nodes(P, c, err) == IGS_OK) row("colloc", c);

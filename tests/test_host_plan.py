@@ -4,8 +4,9 @@ The probe in tests/host/plan_probe.cpp links only the planner (plan.cpp) and
 prints its integer description of a discretisation; the oracle's
 Discretization fixes the same quantities from Sects. 3-4: the node positions,
 the node sets N^(i) of Sect. 4.1 (the planner stores them as contiguous
-unrolled ranges, physical node = u mod N_quad) and the collocation nodes of
-the collocation form (oracle.collocation.collocation_nodes).
+unrolled ranges, physical node = u mod N_quad), the exactness sets J^(i),
+the test functions non-zero at each node, and the collocation nodes of the
+collocation form (oracle.collocation.collocation_nodes).
 """
 import os
 import shutil
@@ -62,5 +63,16 @@ def test_planner_matches_oracle(probe, n, d, nref, closed):
     for i in range(disc.n):
         nodes = set(int(u) % disc.Nq for u in range(got["lo"][i], got["hi"][i] + 1))
         assert nodes == set(int(m) for m in disc.support_nodes(i)), i
+    # J^(i): one or two ranges of exactness functions
+    for i in range(disc.n):
+        js = set(range(got["jlo1"][i], got["jhi1"][i] + 1)) | set(range(got["jlo2"][i], got["jhi2"][i] + 1))
+        assert js == set(int(j) for j in disc.overlapping_fine(i)), i
+    # node bands: B_{jfirst + r}(eta_m) != 0 exactly for the member bits r (unrolled test index);
+    # at a knot the end of a support evaluates to rounding-level values in floating point
+    Bt = disc.test_basis(disc.eta)[0]                    # (n, N_quad), cyclic for closed curves
+    for m in range(disc.Nq):
+        nz = set(int(i) for i in np.nonzero(np.abs(Bt[:, m]) > 1e-12)[0])
+        band = set((got["jfirst"][m] + r) % disc.n for r in range(d + 1) if (got["member"][m] >> r) & 1)
+        assert band == nz, m
     if closed:
         np.testing.assert_array_equal(got["colloc"], oc.collocation_nodes(disc))
