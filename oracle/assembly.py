@@ -36,7 +36,7 @@ import scipy.linalg as sla
 from . import bspline, rules
 from .discretization import Discretization
 
-G_RHS = 4                      # Gauss points per refined element for the b2 inner integral
+G_RHS = 8                      # Gauss points per refined element for the b2 inner integral
 
 
 def make_discretization(curve, n_elems: int, degree: int, n_ref: int) -> Discretization:

@@ -14,7 +14,7 @@ namespace igs {
 constexpr int kMaxDegree = 5;
 constexpr int kMaxNref = 4;
 constexpr int kMaxGeomDegree = 7;
-constexpr int kGaussRhs = 4;          // Gauss points per refined element for the b2 inner rule
+constexpr int kGaussRhs = 8;          // Gauss points per refined element for the b2 inner rule
 constexpr double kPi = 3.14159265358979323846;
 
 // ------------------------------------------------------------------ errors

@@ -71,6 +71,7 @@ int64_t estimate_bytes(const igs_request& r) {
     else b += ncols * Nq * 8 + ncols * NE * 8 + (2 * B + 2 * R + 4) * Nq * 12 + ncols * 1024 * D1 * 8;
     b += 2 * M * 2 * D1 * D1 * 8;                       // element-moment table
     b += Nq * 160 + n * 64 * 2 * tsz + (int64_t)r.nrhs * (n * 40 + M * 40);
+    b += M * igs::kGaussRhs * (7 * 8 + (int64_t)r.nrhs * 8);  // b2 rule: points, weights, geometry, u_D there
     b += n * 8 * 8;                                      // published solution words
     if (r.precision == IGS_MIXED && n >= 4096)           // split operand images of two outer blocks
         b += (int64_t)2 * 8 * 2 * ((n + 127) / 128) * 2048 * 4;
