@@ -192,7 +192,10 @@ int igs_build_rhs(igs_prob prob, const double* uD, int nrhs, double* beta_out, i
  * allocating library routine.
  *   uD:       DEVICE, nrhs x n_rhs_pts (layout of igs_build_rhs)
  *   beta_out: DEVICE, nrhs x n, written (the problem's own beta is not changed)
- * Limits: 1 <= nrhs <= 8 and 9 * n_quad * nrhs <= 2097152 (else INVALID_ARG).
+ * Limits: 1 <= nrhs <= 8 and slots * n_quad * nrhs <= 2097152 doubles (else
+ * INVALID_ARG), with slots = 9 for a MIXED closed curve, 8 for an FP64 closed
+ * curve and 0 for an open arc (no double-layer term, so no scratch and no
+ * size limit beyond nrhs).
  * Preconditions: the rules, the node geometry and the rhs points exist (call
  * igs_assemble and igs_rhs_points first), else STATE.  The work is queued on
  * the context stream and not waited for.  The first call on a device looks up

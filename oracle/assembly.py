@@ -129,9 +129,11 @@ def kernel_Kbar(f_s, f_t, f1_t):
     return (dx * f1_t[1][None, :] - dy * f1_t[0][None, :]) / (dx * dx + dy * dy)
 
 
-def build_rhs(curve, n_elems: int, degree: int, n_ref: int, uD_nodes, uD_gauss) -> np.ndarray:
+def build_rhs(curve, n_elems: int, degree: int, n_ref: int, uD_nodes, uD_gauss, terms: bool = False):
     """beta (n x nrhs).  uD_nodes: (Nq, nrhs) values of u_D at eta;
-    uD_gauss: (Ng, nrhs) values at the Gauss points (closed curves only)."""
+    uD_gauss: (Ng, nrhs) values at the Gauss points (closed curves only).
+    With terms=True returns (beta, b1/2, b2/(2 pi)) for a closed curve and
+    (beta, b1, 0) for an open arc: the two terms whose difference is beta."""
     disc = make_discretization(curve, n_elems, degree, n_ref)
     W = rules.regular_rules(disc)
     f, f1, J = geometry_at(curve, disc.eta)
@@ -139,19 +141,20 @@ def build_rhs(curve, n_elems: int, degree: int, n_ref: int, uD_nodes, uD_gauss) 
     uD_nodes = np.asarray(uD_nodes, np.float64).reshape(disc.Nq, -1)
     b1 = P.T @ uD_nodes
     if not disc.closed:
-        return b1
+        return (b1, b1, np.zeros_like(b1)) if terms else b1
     tg, wg = disc.fine_gauss(G_RHS)
     ft, f1t, _ = geometry_at(curve, tg)
     Kb = kernel_Kbar(f, ft, f1t)                         # (Nq, Ng)
     uD_gauss = np.asarray(uD_gauss, np.float64).reshape(len(tg), -1)
     b2 = P.T @ (Kb @ (wg[:, None] * uD_gauss))
-    return 0.5 * b1 - b2 / (2.0 * np.pi)
+    beta = 0.5 * b1 - b2 / (2.0 * np.pi)
+    return (beta, 0.5 * b1, b2 / (2.0 * np.pi)) if terms else beta
 
 
-def build_rhs_rows(curve, n_elems: int, degree: int, n_ref: int, rows, uD_nodes, uD_gauss) -> np.ndarray:
+def build_rhs_rows(curve, n_elems: int, degree: int, n_ref: int, rows, uD_nodes, uD_gauss, terms: bool = False):
     """Entries `rows` of beta (len(rows) x nrhs) by the same sums as build_rhs,
     restricted to the nodes N^(i) where P[n, i] can be non-zero (sampled
-    parity checks at large size)."""
+    parity checks at large size).  terms=True as in build_rhs."""
     disc = make_discretization(curve, n_elems, degree, n_ref)
     W = rules.regular_rules(disc)
     rows = np.asarray(rows)
@@ -161,13 +164,14 @@ def build_rhs_rows(curve, n_elems: int, degree: int, n_ref: int, rows, uD_nodes,
     uD_nodes = np.asarray(uD_nodes, np.float64).reshape(disc.Nq, -1)
     b1 = P.T @ uD_nodes[need]
     if not disc.closed:
-        return b1
+        return (b1, b1, np.zeros_like(b1)) if terms else b1
     tg, wg = disc.fine_gauss(G_RHS)
     ft, f1t, _ = geometry_at(curve, tg)
     Kb = kernel_Kbar(f, ft, f1t)                         # (len(need), Ng)
     uD_gauss = np.asarray(uD_gauss, np.float64).reshape(len(tg), -1)
     b2 = P.T @ (Kb @ (wg[:, None] * uD_gauss))
-    return 0.5 * b1 - b2 / (2.0 * np.pi)
+    beta = 0.5 * b1 - b2 / (2.0 * np.pi)
+    return (beta, 0.5 * b1, b2 / (2.0 * np.pi)) if terms else beta
 
 
 # ----------------------------------------------------------------------------

@@ -420,10 +420,12 @@ void rhs_build_noalloc(igs_prob p, const double* d_uD, int nrhs, double* d_beta)
     if (!p->rules_ready || !p->geometry_ready || !p->d_rhs_geo)
         throw Error(IGS_E_STATE, "igs_build_rhs_noalloc needs the rules, the node geometry and the rhs points: "
                                  "call igs_assemble and igs_rhs_points first");
-    const size_t need = (size_t)rhs_slots(p) * nrhs * P.Nq;
+    const int slots = rhs_slots(p);
+    const size_t need = (size_t)slots * nrhs * P.Nq;
     if (need > kNoAllocScratchDoubles)
-        throw Error(IGS_E_INVALID_ARG, "igs_build_rhs_noalloc: needs " + std::to_string(need) +
-                                           " scratch doubles (9 x n_quad x nrhs), more than the fixed " +
+        throw Error(IGS_E_INVALID_ARG, "igs_build_rhs_noalloc: needs " + std::to_string(need) + " scratch doubles (" +
+                                           std::to_string(slots) + " slots x n_quad " + std::to_string(P.Nq) +
+                                           " x nrhs " + std::to_string(nrhs) + "), more than the fixed " +
                                            std::to_string(kNoAllocScratchDoubles));
     double* scratch = scratch_address(p->geom->ctx->device);
     rhs_compute(p, d_uD, nrhs, d_beta, scratch, p->geom->ctx->stream);

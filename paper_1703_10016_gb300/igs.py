@@ -257,11 +257,24 @@ def igs_rhs_points(prob) -> np.ndarray:
     return xy
 
 
+def _require_dev_f64(t, shape, where: str, what: str) -> None:
+    """The C ABI carries no sizes for device buffers: refuse, before the call,
+    a tensor the kernels would read or write out of bounds."""
+    ok = (hasattr(t, "is_cuda") and t.is_cuda and str(t.dtype) == "torch.float64"
+          and t.is_contiguous() and tuple(t.shape) == tuple(shape))
+    if not ok:
+        got = (f"{tuple(t.shape)} {t.dtype} {'cuda' if t.is_cuda else 'cpu'} "
+               f"{'contiguous' if t.is_contiguous() else 'strided'}") if hasattr(t, "is_cuda") else type(t).__name__
+        raise IgsError(IGS_E_INVALID_ARG, where,
+                       f"{what} must be a contiguous float64 CUDA tensor of shape {tuple(shape)}, got {got}")
+
+
 def igs_build_rhs(prob, uD, return_beta: bool = True):
     """uD: (nrhs, n_rhs_pts) values at igs_rhs_points: a host array, or a CUDA
     tensor (device memory; beta is then returned as a CUDA tensor)."""
     if hasattr(uD, "is_cuda") and uD.is_cuda:
         u = uD if uD.dim() == 2 else uD[None, :]
+        _require_dev_f64(u, (u.shape[0], igs_problem_info(prob).n_rhs_pts), "igs_build_rhs", "uD")
         beta = None
         if return_beta:
             import torch
@@ -280,7 +293,12 @@ def igs_build_rhs(prob, uD, return_beta: bool = True):
 def igs_build_rhs_noalloc(prob, uD, beta_out) -> None:
     """Right-hand side into caller-owned device memory without any device
     allocation (uD: CUDA tensor nrhs x n_rhs_pts; beta_out: CUDA tensor nrhs x n)."""
-    u = uD if uD.dim() == 2 else uD[None, :]
+    info = igs_problem_info(prob)
+    u = uD if (hasattr(uD, "dim") and uD.dim() == 2) else (uD[None, :] if hasattr(uD, "dim") else uD)
+    _require_dev_f64(u, (u.shape[0], info.n_rhs_pts), "igs_build_rhs_noalloc", "uD")
+    _require_dev_f64(beta_out, (u.shape[0], info.n), "igs_build_rhs_noalloc", "beta_out")
+    if beta_out.device != u.device:
+        raise IgsError(IGS_E_INVALID_ARG, "igs_build_rhs_noalloc", "uD and beta_out must be on the same device")
     _check(_lib.igs_build_rhs_noalloc(prob, _ptr(u), int(u.shape[0]), _ptr(beta_out)), "igs_build_rhs_noalloc")
 
 
@@ -305,9 +323,11 @@ def igs_solve_data(prob, uD, alpha_out=None):
     if hasattr(uD, "is_cuda") and uD.is_cuda:
         u = uD if uD.dim() == 2 else uD[None, :]
         nrhs = int(u.shape[0])
+        _require_dev_f64(u, (nrhs, igs_problem_info(prob).n_rhs_pts), "igs_solve_data", "uD")
         if alpha_out is None:
             import torch
             alpha_out = torch.empty((nrhs, n), dtype=torch.float64, device=u.device)
+        _require_dev_f64(alpha_out, (nrhs, n), "igs_solve_data", "alpha_out")
         res = np.empty(nrhs, dtype=np.float64)
         _check(_lib.igs_solve_data(prob, _ptr(u), nrhs, _ptr(alpha_out), _ptr(res), IGS_MEM_DEVICE), "igs_solve_data")
         return alpha_out, res
