@@ -428,6 +428,26 @@ int igs_get_node_geometry(igs_prob prob, double* xy, double* J);
  * 0 otherwise.  The CUDA context stays usable.  Errors: INVALID_ARG, CUDA. */
 int igs_selftest_wait(igs_ctx ctx, double budget_s, int* gave_up);
 
+/* Throughput of one arithmetic pipe of the context's GPU, measured by a probe
+ * kernel that fills every SM with independent dependency chains of one
+ * instruction kind (one warm-up launch, then one launch timed with CUDA
+ * events, 10-50 ms).  The paper has no counterpart: these are the measured
+ * denominators of the roofline fractions of the assembly and right-hand side
+ * kernels, which run on the FP32 FMA and special-function (MUFU) pipes.
+ *   kind IGS_PEAK_FP32_FMA: FP32 fused multiply-add, flop/s (2 per FMA)
+ *        IGS_PEAK_MUFU_LG2: lg2.approx.f32, instructions/s
+ *        IGS_PEAK_MUFU_RCP: rcp.approx.f32, instructions/s
+ *        IGS_PEAK_FP64_FMA: FP64 fused multiply-add, flop/s (2 per FMA)
+ * *rate (HOST) receives the rate, *ms (HOST, may be NULL) the timed launch's
+ * duration.  Allocates 1 KB of device memory for the duration of the call;
+ * runs on the legacy default stream and waits for it.
+ * Errors: INVALID_ARG (NULL rate, unknown kind), CUDA. */
+#define IGS_PEAK_FP32_FMA 0
+#define IGS_PEAK_MUFU_LG2 1
+#define IGS_PEAK_MUFU_RCP 2
+#define IGS_PEAK_FP64_FMA 3
+int igs_measure_peak(igs_ctx ctx, int kind, double* rate, double* ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -129,11 +129,12 @@ def kernel_Kbar(f_s, f_t, f1_t):
     return (dx * f1_t[1][None, :] - dy * f1_t[0][None, :]) / (dx * dx + dy * dy)
 
 
-def build_rhs(curve, n_elems: int, degree: int, n_ref: int, uD_nodes, uD_gauss, terms: bool = False):
+def build_rhs(curve, n_elems: int, degree: int, n_ref: int, uD_nodes, uD_gauss, magnitude: bool = False):
     """beta (n x nrhs).  uD_nodes: (Nq, nrhs) values of u_D at eta;
     uD_gauss: (Ng, nrhs) values at the Gauss points (closed curves only).
-    With terms=True returns (beta, b1/2, b2/(2 pi)) for a closed curve and
-    (beta, b1, 0) for an open arc: the two terms whose difference is beta."""
+    With magnitude=True returns (beta, S): S holds the same sums taken over
+    the absolute values of their terms, the scale of the rounding error of
+    any evaluation of them (|fl(sum x) - sum x| <= N eps sum |x|)."""
     disc = make_discretization(curve, n_elems, degree, n_ref)
     W = rules.regular_rules(disc)
     f, f1, J = geometry_at(curve, disc.eta)
@@ -141,20 +142,24 @@ def build_rhs(curve, n_elems: int, degree: int, n_ref: int, uD_nodes, uD_gauss, 
     uD_nodes = np.asarray(uD_nodes, np.float64).reshape(disc.Nq, -1)
     b1 = P.T @ uD_nodes
     if not disc.closed:
-        return (b1, b1, np.zeros_like(b1)) if terms else b1
+        return (b1, np.abs(P).T @ np.abs(uD_nodes)) if magnitude else b1
     tg, wg = disc.fine_gauss(G_RHS)
     ft, f1t, _ = geometry_at(curve, tg)
     Kb = kernel_Kbar(f, ft, f1t)                         # (Nq, Ng)
     uD_gauss = np.asarray(uD_gauss, np.float64).reshape(len(tg), -1)
     b2 = P.T @ (Kb @ (wg[:, None] * uD_gauss))
     beta = 0.5 * b1 - b2 / (2.0 * np.pi)
-    return (beta, 0.5 * b1, b2 / (2.0 * np.pi)) if terms else beta
+    if not magnitude:
+        return beta
+    S = 0.5 * (np.abs(P).T @ np.abs(uD_nodes)) + \
+        (np.abs(P).T @ (np.abs(Kb) @ (wg[:, None] * np.abs(uD_gauss)))) / (2.0 * np.pi)
+    return beta, S
 
 
-def build_rhs_rows(curve, n_elems: int, degree: int, n_ref: int, rows, uD_nodes, uD_gauss, terms: bool = False):
+def build_rhs_rows(curve, n_elems: int, degree: int, n_ref: int, rows, uD_nodes, uD_gauss, magnitude: bool = False):
     """Entries `rows` of beta (len(rows) x nrhs) by the same sums as build_rhs,
     restricted to the nodes N^(i) where P[n, i] can be non-zero (sampled
-    parity checks at large size).  terms=True as in build_rhs."""
+    parity checks at large size).  magnitude=True as in build_rhs."""
     disc = make_discretization(curve, n_elems, degree, n_ref)
     W = rules.regular_rules(disc)
     rows = np.asarray(rows)
@@ -164,14 +169,18 @@ def build_rhs_rows(curve, n_elems: int, degree: int, n_ref: int, rows, uD_nodes,
     uD_nodes = np.asarray(uD_nodes, np.float64).reshape(disc.Nq, -1)
     b1 = P.T @ uD_nodes[need]
     if not disc.closed:
-        return (b1, b1, np.zeros_like(b1)) if terms else b1
+        return (b1, np.abs(P).T @ np.abs(uD_nodes[need])) if magnitude else b1
     tg, wg = disc.fine_gauss(G_RHS)
     ft, f1t, _ = geometry_at(curve, tg)
     Kb = kernel_Kbar(f, ft, f1t)                         # (len(need), Ng)
     uD_gauss = np.asarray(uD_gauss, np.float64).reshape(len(tg), -1)
     b2 = P.T @ (Kb @ (wg[:, None] * uD_gauss))
     beta = 0.5 * b1 - b2 / (2.0 * np.pi)
-    return (beta, 0.5 * b1, b2 / (2.0 * np.pi)) if terms else beta
+    if not magnitude:
+        return beta
+    S = 0.5 * (np.abs(P).T @ np.abs(uD_nodes[need])) + \
+        (np.abs(P).T @ (np.abs(Kb) @ (wg[:, None] * np.abs(uD_gauss)))) / (2.0 * np.pi)
+    return beta, S
 
 
 # ----------------------------------------------------------------------------

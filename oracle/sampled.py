@@ -201,3 +201,66 @@ class EntrySampler:
         Ws = self.singular(Ni, Nj)
         inner = C0 @ (Jj * wj) + Ws @ (Jj * test_values(disc, j, disc.eta[Nj]))
         return float(-((Ji * wi) @ inner) / (2.0 * np.pi))
+
+
+# ----------------------------------------------------------------------------
+# Whole rows of A at large size
+# ----------------------------------------------------------------------------
+def regular_rules_sparse(disc: Discretization, cols=None):
+    """The regular rules w^(i) of Algorithm 1 for test functions `cols`
+    (default all), as (i, N^(i), w^(i)) triples: `regular_rule` per function."""
+    cols = range(disc.n) if cols is None else cols
+    return [(int(i),) + regular_rule(disc, int(i)) for i in cols]
+
+
+class RowSampler:
+    """Rows A[i, :] one by one at any size, from the same definitions as the
+    dense oracle restricted to what a row touches (eqs. IK1e2, IK1e2_bis):
+
+        A[i, :] = -(1/2 pi) sum_{n in N^(i)} J_n w^(i)_n
+                  ( sum_{n'} K1(eta_n, eta_n') P[n', :] + sum_{n'} W^s[n][n'] Q[n', :] )
+
+    with P[n', j] = J_n' w^(j)_n' (all n regular rules, kept sparse),
+    Q[n', j] = J_n' B_j(eta_n') (d + 1 non-zeros per node, cyclic wrap for
+    closed curves) and the singular rules W^s[n][:] of Algorithm 2 for the
+    nodes n in N^(i).  `rules` may hand in the (i, N^(i), w^(i)) triples of
+    `regular_rules_sparse` (computed elsewhere, e.g. in parallel)."""
+
+    def __init__(self, curve, n_elems: int, degree: int, n_ref: int, rules=None):
+        import scipy.sparse as sp
+        self.curve = curve
+        disc = self.disc = make_discretization(curve, n_elems, degree, n_ref)
+        self.entry_sampler = EntrySampler(curve, n_elems, degree, n_ref)
+        f, _, J = geometry_at(curve, disc.eta)
+        self.f, self.J = f, J
+        if rules is None:
+            rules = regular_rules_sparse(disc)
+        rows, cols, vals = [], [], []
+        self.rule = {}
+        for i, Ni, wi in rules:
+            self.rule[i] = (Ni, wi)
+            rows.append(Ni)
+            cols.append(np.full(len(Ni), i))
+            vals.append(J[Ni] * wi)
+        self.P = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                               shape=(disc.Nq, disc.n))
+        first, v = local_basis(disc.test_knots, disc.d, disc.eta)
+        qr, qc, qv = [], [], []
+        for r in range(disc.d + 1):
+            j = first + r
+            if disc.closed:
+                j = np.where(j >= disc.Nh, j - disc.Nh, j)
+            keep = v[0, :, r] != 0.0
+            qr.append(np.nonzero(keep)[0])
+            qc.append(j[keep])
+            qv.append(J[keep] * v[0, keep, r])
+        self.Q = sp.csr_matrix((np.concatenate(qv), (np.concatenate(qr), np.concatenate(qc))),
+                               shape=(disc.Nq, disc.n))
+
+    def row(self, i: int) -> np.ndarray:
+        disc = self.disc
+        Ni, wi = self.rule[i]
+        C0 = kernel_K1(disc, self.f[:, Ni], self.J[Ni], disc.eta[Ni], self.f, disc.eta)   # (|N^(i)|, Nq)
+        Ws = self.entry_sampler.singular(Ni, np.arange(disc.Nq))                          # (|N^(i)|, Nq)
+        inner = (self.P.T @ C0.T).T + (self.Q.T @ Ws.T).T                                  # (|N^(i)|, n)
+        return -((self.J[Ni] * wi) @ inner) / (2.0 * np.pi)

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libigs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "plan.cpp", "rules.cu", "geometry.cu", "assemble.cu", "rhs.cu", "potential.cu", "collocation.cu", "solve.cu", "batch.cu", "server.cu"]
+SOURCES = ["api.cu", "plan.cpp", "rules.cu", "geometry.cu", "assemble.cu", "rhs.cu", "potential.cu", "collocation.cu", "solve.cu", "batch.cu", "server.cu", "peaks.cu"]
 
 
 def _nvcc() -> str:

@@ -168,6 +168,14 @@ int igs_selftest_wait(igs_ctx ctx, double budget_s, int* gave_up) {
     API_END
 }
 
+int igs_measure_peak(igs_ctx ctx, int kind, double* rate, double* ms) {
+    API_BEGIN
+    REQUIRE(ctx && rate, IGS_E_INVALID_ARG, "ctx or rate is NULL");
+    REQUIRE(kind >= IGS_PEAK_FP32_FMA && kind <= IGS_PEAK_FP64_FMA, IGS_E_INVALID_ARG, "unknown peak kind");
+    *rate = measure_peak(ctx->device, kind, ms);
+    API_END
+}
+
 int igs_create_geometry(igs_ctx ctx, igs_geom* out, int degree, const double* knots, int n_knots,
                         const double* ctrl_xy, const double* weights, int n_ctrl, int closed) {
     API_BEGIN

@@ -196,6 +196,7 @@ void collocation_solve(igs_prob p, const double* d_uD, int nrhs, double* d_alpha
 void potential_eval(igs_prob p, const double* d_alpha, const double* d_uD, int nrhs, const double* d_xy,
                     int64_t count, double* d_u);
 void solve_system(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double* resid);
+double measure_peak(int device, int kind, double* ms);    // rate of one pipe (peaks.cu)
 int wait_selftest(int device, double budget_s);   // 1: the bounded wait gave up
 }  // namespace igs
 

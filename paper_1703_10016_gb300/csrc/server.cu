@@ -3,7 +3,8 @@
 // a context with its own CUDA stream; a worker takes the oldest queued request
 // as soon as its device-memory estimate fits in what the running requests
 // leave of the budget (first come, first served: a large request at the head
-// is not overtaken), runs it through the library's own entry points, stores
+// is not overtaken), runs it through the library's own entry points (the
+// right-hand side beside the factorisation, as igs_solve_data does), stores
 // the result and frees its memory share.  Requests on different slots overlap
 // on the device; each one's arithmetic is the same as when it runs alone.
 // With a cache budget, each slot keeps the problems of its recent requests
@@ -200,8 +201,8 @@ void run_request(igs_server s, int slot, Ticket& t) {
             t.n = info.n;
             t.alpha.assign((size_t)r.nrhs * info.n, 0.0);
             t.resid.assign(r.nrhs, 0.0);
-            rc = igs_build_rhs(p, uD.data(), r.nrhs, nullptr, IGS_MEM_HOST);
-            if (rc == IGS_OK) rc = igs_solve(p, nullptr, r.nrhs, t.alpha.data(), t.resid.data(), IGS_MEM_HOST);
+            // right-hand side on the problem's second stream beside the factorisation
+            rc = igs_solve_data(p, uD.data(), r.nrhs, t.alpha.data(), t.resid.data(), IGS_MEM_HOST);
             igs_timing tm{};
             if (rc == IGS_OK && igs_problem_timing(p, &tm) == IGS_OK) t.ir = tm.ir_iterations;
             if (rc != IGS_OK) fail(rc, igs_last_error());

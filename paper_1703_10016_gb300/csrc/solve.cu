@@ -757,10 +757,12 @@ static void launch_trsv_pk(int n, const float* F, const float* Linv, float* X, i
     }
 }
 
-// r = beta - As alpha (FP64), one warp per row; also |r|^2 and |beta|^2 per rhs.
+// r = beta - As alpha (FP64), one warp per row (lanes over columns, then a
+// fixed shuffle tree).  The norms |r|^2 and |beta|^2 are summed afterwards by
+// k_norms in a fixed order, so the refinement is deterministic.
 template <int NR>
 __global__ void k_resid(int n, const double* __restrict__ As, const double* __restrict__ alpha,
-                        const double* __restrict__ beta, double* __restrict__ r, double* __restrict__ norms) {
+                        const double* __restrict__ beta, double* __restrict__ r) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
     if (warp >= n) return;
     const int i = warp;
@@ -776,12 +778,36 @@ __global__ void k_resid(int n, const double* __restrict__ As, const double* __re
     for (int k = 0; k < NR; ++k) {
         double v = s[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) {
-            const double rv = beta[(size_t)k * n + i] - v;
-            r[(size_t)k * n + i] = rv;
-            atomicAdd(&norms[2 * k], rv * rv);
-            atomicAdd(&norms[2 * k + 1], beta[(size_t)k * n + i] * beta[(size_t)k * n + i]);
+        if (lane == 0) r[(size_t)k * n + i] = beta[(size_t)k * n + i] - v;
+    }
+}
+
+// norms[2k] = |r_k|^2, norms[2k+1] = |beta_k|^2: one block per data set,
+// thread t sums entries t, t + 1024, ... in order, then a fixed tree.
+constexpr int kNormThreads = 1024;
+__global__ void __launch_bounds__(kNormThreads) k_norms(int n, const double* __restrict__ r,
+                                                        const double* __restrict__ beta, double* __restrict__ norms) {
+    __shared__ double s_r[kNormThreads], s_b[kNormThreads];
+    const int k = blockIdx.x, t = threadIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int i = t; i < n; i += kNormThreads) {
+        const double rv = r[(size_t)k * n + i], bv = beta[(size_t)k * n + i];
+        a = fma(rv, rv, a);
+        b = fma(bv, bv, b);
+    }
+    s_r[t] = a;
+    s_b[t] = b;
+    __syncthreads();
+    for (int h = kNormThreads / 2; h > 0; h >>= 1) {
+        if (t < h) {
+            s_r[t] += s_r[t + h];
+            s_b[t] += s_b[t + h];
         }
+        __syncthreads();
+    }
+    if (t == 0) {
+        norms[2 * k] = s_r[0];
+        norms[2 * k + 1] = s_b[0];
     }
 }
 
@@ -789,15 +815,16 @@ static void launch_resid(int n, int nrhs, const double* As, const double* alpha,
                          double* norms, cudaStream_t s) {
     const dim3 g((n * 32 + 255) / 256), b(256);
     switch (nrhs) {
-        case 1: k_resid<1><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
-        case 2: k_resid<2><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
-        case 3: k_resid<3><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
-        case 4: k_resid<4><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
-        case 5: k_resid<5><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
-        case 6: k_resid<6><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
-        case 7: k_resid<7><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
-        default: k_resid<8><<<g, b, 0, s>>>(n, As, alpha, beta, r, norms); break;
+        case 1: k_resid<1><<<g, b, 0, s>>>(n, As, alpha, beta, r); break;
+        case 2: k_resid<2><<<g, b, 0, s>>>(n, As, alpha, beta, r); break;
+        case 3: k_resid<3><<<g, b, 0, s>>>(n, As, alpha, beta, r); break;
+        case 4: k_resid<4><<<g, b, 0, s>>>(n, As, alpha, beta, r); break;
+        case 5: k_resid<5><<<g, b, 0, s>>>(n, As, alpha, beta, r); break;
+        case 6: k_resid<6><<<g, b, 0, s>>>(n, As, alpha, beta, r); break;
+        case 7: k_resid<7><<<g, b, 0, s>>>(n, As, alpha, beta, r); break;
+        default: k_resid<8><<<g, b, 0, s>>>(n, As, alpha, beta, r); break;
     }
+    k_norms<<<nrhs, kNormThreads, 0, s>>>(n, r, beta, norms);
 }
 
 template <typename T>
@@ -1561,9 +1588,8 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
             launch_trsv<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 0, s);
         }
         k_accum<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, d_x, d_alpha, scale, n, it == 0);
-        IGS_CUDA(cudaMemsetAsync(d_norm, 0, sizeof(double) * 2 * nrhs, s));
         launch_resid(n, nrhs, p->d_As64, d_alpha, d_beta, d_r, d_norm, s);
-        p->launches += 5;
+        p->launches += 6;
         IGS_CUDA(cudaGetLastError());
         if (it == 0 && max_it > 1) {
             // an FP32 factor never meets the tolerance after one step: go on to the

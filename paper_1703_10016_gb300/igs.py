@@ -38,11 +38,12 @@ EXPORTED = [
     "igs_get_matrix", "igs_batch_create", "igs_batch_destroy", "igs_batch_assemble", "igs_batch_tune", "igs_batch_set_config",
     "igs_batch_get_config",
     "igs_server_create", "igs_server_submit", "igs_server_wait", "igs_server_result", "igs_server_drain",
-    "igs_server_destroy", "igs_selftest_wait",
+    "igs_server_destroy", "igs_selftest_wait", "igs_measure_peak",
 ]
 IGS_REQ_QUEUED, IGS_REQ_RUNNING, IGS_REQ_DONE, IGS_REQ_FAILED = 0, 1, 2, 3
 IGS_REUSE_NONE, IGS_REUSE_RULES, IGS_REUSE_FACTOR = 0, 1, 2
 IGS_ORDER_NATURAL, IGS_ORDER_INTERLEAVED, IGS_ORDER_LARGEST_FIRST = 0, 1, 2
+IGS_PEAK_FP32_FMA, IGS_PEAK_MUFU_LG2, IGS_PEAK_MUFU_RCP, IGS_PEAK_FP64_FMA = 0, 1, 2, 3
 
 
 class IgsError(RuntimeError):
@@ -130,6 +131,7 @@ def _load() -> C.CDLL:
         "igs_server_drain": [vp, i32],
         "igs_server_destroy": [vp],
         "igs_selftest_wait": [vp, C.c_double, C.POINTER(i32)],
+        "igs_measure_peak": [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -408,6 +410,14 @@ def igs_selftest_wait(ctx, budget_s=0.01):
     out = C.c_int(0)
     _check(_lib.igs_selftest_wait(ctx, float(budget_s), C.byref(out)), "igs_selftest_wait")
     return out.value
+
+
+def igs_measure_peak(ctx, kind: int) -> tuple[float, float]:
+    """(rate, ms) of one arithmetic pipe: flop/s for the FMA kinds,
+    instructions/s for the MUFU kinds."""
+    rate, ms = C.c_double(0.0), C.c_double(0.0)
+    _check(_lib.igs_measure_peak(ctx, int(kind), C.byref(rate), C.byref(ms)), "igs_measure_peak")
+    return rate.value, ms.value
 
 
 # ------------------------------------------------------------------ batched form

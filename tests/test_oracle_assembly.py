@@ -159,3 +159,44 @@ def test_build_rhs_rows_matches_full():
         rows = np.array([0, 3, full.shape[0] - 1])
         part = oa.build_rhs_rows(c, n, d, 2, rows, un, ug)
         np.testing.assert_allclose(part, full[rows], rtol=1e-13, atol=1e-16)
+
+
+def test_error_measures_closed_forms():
+    """E_R and E_M of Sect. 6 on a density with known errors: the cyclic
+    basis is a partition of unity, so alpha = 1 gives q_h = 1 exactly; against
+    q = 1 + c sin(2 pi s) on I = [0, 1]:
+        E_R = sqrt(int (c sin)^2 / int (1 + c sin)^2) = sqrt((c^2/2) / (1 + c^2/2)),
+        E_M = c max_k |sin(2 pi s_k)| over the 500 uniform points s_k of I."""
+    from oracle.discretization import Discretization
+    c = 0.3
+    disc = Discretization(0.0, 1.0, 16, 3, 2, True)
+    ER, EM = oa.errors(disc, np.ones(disc.n), lambda s: 1.0 + c * np.sin(2 * np.pi * s))
+    assert abs(ER - np.sqrt((c * c / 2) / (1 + c * c / 2))) < 1e-12
+    sk = np.linspace(0.0, 1.0, 500)
+    assert abs(EM - c * np.max(np.abs(np.sin(2 * np.pi * sk)))) < 1e-12
+    # and exact zero for the exact density
+    ER0, EM0 = oa.errors(disc, np.ones(disc.n), lambda s: np.ones_like(s))
+    assert ER0 < 1e-14 and EM0 < 1e-14
+
+
+def test_rhs_magnitude_bounds_beta():
+    """The rounding-error scale S of build_rhs (the same sums over absolute
+    values) bounds |beta| entry by entry and equals it for data whose terms
+    all have one sign (open arc, u_D >= 0, where beta = b1 has terms P u_D and
+    S = |P| u_D: equal where the row weights are non-negative)."""
+    c = wl.star_curve()
+    n, d = 48, 3
+    eta, tg, _ = oa.rhs_points(c, n, d, 2)
+    h = wl.Harmonic("log")
+    un = h.value(*bspline.curve_eval(c, eta, 0)[0])[:, None]
+    ug = h.value(*bspline.curve_eval(c, tg, 0)[0])[:, None]
+    beta, S = oa.build_rhs(c, n, d, 2, un, ug, magnitude=True)
+    assert np.all(S >= np.abs(beta) * (1 - 1e-14))
+    assert np.max(S) > 2 * np.max(np.abs(beta))          # the star's terms cancel
+    arc = wl.parabola_arc()
+    eta, tg, _ = oa.rhs_points(arc, 12, 2, 1)
+    b1, S1 = oa.build_rhs(arc, 12, 2, 1, np.ones((len(eta), 1)), np.ones((len(tg), 1)), magnitude=True)
+    W = oa.rules.regular_rules(oa.make_discretization(arc, 12, 2, 1))
+    nonneg = np.all(W >= 0, axis=0)
+    np.testing.assert_allclose(S1[nonneg, 0], b1[nonneg, 0], rtol=1e-14)
+    assert np.all(S1 >= np.abs(b1) * (1 - 1e-14))

@@ -96,3 +96,24 @@ def test_nodes_and_index_sets(closed, d, nh, nref):
     # closed test space: partition of unity of the cyclic basis
     if closed:
         np.testing.assert_allclose(Bt.sum(axis=0), 1.0, atol=1e-13)
+
+
+def test_nodes_written_out_for_one_small_case():
+    """Sect. 4's node vector for d = 2, N_ref = 1, N_h = 4 on [0, 1] written out
+    by hand: d + 2 = 4 uniform points (end points included) in the first and the
+    last refined element, the midpoint of every inner element and the
+    breakpoints between inner elements: N_quad = 2d + 2M - 1 = 11."""
+    want = np.array([0.0, 1 / 12, 2 / 12, 3 / 12,          # first element [0, 1/4]
+                     3 / 8,                                # midpoint of [1/4, 1/2]
+                     1 / 2, 5 / 8,                         # breakpoint 1/2, midpoint of [1/2, 3/4]
+                     9 / 12, 10 / 12, 11 / 12, 1.0])       # last element [3/4, 1]
+    for closed in (True, False):
+        disc = Discretization(0.0, 1.0, 4, 2, 1, closed)
+        np.testing.assert_allclose(disc.eta, want, rtol=0, atol=1e-15)
+    # d = 3, N_ref = 2, N_h = 4 on [-1, 3] (h_f = 1/2, M = 8): 5 points per end element
+    disc = Discretization(-1.0, 3.0, 4, 3, 2, True)
+    want = np.array([-1.0, -0.875, -0.75, -0.625, -0.5,                  # [-1, -1/2]
+                     -0.25, 0.0, 0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 1.75, 2.0, 2.25,   # midpoints, inner breakpoints
+                     2.5, 2.625, 2.75, 2.875, 3.0])                       # [5/2, 3]
+    assert disc.Nq == 21
+    np.testing.assert_allclose(disc.eta, want, rtol=0, atol=1e-15)

@@ -43,3 +43,16 @@ def test_entries_match_dense_oracle(name, n, d, nref):
     pairs = [(0, 0), (0, m - 1), (m - 1, 0), (1, 2), (m // 2, m // 2 + 1), (3, m - 2), (m - 1, m - 1), (2, m // 2)]
     for i, j in pairs:
         assert abs(S.entry(i, j) - A[i, j]) <= 1e-14 * np.max(np.abs(A)), (i, j)
+
+
+@pytest.mark.parametrize("name,n,d,nref", [("star", 24, 3, 2), ("circle", 16, 4, 2), ("arc", 14, 3, 2),
+                                           ("star", 12, 5, 1)])
+def test_rows_match_dense_oracle(name, n, d, nref):
+    """Whole rows from the sparse row sampler (used for the CPU baseline at
+    n = 16384) equal the dense oracle's rows."""
+    from oracle.sampled import RowSampler
+    c = {"star": wl.star_curve(), "circle": wl.nurbs_circle(0.5), "arc": wl.parabola_arc()}[name]
+    A = oa.assemble(c, n, d, nref)["A"]
+    R = RowSampler(c, n, d, nref)
+    for i in (0, 1, A.shape[0] // 2, A.shape[0] - 1):
+        np.testing.assert_allclose(R.row(i), A[i], rtol=0, atol=1e-14 * np.max(np.abs(A)))
