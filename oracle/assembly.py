@@ -132,9 +132,15 @@ def kernel_Kbar(f_s, f_t, f1_t):
 def build_rhs(curve, n_elems: int, degree: int, n_ref: int, uD_nodes, uD_gauss, magnitude: bool = False):
     """beta (n x nrhs).  uD_nodes: (Nq, nrhs) values of u_D at eta;
     uD_gauss: (Ng, nrhs) values at the Gauss points (closed curves only).
-    With magnitude=True returns (beta, S): S holds the same sums taken over
+    With magnitude=True returns (beta, S, K): S holds the same sums taken over
     the absolute values of their terms, the scale of the rounding error of
-    any evaluation of them (|fl(sum x) - sum x| <= N eps sum |x|)."""
+    any evaluation of them (|fl(sum x) - sum x| <= N eps sum |x|); K bounds
+    the first-order change of beta when every coordinate of f at the nodes and
+    f, f' at the Gauss points changes by one unit in the last place (relative
+    2^-53): since |d Kbar / d(f(t) - f(s))| <= 3 |f'(t)| / r^2 with
+    r = |f(t) - f(s)|,
+        K_i = (1/2pi) sum_n |P[n,i]| sum_g w_g |u_D(t_g)| 3 |f'(t_g)| (|f(s_n)| + |f(t_g)|) / r^2
+    times 2^-53 (zero for an open arc)."""
     disc = make_discretization(curve, n_elems, degree, n_ref)
     W = rules.regular_rules(disc)
     f, f1, J = geometry_at(curve, disc.eta)
@@ -142,7 +148,7 @@ def build_rhs(curve, n_elems: int, degree: int, n_ref: int, uD_nodes, uD_gauss, 
     uD_nodes = np.asarray(uD_nodes, np.float64).reshape(disc.Nq, -1)
     b1 = P.T @ uD_nodes
     if not disc.closed:
-        return (b1, np.abs(P).T @ np.abs(uD_nodes)) if magnitude else b1
+        return (b1, np.abs(P).T @ np.abs(uD_nodes), np.zeros_like(b1)) if magnitude else b1
     tg, wg = disc.fine_gauss(G_RHS)
     ft, f1t, _ = geometry_at(curve, tg)
     Kb = kernel_Kbar(f, ft, f1t)                         # (Nq, Ng)
@@ -151,9 +157,7 @@ def build_rhs(curve, n_elems: int, degree: int, n_ref: int, uD_nodes, uD_gauss, 
     beta = 0.5 * b1 - b2 / (2.0 * np.pi)
     if not magnitude:
         return beta
-    S = 0.5 * (np.abs(P).T @ np.abs(uD_nodes)) + \
-        (np.abs(P).T @ (np.abs(Kb) @ (wg[:, None] * np.abs(uD_gauss)))) / (2.0 * np.pi)
-    return beta, S
+    return (beta,) + _rhs_scales(P, uD_nodes, f, ft, f1t, Kb, wg, uD_gauss)
 
 
 def build_rhs_rows(curve, n_elems: int, degree: int, n_ref: int, rows, uD_nodes, uD_gauss, magnitude: bool = False):
@@ -169,7 +173,7 @@ def build_rhs_rows(curve, n_elems: int, degree: int, n_ref: int, rows, uD_nodes,
     uD_nodes = np.asarray(uD_nodes, np.float64).reshape(disc.Nq, -1)
     b1 = P.T @ uD_nodes[need]
     if not disc.closed:
-        return (b1, np.abs(P).T @ np.abs(uD_nodes[need])) if magnitude else b1
+        return (b1, np.abs(P).T @ np.abs(uD_nodes[need]), np.zeros_like(b1)) if magnitude else b1
     tg, wg = disc.fine_gauss(G_RHS)
     ft, f1t, _ = geometry_at(curve, tg)
     Kb = kernel_Kbar(f, ft, f1t)                         # (len(need), Ng)
@@ -178,9 +182,20 @@ def build_rhs_rows(curve, n_elems: int, degree: int, n_ref: int, rows, uD_nodes,
     beta = 0.5 * b1 - b2 / (2.0 * np.pi)
     if not magnitude:
         return beta
-    S = 0.5 * (np.abs(P).T @ np.abs(uD_nodes[need])) + \
-        (np.abs(P).T @ (np.abs(Kb) @ (wg[:, None] * np.abs(uD_gauss)))) / (2.0 * np.pi)
-    return beta, S
+    return (beta,) + _rhs_scales(P, uD_nodes[need], f, ft, f1t, Kb, wg, uD_gauss)
+
+
+def _rhs_scales(P, uN, f, ft, f1t, Kb, wg, ug):
+    """(S, K) of build_rhs(magnitude=True) for a closed curve."""
+    aP = np.abs(P).T
+    wu = wg[:, None] * np.abs(ug)
+    S = 0.5 * (aP @ np.abs(uN)) + (aP @ (np.abs(Kb) @ wu)) / (2.0 * np.pi)
+    dx = ft[0][None, :] - f[0][:, None]
+    dy = ft[1][None, :] - f[1][:, None]
+    sens = 3.0 * np.hypot(f1t[0], f1t[1])[None, :] * \
+        (np.hypot(f[0], f[1])[:, None] + np.hypot(ft[0], ft[1])[None, :]) / (dx * dx + dy * dy)
+    K = 2.0 ** -53 * (aP @ (sens @ wu)) / (2.0 * np.pi)
+    return S, K
 
 
 # ----------------------------------------------------------------------------

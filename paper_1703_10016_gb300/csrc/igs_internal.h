@@ -138,7 +138,8 @@ struct igs_prob_s {
     int tepoch = 0;               // flag value of the current triangular solve
     cudaStream_t aux_stream = nullptr;   // right-hand side beside the factorisation (igs_solve_data)
     bool coop_ok = false;         // cooperative launch available
-    double* d_As64 = nullptr;     // (A+A^T)/2 in FP64 for residuals (MIXED)
+    double* d_As64 = nullptr;     // (A+A^T)/2 in FP64 for the refinement residuals
+    double* d_dscale = nullptr;   // [n] As_ii^-1/2: the MIXED factor is that of D As D
     int rhs_n = 0;
     double* d_beta = nullptr;     // [nrhs][n]
     double* d_rhs_geo = nullptr;  // [5][Ng] geometry at the rhs Gauss points

@@ -5,7 +5,8 @@
 //   FP32 FMA      a = a * b + c                  (2 flop per instruction)
 //   MUFU lg2      a = lg2.approx(a) + 1          (a stays in [1, 2); the add
 //                 goes to the FMA pipe, which has 8x the lanes of the MUFU)
-//   MUFU rcp      a = rcp.approx(a)              (a alternates between x and 1/x)
+//   MUFU rcp      a = rcp.approx(a) + 1/2        (a tends to the fixed point 1.28;
+//                 the add keeps successive reciprocals from cancelling)
 //   FP64 FMA      a = a * b + c                  (2 flop per instruction)
 // The grid fills every SM (resident blocks per SM from the occupancy query);
 // the result is counted instructions (flop for the FMA kinds) per second of
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(256) k_peak(int iters, float seed, float* __re
                 } else if (KIND == IGS_PEAK_MUFU_RCP) {
                     float r;
                     asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a[c]));
-                    a[c] = r;
+                    a[c] = r + 0.5f;
                 } else {
                     ad[c] = fma(ad[c], bd, cd);
                 }

@@ -55,14 +55,17 @@ __device__ __forceinline__ float kb32_pair(float gxh, float gxl, float gyh, floa
 // MIXED far field: partial sums over Gauss slice blockIdx.y, FP32, every pair
 // (the near pairs are replaced by k_double_layer_near).  Gauss data in shared
 // memory as 16-byte coordinate records and 8-byte (a, b) records.  A block
-// holds kFarNodes nodes and kFarParts threads per node: part p of a node sums
-// the chunk's Gauss points q = p (mod kFarParts) (one warp = 32 nodes of one
-// part, so every shared-memory read is a broadcast), and the parts are added
-// in a fixed order at the end.
-constexpr int kFarNodes = 64, kFarParts = 4;
+// holds kFarNodes nodes: thread (j, p), j < kFarLanes, p < kFarParts, keeps
+// the float-float coordinates of the kFarNN nodes j + kFarLanes k in
+// registers and sums the chunk's Gauss points q = p (mod kFarParts) for all of
+// them, so one shared-memory read of a Gauss point serves kFarNN pairs (one
+// warp = 32 node groups of one part: every read is a broadcast).  The parts
+// are added in a fixed order at the end.
+constexpr int kFarLanes = 32, kFarParts = 8, kFarNN = 4;
+constexpr int kFarNodes = kFarLanes * kFarNN;
 
 template <int NR>
-__global__ void __launch_bounds__(kFarNodes * kFarParts) k_double_layer_f(int Nq, int Ng, const double* __restrict__ geo,
+__global__ void __launch_bounds__(kFarLanes * kFarParts) k_double_layer_f(int Nq, int Ng, const double* __restrict__ geo,
                                                                           const double* __restrict__ rgeo,
                                                                           const double* __restrict__ rw,
                                                                           const double* __restrict__ uD, int ldu, int off,
@@ -71,17 +74,20 @@ __global__ void __launch_bounds__(kFarNodes * kFarParts) k_double_layer_f(int Nq
     __shared__ float2 sab[kRhsChunk];
     __shared__ float su[NR][kRhsChunk];
     __shared__ float red[kFarParts][NR][kFarNodes];
-    const int node = threadIdx.x % kFarNodes, prt = threadIdx.x / kFarNodes;
-    const int m = blockIdx.x * kFarNodes + node;
-    const bool live = m < Nq;
-    float xh = 0, xl = 0, yh = 0, yl = 0;
-    if (live) {
-        split2(geo[m], xh, xl);
-        split2(geo[Nq + m], yh, yl);
-    }
-    float acc[NR];
+    const int lane = threadIdx.x % kFarLanes, prt = threadIdx.x / kFarLanes;
+    const int m0 = blockIdx.x * kFarNodes + lane;
+    float xh[kFarNN], xl[kFarNN], yh[kFarNN], yl[kFarNN];
 #pragma unroll
-    for (int k = 0; k < NR; ++k) acc[k] = 0.f;
+    for (int k = 0; k < kFarNN; ++k) {
+        const int m = min(m0 + kFarLanes * k, Nq - 1);
+        split2(geo[m], xh[k], xl[k]);
+        split2(geo[Nq + m], yh[k], yl[k]);
+    }
+    float acc[kFarNN][NR];
+#pragma unroll
+    for (int k = 0; k < kFarNN; ++k)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[k][r] = 0.f;
     const int per = (Ng + kSplit - 1) / kSplit;
     const int g_lo = blockIdx.y * per, g_hi = min(Ng, g_lo + per);
     for (int g0 = g_lo; g0 < g_hi; g0 += kRhsChunk) {
@@ -96,31 +102,37 @@ __global__ void __launch_bounds__(kFarNodes * kFarParts) k_double_layer_f(int Nq
             sab[q] = make_float2((float)rgeo[3 * Ng + g], (float)(-rgeo[2 * Ng + g]));   // f2'(t), -f1'(t)
             const double w = rw[g];
 #pragma unroll
-            for (int k = 0; k < NR; ++k) su[k][q] = (float)(w * uD[(size_t)k * ldu + off + g]);
+            for (int r = 0; r < NR; ++r) su[r][q] = (float)(w * uD[(size_t)r * ldu + off + g]);
         }
         __syncthreads();
-        if (live) {
-#pragma unroll 4
-            for (int q = prt; q < cn; q += kFarParts) {
-                const float4 c = sg[q];
-                const float2 ab = sab[q];
-                const float kb = kb32_pair(c.x, c.y, c.z, c.w, ab.x, ab.y, xh, xl, yh, yl);
+#pragma unroll 2
+        for (int q = prt; q < cn; q += kFarParts) {
+            const float4 c = sg[q];
+            const float2 ab = sab[q];
+            float u[NR];
 #pragma unroll
-                for (int k = 0; k < NR; ++k) acc[k] = fmaf(kb, su[k][q], acc[k]);
+            for (int r = 0; r < NR; ++r) u[r] = su[r][q];
+#pragma unroll
+            for (int k = 0; k < kFarNN; ++k) {
+                const float kb = kb32_pair(c.x, c.y, c.z, c.w, ab.x, ab.y, xh[k], xl[k], yh[k], yl[k]);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[k][r] = fmaf(kb, u[r], acc[k][r]);
             }
         }
     }
 #pragma unroll
-    for (int k = 0; k < NR; ++k) red[prt][k][node] = acc[k];
+    for (int k = 0; k < kFarNN; ++k)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) red[prt][r][lane + kFarLanes * k] = acc[k][r];
     __syncthreads();
-    if (live && prt == 0) {
+    for (int idx = threadIdx.x; idx < NR * kFarNodes; idx += blockDim.x) {
+        const int r = idx / kFarNodes, j = idx % kFarNodes;
+        const int m = blockIdx.x * kFarNodes + j;
+        if (m >= Nq) continue;
+        float v = red[0][r][j];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            float v = red[0][k][node];
-#pragma unroll
-            for (int q = 1; q < kFarParts; ++q) v += red[q][k][node];
-            part[((size_t)blockIdx.y * NR + k) * Nq + m] = (double)v;
-        }
+        for (int q = 1; q < kFarParts; ++q) v += red[q][r][j];
+        part[((size_t)blockIdx.y * NR + r) * Nq + m] = (double)v;
     }
 }
 
@@ -307,7 +319,7 @@ template <int NR>
 static void launch_far(igs_prob p, const double* d_uD, int ldu, double* part, cudaStream_t s) {
     const Plan& P = p->plan;
     if (p->precision == IGS_MIXED)
-        k_double_layer_f<NR><<<dim3((P.Nq + kFarNodes - 1) / kFarNodes, kSplit), kFarNodes * kFarParts, 0, s>>>(
+        k_double_layer_f<NR><<<dim3((P.Nq + kFarNodes - 1) / kFarNodes, kSplit), kFarLanes * kFarParts, 0, s>>>(
             P.Nq, p->Ng, p->d_geo, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, part);
     else
         k_double_layer_d<NR><<<dim3((P.Nq + 255) / 256, kSplit), 256, 0, s>>>(P.Nq, p->Ng, p->d_geo, p->d_rhs_geo,

@@ -11,10 +11,13 @@
 //            second captured stream beside the next panel (look-ahead); in the
 //            MIXED tier that rest runs on the tensor cores (k_syrk_tc).
 // FP64 tier: all in FP64, then one substitution pair.  MIXED tier: the same in
-// FP32, then iterative refinement with FP64 residuals r = beta - A_s alpha until
-// ||r|| <= 1e-10 ||beta||.  The triangular solves go by 64-row blocks in solve
+// FP32 on D A_s D with D = diag(A_s)^-1/2 (unit diagonal, every factor entry at
+// most 1 in magnitude), then iterative refinement with FP64 residuals
+// r = beta - A_s alpha until ||r|| <= 1e-10 ||beta||.  The triangular solves go by 64-row blocks in solve
 // order: the inverted diagonal block (computed once per factorisation, in
 // parallel), then a rank-64 update of the rows not yet solved.
+#include <cuda_fp16.h>
+
 #include <cmath>
 
 #include "igs_internal.h"
@@ -23,13 +26,58 @@ namespace igs {
 
 constexpr int kNB = 64;      // Cholesky panel width / triangular-solve block
 
+// Tiles of 64 x 64 over the lower triangle of tile pairs (bi >= bj), CTAs
+// numbered over that triangle.
+constexpr int kTT = 64;
+__device__ __forceinline__ void tri_decode(int t, int& ti, int& tj);
+
+// dscale[i] = 1 / sqrt(A_ii): the unit-diagonal scaling D of the MIXED tier's
+// factorisation (a non-positive diagonal keeps 1 and the factorisation flags it).
 template <typename T>
-__global__ void k_symmetrize(int n, const T* __restrict__ A, T* __restrict__ F, double* __restrict__ As64) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
-    if (j >= n) return;
-    const double v = 0.5 * ((double)A[(size_t)i * n + j] + (double)A[(size_t)j * n + i]);
-    F[(size_t)i * n + j] = (T)v;
-    if (As64) As64[(size_t)i * n + j] = v;
+__global__ void k_diag_scale(int n, const T* __restrict__ A, double* __restrict__ dscale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = (double)A[(size_t)i * n + i];
+    dscale[i] = a > 0.0 ? 1.0 / sqrt(a) : 1.0;
+}
+
+// As = (A + A^T)/2 by tile pairs (TS x TS: 64 for FP32, 32 for FP64 to stay
+// within static shared memory), both tiles read and both written row by row
+// through shared memory (coalesced in both orientations).  F gets the lower
+// triangle of D As D (D = diag(dscale), identity if dscale is NULL) in the
+// tier type; As64, if given, the whole As in FP64 (exact for an FP32 A).
+template <typename T> __host__ __device__ constexpr int sym_tile() { return sizeof(T) == 8 ? 32 : 64; }
+template <typename T>
+__global__ void __launch_bounds__(256) k_symmetrize(int n, const T* __restrict__ A, T* __restrict__ F,
+                                                    double* __restrict__ As64, const double* __restrict__ dscale) {
+    constexpr int TS = sym_tile<T>(), RS = 256 / TS;          // RS rows per pass
+    __shared__ T t1[TS][TS + 1];             // A tile (bi, bj)
+    __shared__ T t2[TS][TS + 1];             // A tile (bj, bi)
+    int bi, bj;
+    tri_decode(blockIdx.x, bi, bj);
+    const int i0 = bi * TS, j0 = bj * TS;
+    const int c = threadIdx.x % TS, r0 = threadIdx.x / TS;
+    for (int r = r0; r < TS; r += RS) {
+        const int i = i0 + r, j = j0 + c;
+        t1[r][c] = (i < n && j < n) ? A[(size_t)i * n + j] : (T)0;
+        const int i2 = j0 + r, j2 = i0 + c;
+        t2[r][c] = (i2 < n && j2 < n) ? A[(size_t)i2 * n + j2] : (T)0;
+    }
+    __syncthreads();
+    // s(r, c) = (A[i0+r][j0+c] + A[j0+c][i0+r]) / 2 = (t1[r][c] + t2[c][r]) / 2
+    for (int r = r0; r < TS; r += RS) {
+        const int i = i0 + r, j = j0 + c;
+        if (i >= n || j >= n) continue;
+        const double v = 0.5 * ((double)t1[r][c] + (double)t2[c][r]);
+        if (j <= i) F[(size_t)i * n + j] = dscale ? (T)(v * dscale[i] * dscale[j]) : (T)v;
+        if (As64) As64[(size_t)i * n + j] = v;
+    }
+    if (As64 && bi != bj) {
+        for (int r = r0; r < TS; r += RS) {                 // tile (bj, bi): s(c, r) transposed
+            const int i = j0 + r, j = i0 + c;
+            if (i < n && j < n) As64[(size_t)i * n + j] = 0.5 * ((double)t1[c][r] + (double)t2[r][c]);
+        }
+    }
 }
 
 template <typename T> struct Vec16;
@@ -311,16 +359,30 @@ __global__ void __launch_bounds__(256) k_syrk(int n, T* __restrict__ F, int k0, 
     }
 }
 
-// Diagonal blocks back into F, and U = L^T into the upper triangle.
+// Diagonal blocks back into F, and U = L^T into the upper triangle: one
+// 64 x 64 tile pair per CTA (tiles align with the 64-wide diagonal blocks),
+// the lower tile read row by row and written transposed through shared memory.
 template <typename T>
-__global__ void k_finalize(int n, T* __restrict__ F, const T* __restrict__ diagL) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
-    if (j > i) return;
-    T v;
-    if (i / kNB == j / kNB) v = diagL[(size_t)i * kNB + (j % kNB)];
-    else v = F[(size_t)i * n + j];
-    F[(size_t)i * n + j] = v;
-    if (j < i) F[(size_t)j * n + i] = v;
+__global__ void __launch_bounds__(256) k_finalize(int n, T* __restrict__ F, const T* __restrict__ diagL) {
+    __shared__ T t[kTT][kTT + 1];
+    int bi, bj;
+    tri_decode(blockIdx.x, bi, bj);
+    const int i0 = bi * kTT, j0 = bj * kTT;
+    const int c = threadIdx.x % kTT, r4 = threadIdx.x / kTT;
+    for (int r = r4; r < kTT; r += 4) {
+        const int i = i0 + r, j = j0 + c;
+        T v = (T)0;
+        if (i < n && j < n && j <= i) {
+            v = (bi == bj) ? diagL[(size_t)i * kNB + c] : F[(size_t)i * n + j];
+            if (bi == bj) F[(size_t)i * n + j] = v;
+        }
+        t[r][c] = v;
+    }
+    __syncthreads();
+    for (int r = r4; r < kTT; r += 4) {                      // F[j0 + r][i0 + c] = L[i0 + c][j0 + r]
+        const int i = j0 + r, j = i0 + c;
+        if (i < n && j < n && j > i) F[(size_t)i * n + j] = t[c][r];
+    }
 }
 
 // Inverses of the 64 x 64 diagonal blocks of L (one CTA per block, after the
@@ -827,24 +889,30 @@ static void launch_resid(int n, int nrhs, const double* As, const double* alpha,
     k_norms<<<nrhs, kNormThreads, 0, s>>>(n, r, beta, norms);
 }
 
+// Right-hand side of one refinement step in the factor's type: the residual
+// divided by its norm (sqrt of scale[2k], if given) and, for a factor of
+// D As D, multiplied by D (dscale, if given).
 template <typename T>
 __global__ void k_cast_in(int cnt, const double* __restrict__ src, T* __restrict__ dst, const double* __restrict__ scale,
-                          int n) {
+                          int n, const double* __restrict__ dscale) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= cnt) return;
     const double sc = scale ? scale[2 * (q / n)] : 0.0;
     const double inv = (sc > 0) ? 1.0 / sqrt(sc) : 1.0;
-    dst[q] = (T)(src[q] * inv);
+    const double dv = dscale ? dscale[q % n] : 1.0;
+    dst[q] = (T)(src[q] * inv * dv);
 }
 
+// x += D dx times the residual norm (the correction of one refinement step).
 template <typename T>
 __global__ void k_accum(int cnt, const T* __restrict__ dx, double* __restrict__ x, const double* __restrict__ scale,
-                        int n, int first) {
+                        int n, int first, const double* __restrict__ dscale) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= cnt) return;
     const double sc = scale ? scale[2 * (q / n)] : 0.0;
     const double f = (sc > 0) ? sqrt(sc) : 1.0;
-    const double v = (double)dx[q] * f;
+    const double dv = dscale ? dscale[q % n] : 1.0;
+    const double v = (double)dx[q] * f * dv;
     x[q] = first ? v : x[q] + v;
 }
 
@@ -1016,33 +1084,35 @@ __global__ void __launch_bounds__(256) k_syrk_tc(int n, float* __restrict__ F, i
 }
 
 // Outer-block operands for the tensor-core update, split once per outer block:
-// rows base .. base + 64 G2 - 1 of columns K0 .. K0 + kbo - 1 of F, as TF32
-// high and low parts, in the shared-memory image the MMA descriptors read
-// (K-major core matrices: element (r, l) of a 64-row group and a chunk of
-// kKC = 32 columns at float offset (((r/8)*8 + l/4)*8 + r%8)*4 + l%4).
-// img[(kc*2 + part)*G2 + g] is the 8 KB image of row group g, K chunk kc,
-// part 0 = high, 1 = low; rows >= n and columns >= K0 + kbo are zero.
-// Grid (G2, chunks).
-constexpr int kKC = 32;
-constexpr int kImgFloats = 64 * kKC;
+// rows base .. base + 64 G2 - 1 of columns K0 .. K0 + kbo - 1 of F (the factor
+// of D As D, every entry at most 1 in magnitude), as FP16 high and low parts
+// x = hi + lo + O(2^-22 |x| + 2^-25), in the shared-memory image the MMA
+// descriptors read: K-major core matrices of 8 rows x 16 bytes, element (r, l)
+// of a 64-row group and a chunk of kKC = 64 columns at half offset
+// (((r/8)*8 + l/8)*8 + r%8)*8 + l%8.  img[(kc*2 + part)*G2 + g] is the 8 KB
+// image of row group g, K chunk kc, part 0 = high, 1 = low; rows >= n and
+// columns >= K0 + kbo are zero.  Grid (G2, chunks).
+constexpr int kKC = 64;                     // factor columns per K chunk (128 bytes of FP16 per row)
+constexpr int kImgHalves = 64 * kKC;        // one 64-row group of one chunk and part (8 KB)
 __global__ void __launch_bounds__(256) k_split_panel(int n, const float* __restrict__ F, int K0, int kbo, int base,
-                                                     int G2, float* __restrict__ img) {
+                                                     int G2, __half* __restrict__ img) {
     const int g = blockIdx.x, kc = blockIdx.y;
-    float* hi = img + ((size_t)(kc * 2 + 0) * G2 + g) * kImgFloats;
-    float* lo = img + ((size_t)(kc * 2 + 1) * G2 + g) * kImgFloats;
-    for (int idx = threadIdx.x; idx < kImgFloats / 4; idx += blockDim.x) {
-        const int r8 = idx % 8, c = (idx / 8) % (kKC / 4), rg = idx / (8 * (kKC / 4));
-        const int row = base + g * 64 + rg * 8 + r8, col = K0 + kc * kKC + 4 * c;
-        float v[4];
+    __half* hi = img + ((size_t)(kc * 2 + 0) * G2 + g) * kImgHalves;
+    __half* lo = img + ((size_t)(kc * 2 + 1) * G2 + g) * kImgHalves;
+    for (int idx = threadIdx.x; idx < kImgHalves / 8; idx += blockDim.x) {
+        const int r8 = idx % 8, c = (idx / 8) % (kKC / 8), rg = idx / (8 * (kKC / 8));
+        const int row = base + g * 64 + rg * 8 + r8, col = K0 + kc * kKC + 8 * c;
+        float v[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = (row < n && col + q < K0 + kbo) ? F[(size_t)row * n + col + q] : 0.0f;
-        float4 h, l;
-        h.x = tc::tf32_hi(v[0]); l.x = v[0] - h.x;
-        h.y = tc::tf32_hi(v[1]); l.y = v[1] - h.y;
-        h.z = tc::tf32_hi(v[2]); l.z = v[2] - h.z;
-        h.w = tc::tf32_hi(v[3]); l.w = v[3] - h.w;
-        reinterpret_cast<float4*>(hi)[idx] = h;                 // idx = ((rg*8 + c)*8 + r8)
-        reinterpret_cast<float4*>(lo)[idx] = l;
+        for (int q = 0; q < 8; ++q) v[q] = (row < n && col + q < K0 + kbo) ? F[(size_t)row * n + col + q] : 0.0f;
+        __align__(16) __half h[8], l[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            h[q] = __float2half_rn(v[q]);
+            l[q] = __float2half_rn(v[q] - __half2float(h[q]));
+        }
+        reinterpret_cast<uint4*>(hi)[idx] = *reinterpret_cast<const uint4*>(h);   // idx = ((rg*8 + c)*8 + r8)
+        reinterpret_cast<uint4*>(lo)[idx] = *reinterpret_cast<const uint4*>(l);
     }
 }
 
@@ -1051,22 +1121,25 @@ __global__ void __launch_bounds__(256) k_split_panel(int n, const float* __restr
 // n >= 4096): one CTA per SM walks its share of the 128 x 128 lower-triangle
 // tiles (column tiles tj_off .. ntc-1; in column tile tj the row tiles
 // tj .. ntr-1) in column order.  Warp 0 issues the bulk copies of the split
-// operand images into kTcpStages 64 KB stages, warp 1 issues the 3xTF32 MMAs
-// (N = 128) into one of two TMEM accumulators, warps 4-7 read the other
+// operand images into kTcpStages 64 KB stages, warp 1 issues the MMAs of the
+// three-term FP16 split (hi.hi + hi.lo + lo.hi, FP32 accumulation; kind::f16
+// runs at twice the TF32 rate on half the operand bytes; N = 128) into one of
+// two TMEM accumulators, warps 4-7 read the other
 // accumulator back (one tile row per lane, two halves of 64 columns) and
 // apply C -= D, so a tile's epilogue runs under the next tile's copies and
 // MMAs.  Every wait is bounded: on a timeout (or after another role's
 // timeout) the kernel sets *flag |= 2 and skips the rest.
 constexpr int kTcpStages = 3;
 constexpr uint32_t kTN = 128;                                  // tile columns (MMA N)
-constexpr uint32_t kTcpStageFloats = 2 * tc::kM * kKC + 2 * kTN * kKC;
-constexpr size_t tcp_smem_bytes() { return (size_t)kTcpStages * kTcpStageFloats * 4 + 128; }
-// D F32, A and B TF32, both K-major, N = kTN, M = 128
+constexpr uint32_t kTcpPartBytes = tc::kM * kKC * 2;           // 128 rows x one chunk of FP16 (16 KB)
+constexpr uint32_t kTcpStageBytes = 4 * kTcpPartBytes;         // A hi, A lo, B hi, B lo (kTN == kM)
+constexpr size_t tcp_smem_bytes() { return (size_t)kTcpStages * kTcpStageBytes + 128; }
+// D F32, A and B F16, both K-major, N = kTN, M = 128
 __host__ __device__ constexpr uint32_t tcp_idesc() {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((kTN >> 3) << 17) | ((tc::kM >> 4) << 24);
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((kTN >> 3) << 17) | ((tc::kM >> 4) << 24);
 }
 __device__ __forceinline__ void tcp_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
-    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
                  :: "r"(d), "l"(a), "l"(b), "r"(tcp_idesc()), "r"(accumulate));
 }
 
@@ -1097,13 +1170,13 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity
     return false;
 }
 
-__global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ F, const float* __restrict__ img,
+__global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ F, const __half* __restrict__ img,
                                                      int K0, int kbo, int G2, int tj_off, int ntc, int ntr, int ntiles,
                                                      int* __restrict__ flag) {
     using namespace tc;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    float* stages = (float*)smem_raw;
-    uint64_t* bars = (uint64_t*)(stages + (size_t)kTcpStages * kTcpStageFloats);
+    unsigned char* stages = smem_raw;
+    uint64_t* bars = (uint64_t*)(stages + (size_t)kTcpStages * kTcpStageBytes);
     uint64_t* full = bars;                         // [kTcpStages]
     uint64_t* empty = bars + kTcpStages;           // [kTcpStages]
     uint64_t* accf = bars + 2 * kTcpStages;        // [2]
@@ -1149,24 +1222,23 @@ __global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ 
                 const int s = (int)(g % kTcpStages);
                 const long use = g / kTcpStages;
                 if (use >= 1 && !mbar_wait_or_abort(su32(empty + s), (uint32_t)((use - 1) & 1), s_abort)) { abort(); break; }
-                float* sA = stages + (size_t)s * kTcpStageFloats;
+                unsigned char* sA = stages + (size_t)s * kTcpStageBytes;
                 const uint32_t fb = su32(full + s);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"(kTcpStageFloats * 4) : "memory");
-                const float* srcs[4] = {img + ((size_t)(kc * 2 + 0) * G2 + 2 * it.ti) * kImgFloats,
-                                        img + ((size_t)(kc * 2 + 1) * G2 + 2 * it.ti) * kImgFloats,
-                                        img + ((size_t)(kc * 2 + 0) * G2 + 2 * it.tj) * kImgFloats,
-                                        img + ((size_t)(kc * 2 + 1) * G2 + 2 * it.tj) * kImgFloats};
-                float* dsts[4] = {sA, sA + kM * kKC, sA + 2 * kM * kKC, sA + 2 * kM * kKC + kTN * kKC};
-                const uint32_t sizes[4] = {kM * kKC * 4, kM * kKC * 4, kTN * kKC * 4, kTN * kKC * 4};
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"(kTcpStageBytes) : "memory");
+                // two consecutive 64-row groups (8 KB each) per operand part: 16 KB contiguous
+                const __half* srcs[4] = {img + ((size_t)(kc * 2 + 0) * G2 + 2 * it.ti) * kImgHalves,
+                                         img + ((size_t)(kc * 2 + 1) * G2 + 2 * it.ti) * kImgHalves,
+                                         img + ((size_t)(kc * 2 + 0) * G2 + 2 * it.tj) * kImgHalves,
+                                         img + ((size_t)(kc * 2 + 1) * G2 + 2 * it.tj) * kImgHalves};
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                                 :: "r"(su32(dsts[q])), "l"(srcs[q]), "r"(sizes[q]), "r"(fb) : "memory");
+                                 :: "r"(su32(sA + q * kTcpPartBytes)), "l"(srcs[q]), "r"(kTcpPartBytes), "r"(fb) : "memory");
             }
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: accumulator lt & 1 for the tile with local index lt
-        const uint32_t lbo = 128, sbo = (kKC / 4) * 128;
+        const uint32_t lbo = 128, sbo = (kKC / 8) * 128;
         long g = 0;
         int lt = 0;
         for (int t = blockIdx.x; t < ntiles && !*s_abort; t += gridDim.x, ++lt) {
@@ -1179,10 +1251,10 @@ __global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ 
                 const int s = (int)(g % kTcpStages);
                 if (!mbar_wait_or_abort(su32(full + s), (uint32_t)((g / kTcpStages) & 1), s_abort)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const float* sA = stages + (size_t)s * kTcpStageFloats;
-                const uint32_t aH = su32(sA), aL = su32(sA + kM * kKC), bH = su32(sA + 2 * kM * kKC),
-                               bL = su32(sA + 2 * kM * kKC + kTN * kKC);
-                for (uint32_t ks = 0; ks < kKC / 8; ++ks) {
+                const unsigned char* sA = stages + (size_t)s * kTcpStageBytes;
+                const uint32_t aH = su32(sA), aL = su32(sA + kTcpPartBytes), bH = su32(sA + 2 * kTcpPartBytes),
+                               bL = su32(sA + 3 * kTcpPartBytes);
+                for (uint32_t ks = 0; ks < kKC / 16; ++ks) {                  // K = 16 halves (32 bytes) per MMA
                     const uint32_t koff = ks * 256;
                     const uint64_t ah = sdesc(aH + koff, lbo, sbo), al = sdesc(aL + koff, lbo, sbo);
                     const uint64_t bh = sdesc(bH + koff, lbo, sbo), bl = sdesc(bL + koff, lbo, sbo);
@@ -1334,7 +1406,8 @@ static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent
         IGS_CUDA(cudaEventRecord(evJ, s1));
         IGS_CUDA(cudaStreamWaitEvent(s0, evJ, 0));
     }
-    k_finalize<T><<<dim3((n + 255) / 256, n), 256, 0, s0>>>(n, F, (const T*)p->d_diagL);
+    const int nft = (n + kTT - 1) / kTT;
+    k_finalize<T><<<nft * (nft + 1) / 2, 256, 0, s0>>>(n, F, (const T*)p->d_diagL);
     k_diag_inverse<T><<<(n + kNB - 1) / kNB, 256, 0, s0>>>(n, (const T*)p->d_diagL, (T*)p->d_diagLinv);
     IGS_CUDA(cudaGetLastError());
 }
@@ -1354,9 +1427,9 @@ constexpr int kBlockedMinN = 4096;
 // block k+1 does not overwrite what the rest-update of block k still reads;
 // the split of block k+2 comes after the s0 wait on that rest-update.
 static int tcb_groups(int n) { return 2 * ((n + (int)tc::kM - 1) / (int)tc::kM); }
-static size_t tcb_image_floats(int n) { return (size_t)(kOB / kKC) * 2 * tcb_groups(n) * kImgFloats; }
+static size_t tcb_image_halves(int n) { return (size_t)(kOB / kKC) * 2 * tcb_groups(n) * kImgHalves; }
 
-static void tcb_launch(int n, float* F, const float* img, int K0, int kbo, int tj_off, int tcols, int* flag,
+static void tcb_launch(int n, float* F, const __half* img, int K0, int kbo, int tj_off, int tcols, int* flag,
                        cudaStream_t s) {
     const int rem = n - K0 - kbo;
     const int ntr = (rem + (int)tc::kM - 1) / (int)tc::kM;
@@ -1397,7 +1470,7 @@ static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, c
         if (rem <= 0) continue;
         const int ntc = (rem + (int)kTN - 1) / (int)kTN;             // 128-column tiles
         const int G2 = 2 * ((rem + (int)tc::kM - 1) / (int)tc::kM);
-        float* img = p->d_timg + (size_t)((K0 / kOB) & 1) * tcb_image_floats(n);
+        __half* img = reinterpret_cast<__half*>(p->d_timg) + (size_t)((K0 / kOB) & 1) * tcb_image_halves(n);
         k_split_panel<<<dim3(G2, (kbo + kKC - 1) / kKC), 256, 0, s0>>>(n, F, K0, kbo, K0 + kbo, G2, img);
         const int first = std::min(ntc, kOB / (int)kTN);             // the next outer block's column tiles
         if (ntc > first) IGS_CUDA(cudaEventRecord(evP, s0));
@@ -1418,7 +1491,8 @@ static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, c
         IGS_CUDA(cudaEventRecord(evJ, s1));
         IGS_CUDA(cudaStreamWaitEvent(s0, evJ, 0));
     }
-    k_finalize<float><<<dim3((n + 255) / 256, n), 256, 0, s0>>>(n, F, (const float*)p->d_diagL);
+    const int nft = (n + kTT - 1) / kTT;
+    k_finalize<float><<<nft * (nft + 1) / 2, 256, 0, s0>>>(n, F, (const float*)p->d_diagL);
     k_diag_inverse<float><<<(n + kNB - 1) / kNB, 256, 0, s0>>>(n, (const float*)p->d_diagL, (float*)p->d_diagLinv);
     IGS_CUDA(cudaGetLastError());
 }
@@ -1537,7 +1611,7 @@ static void prepare_factor(igs_prob p, cudaStream_t s) {
         p->d_tflags = (int*)dev_alloc(p, sizeof(int) * ((n + kNB - 1) / kNB));
         IGS_CUDA(cudaMemsetAsync(p->d_tflags, 0, sizeof(int) * ((n + kNB - 1) / kNB), s));
         if (std::is_same<T, float>::value && n >= kBlockedMinN)
-            p->d_timg = (float*)dev_alloc(p, sizeof(float) * 2 * tcb_image_floats(n));
+            p->d_timg = (float*)dev_alloc(p, sizeof(__half) * 2 * tcb_image_halves(n));
         if (std::is_same<T, float>::value) {
             p->d_tpub = (unsigned long long*)dev_alloc(p, sizeof(unsigned long long) * 8 * (size_t)n);
             IGS_CUDA(cudaMemsetAsync(p->d_tpub, 0, sizeof(unsigned long long) * 8 * (size_t)n, s));
@@ -1551,7 +1625,17 @@ static void prepare_factor(igs_prob p, cudaStream_t s) {
         IGS_CUDA(cudaStreamSynchronize(s));
     }
     if (!p->d_As64) p->d_As64 = (double*)dev_alloc(p, sizeof(double) * (size_t)n * n);
-    k_symmetrize<T><<<dim3((n + 255) / 256, n), 256, 0, s>>>(n, (const T*)p->d_A, (T*)p->d_F, p->d_As64);
+    // MIXED tier: factor D As D with unit diagonal (D = diag(As_ii^-1/2)), so that
+    // every factor entry is at most 1 in magnitude (the tensor-core update's split)
+    const bool scaled = std::is_same<T, float>::value;
+    if (scaled) {
+        if (!p->d_dscale) p->d_dscale = (double*)dev_alloc(p, sizeof(double) * (size_t)n);
+        k_diag_scale<T><<<(n + 255) / 256, 256, 0, s>>>(n, (const T*)p->d_A, p->d_dscale);
+        p->launches++;
+    }
+    const int nst = (n + sym_tile<T>() - 1) / sym_tile<T>();
+    k_symmetrize<T><<<nst * (nst + 1) / 2, 256, 0, s>>>(n, (const T*)p->d_A, (T*)p->d_F, p->d_As64,
+                                                       scaled ? p->d_dscale : nullptr);
     p->launches++;
     IGS_CUDA(cudaGetLastError());
     factor<T>(p, s);
@@ -1572,7 +1656,8 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
     const double* scale = nullptr;
     IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s));
     for (;;) {
-        k_cast_in<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, src, d_x, scale, n);
+        const double* dsc = std::is_same<T, float>::value ? p->d_dscale : nullptr;
+        k_cast_in<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, src, d_x, scale, n, dsc);
         if (std::is_same<T, float>::value && p->coop_ok) {
             launch_trsv_pk(n, (const float*)p->d_F, (const float*)p->d_diagLinv, (float*)d_x, nrhs, 1, p->d_tpub,
                            ++p->tepoch, p->d_flag, s);
@@ -1587,7 +1672,7 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
             launch_trsv<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 1, s);
             launch_trsv<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 0, s);
         }
-        k_accum<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, d_x, d_alpha, scale, n, it == 0);
+        k_accum<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, d_x, d_alpha, scale, n, it == 0, dsc);
         launch_resid(n, nrhs, p->d_As64, d_alpha, d_beta, d_r, d_norm, s);
         p->launches += 6;
         IGS_CUDA(cudaGetLastError());

@@ -190,13 +190,35 @@ def test_rhs_magnitude_bounds_beta():
     h = wl.Harmonic("log")
     un = h.value(*bspline.curve_eval(c, eta, 0)[0])[:, None]
     ug = h.value(*bspline.curve_eval(c, tg, 0)[0])[:, None]
-    beta, S = oa.build_rhs(c, n, d, 2, un, ug, magnitude=True)
+    beta, S, K = oa.build_rhs(c, n, d, 2, un, ug, magnitude=True)
     assert np.all(S >= np.abs(beta) * (1 - 1e-14))
     assert np.max(S) > 2 * np.max(np.abs(beta))          # the star's terms cancel
     arc = wl.parabola_arc()
     eta, tg, _ = oa.rhs_points(arc, 12, 2, 1)
-    b1, S1 = oa.build_rhs(arc, 12, 2, 1, np.ones((len(eta), 1)), np.ones((len(tg), 1)), magnitude=True)
+    b1, S1, K1 = oa.build_rhs(arc, 12, 2, 1, np.ones((len(eta), 1)), np.ones((len(tg), 1)), magnitude=True)
+    assert np.all(K1 == 0.0)
     W = oa.rules.regular_rules(oa.make_discretization(arc, 12, 2, 1))
     nonneg = np.all(W >= 0, axis=0)
     np.testing.assert_allclose(S1[nonneg, 0], b1[nonneg, 0], rtol=1e-14)
     assert np.all(S1 >= np.abs(b1) * (1 - 1e-14))
+
+
+def test_rhs_sensitivity_bound_holds():
+    """K of build_rhs(magnitude=True) bounds the change of beta when the curve
+    moves by about one unit in the last place (control points perturbed by
+    one ulp with random signs: f and f' move by at most about 2 ulps)."""
+    import copy
+    c = wl.star_curve()
+    n, d = 64, 3
+    eta, tg, _ = oa.rhs_points(c, n, d, 2)
+    h = wl.Harmonic("log")
+    un = h.value(*bspline.curve_eval(c, eta, 0)[0])[:, None]
+    ug = h.value(*bspline.curve_eval(c, tg, 0)[0])[:, None]
+    beta, S, K = oa.build_rhs(c, n, d, 2, un, ug, magnitude=True)
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        cp = copy.deepcopy(c)
+        cp.ctrl = c.ctrl * (1.0 + rng.choice([-1.0, 1.0], size=c.ctrl.shape) * 2.0 ** -52)
+        bp = oa.build_rhs(cp, n, d, 2, un, ug)
+        assert np.all(np.abs(bp - beta) <= 4.0 * K + 1e-15 * S)
+    assert np.max(K) > 0
