@@ -117,7 +117,7 @@ template <typename T, int D>
 __global__ void __launch_bounds__(256) k_assemble_tile(
     int n, int Nq, int closed, T invL2, const int* __restrict__ lo, const int* __restrict__ hi,
     const int* __restrict__ jfirst, const typename NodeOf<T>::type* __restrict__ nodes, const T* __restrict__ P,
-    const T* __restrict__ Q, const WsView<T> wsv, T* __restrict__ A, int64_t ld, int maxr) {
+    const T* __restrict__ Q, const WsView<T> wsv, T* __restrict__ A, T* __restrict__ AT, int64_t ld, int maxr) {
     using Node = typename NodeOf<T>::type;
     constexpr int D1 = D + 1;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(256) k_assemble_tile(
             if (r >= 0 && r <= D) s += sPA[a * D1 + r] * sS1[a * (kTile + 1) + jl];
         }
         A[(size_t)i * ld + j0 + jl] = scale * s;
+        if (AT) AT[(size_t)(j0 + jl) * ld + i] = scale * s;
     }
 }
 
@@ -393,11 +394,17 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
         for (int r = 0; r < D1; ++r) acc[r] = 0.0f;
         int jc = sJA[bs];
         float* Arow = t.A + (size_t)i0 * t.ld + j0 + lane;
+        // A^T[j][i]: lane j's row of A^T, consecutive i from this warp (the partial
+        // stores of a 32-byte sector come from one warp and merge in L2)
+        float* ATcol = t.AT ? t.AT + (size_t)(j0 + lane) * t.ld + i0 : nullptr;
         const bool col = lane < nj;
         for (int b = bs; b <= be; ++b) {
             const int jb = sJA[b];
             while (jc < jb) {
-                if (col && jc >= r0 && jc < r1) Arow[(size_t)jc * t.ld] = scale * acc[0];
+                if (col && jc >= r0 && jc < r1) {
+                    Arow[(size_t)jc * t.ld] = scale * acc[0];
+                    if (ATcol) ATcol[jc] = scale * acc[0];
+                }
 #pragma unroll
                 for (int r = 0; r < D; ++r) acc[r] = acc[r + 1];
                 acc[D] = 0.0f;
@@ -409,7 +416,10 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
         }
 #pragma unroll
         for (int r = 0; r < D1; ++r)
-            if (col && jc + r >= r0 && jc + r < r1) Arow[(size_t)(jc + r) * t.ld] = scale * acc[r];
+            if (col && jc + r >= r0 && jc + r < r1) {
+                Arow[(size_t)(jc + r) * t.ld] = scale * acc[r];
+                if (ATcol) ATcol[jc + r] = scale * acc[r];
+            }
     }
 }
 
@@ -430,7 +440,7 @@ TileF tile_args_f(igs_prob p, int maxr) {
     return TileF{P.n, P.Nq, p->d_lo, p->d_hi, p->d_jfirst, (const NodeF*)p->d_nodes,
                  (const float*)p->d_P, (const float*)p->d_Q,
                  WsView<float>{p->d_WsT32, p->d_WsRow32, p->d_WsToe32, P.Nq, p->ws_B, p->ws_R}, (float*)p->d_A,
-                 (int64_t)P.n, maxr};
+                 (float*)p->d_AT, (int64_t)P.n, maxr};
 }
 
 template <int D, bool CLOSED>
@@ -471,7 +481,7 @@ static void launch_tile(igs_prob p, int maxr, cudaStream_t s) {
                        f32 ? (const T*)p->d_WsToe32 : (const T*)p->d_WsToe, P.Nq, p->ws_B, p->ws_R};
     kern<<<grid, 256, sm, s>>>(P.n, P.Nq, P.closed, (T)(f32 ? 1.0 : 1.0 / (P.L * P.L)), p->d_lo, p->d_hi, p->d_jfirst,
                                (const typename NodeOf<T>::type*)p->d_nodes, (const T*)p->d_P, (const T*)p->d_Q, ws,
-                               (T*)p->d_A, (int64_t)P.n, maxr);
+                               (T*)p->d_A, (T*)p->d_AT, (int64_t)P.n, maxr);
     IGS_CUDA(cudaGetLastError());
 }
 
@@ -534,9 +544,11 @@ void assemble_matrix(igs_prob p) {
     const bool mixed = p->precision == IGS_MIXED;
     const size_t esz = mixed ? sizeof(float) : sizeof(double);
     if (!p->d_A) p->d_A = dev_alloc(p, esz * (size_t)P.n * P.n);
+    if (!p->d_AT) p->d_AT = dev_alloc(p, esz * (size_t)P.n * P.n);
     const int maxr = max_tile_range(P, kTile);
     if (mixed) launch_tile_deg<float>(p, maxr, s);
     else launch_tile_deg<double>(p, maxr, s);
+    p->at_ready = 1;
     p->launches++;
 }
 

@@ -86,6 +86,7 @@ void build(igs_batch b) {
         if (maxr > 512) throw Error(IGS_E_INVALID_ARG, "batch: a tile's node range exceeds 512 nodes");
         const int nt = (P.n + TI - 1) / TI;
         items[k] = BatchItemF{tile_args_f(p, maxr), P.d, P.closed, nt};
+        items[k].t.AT = nullptr;                     // the batched form does not factor: no A^T
         ntiles[k] = nt * nt;
         maxthreads = std::max(maxthreads, (maxr + 31) / 32 * 32);
         smem = std::max(smem, tile_smem_f(maxr, P.d, TI));
@@ -171,6 +172,7 @@ float run(igs_batch b) {
         p->geometry_ready = 1;
         p->assembled = 1;
         p->factored = 0;
+        p->at_ready = 0;                             // a later solve transposes A itself
     }
     b->last_ms = ms;
     return ms;

@@ -127,6 +127,8 @@ struct igs_prob_s {
 
     // matrix and solve
     void* d_A = nullptr;          // [n][n] tier type (row-major)
+    void* d_AT = nullptr;         // [n][n] A^T in the tier type, written by the assembly for the symmetrisation
+    int at_ready = 0;             // d_AT holds the transpose of the current A
     void* d_F = nullptr;          // [n][n] Cholesky factor (tier type): lower = L, upper = L^T
     void* d_diagL = nullptr;      // [n][64] factored diagonal blocks of L (tier type)
     void* d_diagLinv = nullptr;   // [n][64] inverses of the diagonal blocks of L (tier type)
@@ -138,8 +140,8 @@ struct igs_prob_s {
     int tepoch = 0;               // flag value of the current triangular solve
     cudaStream_t aux_stream = nullptr;   // right-hand side beside the factorisation (igs_solve_data)
     bool coop_ok = false;         // cooperative launch available
-    double* d_As64 = nullptr;     // (A+A^T)/2 in FP64 for the refinement residuals
-    double* d_dscale = nullptr;   // [n] As_ii^-1/2: the MIXED factor is that of D As D
+    double* d_As64 = nullptr;     // (A+A^T)/2 in FP64 for the refinement residuals (FP64 tier)
+    float* d_dscale = nullptr;    // [n] As_ii^-1/2: the MIXED factor is that of D As D
     int rhs_n = 0;
     double* d_beta = nullptr;     // [nrhs][n]
     double* d_rhs_geo = nullptr;  // [5][Ng] geometry at the rhs Gauss points
@@ -218,6 +220,7 @@ struct TileF {
     const float* Q;
     WsView<float> ws;
     float* A;
+    float* AT;           // A^T (row-major, same ld), written beside A when not NULL
     int64_t ld;
     int maxr;
 };

@@ -57,8 +57,9 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
-// Device bytes a request holds at its peak: the matrix, factor and FP64
-// symmetric copy (n^2 each in the tier type, the copy in FP64), the stored
+// Device bytes a request holds at its peak: the matrix, its transpose and the
+// factor (n^2 each in the tier type) and, in the FP64 tier, the symmetric copy
+// for the residuals (n^2 FP64), the stored
 // rules and their construction work arrays, node data and the right-hand
 // sides; 25% margin.
 int64_t estimate_bytes(const igs_request& r) {
@@ -66,7 +67,7 @@ int64_t estimate_bytes(const igs_request& r) {
     const int64_t n = r.closed ? Nh : Nh + d;
     const int64_t Nq = 2 * d + 2 * M - 1, NE = M + d, D1 = d + 1;
     const int64_t tsz = r.precision == IGS_MIXED ? 4 : 8;
-    int64_t b = n * n * (2 * tsz + 8);
+    int64_t b = n * n * (3 * tsz + (r.precision == IGS_MIXED ? 0 : 8));
     const int64_t B = 24 * D1 + 16, R = d + 2, ncols = 2 * B + 4;
     if (Nq < 2 * B + 2 * R + 64) b += Nq * Nq * 12 + NE * Nq * 8;
     else b += ncols * Nq * 8 + ncols * NE * 8 + (2 * B + 2 * R + 4) * Nq * 12 + ncols * 1024 * D1 * 8;

@@ -31,53 +31,15 @@ constexpr int kNB = 64;      // Cholesky panel width / triangular-solve block
 constexpr int kTT = 64;
 __device__ __forceinline__ void tri_decode(int t, int& ti, int& tj);
 
-// dscale[i] = 1 / sqrt(A_ii): the unit-diagonal scaling D of the MIXED tier's
-// factorisation (a non-positive diagonal keeps 1 and the factorisation flags it).
-template <typename T>
-__global__ void k_diag_scale(int n, const T* __restrict__ A, double* __restrict__ dscale) {
+// dscale[i] = 1 / sqrt(A_ii) in FP32: the unit-diagonal scaling D of the MIXED
+// tier's factorisation (a non-positive diagonal keeps 1 and the factorisation
+// flags it).  The refinement applies the same FP32 values, so the factor is
+// that of D As D with D exactly as stored.
+__global__ void k_diag_scale(int n, const float* __restrict__ A, float* __restrict__ dscale) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double a = (double)A[(size_t)i * n + i];
-    dscale[i] = a > 0.0 ? 1.0 / sqrt(a) : 1.0;
-}
-
-// As = (A + A^T)/2 by tile pairs (TS x TS: 64 for FP32, 32 for FP64 to stay
-// within static shared memory), both tiles read and both written row by row
-// through shared memory (coalesced in both orientations).  F gets the lower
-// triangle of D As D (D = diag(dscale), identity if dscale is NULL) in the
-// tier type; As64, if given, the whole As in FP64 (exact for an FP32 A).
-template <typename T> __host__ __device__ constexpr int sym_tile() { return sizeof(T) == 8 ? 32 : 64; }
-template <typename T>
-__global__ void __launch_bounds__(256) k_symmetrize(int n, const T* __restrict__ A, T* __restrict__ F,
-                                                    double* __restrict__ As64, const double* __restrict__ dscale) {
-    constexpr int TS = sym_tile<T>(), RS = 256 / TS;          // RS rows per pass
-    __shared__ T t1[TS][TS + 1];             // A tile (bi, bj)
-    __shared__ T t2[TS][TS + 1];             // A tile (bj, bi)
-    int bi, bj;
-    tri_decode(blockIdx.x, bi, bj);
-    const int i0 = bi * TS, j0 = bj * TS;
-    const int c = threadIdx.x % TS, r0 = threadIdx.x / TS;
-    for (int r = r0; r < TS; r += RS) {
-        const int i = i0 + r, j = j0 + c;
-        t1[r][c] = (i < n && j < n) ? A[(size_t)i * n + j] : (T)0;
-        const int i2 = j0 + r, j2 = i0 + c;
-        t2[r][c] = (i2 < n && j2 < n) ? A[(size_t)i2 * n + j2] : (T)0;
-    }
-    __syncthreads();
-    // s(r, c) = (A[i0+r][j0+c] + A[j0+c][i0+r]) / 2 = (t1[r][c] + t2[c][r]) / 2
-    for (int r = r0; r < TS; r += RS) {
-        const int i = i0 + r, j = j0 + c;
-        if (i >= n || j >= n) continue;
-        const double v = 0.5 * ((double)t1[r][c] + (double)t2[c][r]);
-        if (j <= i) F[(size_t)i * n + j] = dscale ? (T)(v * dscale[i] * dscale[j]) : (T)v;
-        if (As64) As64[(size_t)i * n + j] = v;
-    }
-    if (As64 && bi != bj) {
-        for (int r = r0; r < TS; r += RS) {                 // tile (bj, bi): s(c, r) transposed
-            const int i = j0 + r, j = i0 + c;
-            if (i < n && j < n) As64[(size_t)i * n + j] = 0.5 * ((double)t1[c][r] + (double)t2[r][c]);
-        }
-    }
+    const float a = A[(size_t)i * n + i];
+    dscale[i] = a > 0.0f ? rsqrtf(a) : 1.0f;
 }
 
 template <typename T> struct Vec16;
@@ -90,6 +52,82 @@ template <> __device__ __forceinline__ float vget<float>(const float4& v, int q)
     return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
 }
 template <> __device__ __forceinline__ double vget<double>(const double2& v, int q) { return q == 0 ? v.x : v.y; }
+
+// A^T from A through 32 x 32 shared-memory tiles (for a matrix assembled
+// without its transpose, e.g. by the batched form).
+template <typename T>
+__global__ void __launch_bounds__(256) k_transpose(int n, const T* __restrict__ A, T* __restrict__ AT) {
+    __shared__ T t[32][33];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    for (int r = threadIdx.x / 32; r < 32; r += 8) {
+        const int i = i0 + r, j = j0 + threadIdx.x % 32;
+        if (i < n && j < n) t[r][threadIdx.x % 32] = A[(size_t)i * n + j];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x / 32; r < 32; r += 8) {
+        const int i = j0 + r, j = i0 + threadIdx.x % 32;
+        if (i < n && j < n) AT[(size_t)i * n + j] = t[threadIdx.x % 32][r];
+    }
+}
+
+// FP64 tier: As = (A + A^T)/2 from A and A^T (both row-major, written by the
+// assembly), one 16-byte vector of each per thread: a streaming kernel, every
+// access coalesced.  F gets the lower triangle of As, As64 the whole As (for
+// the residual).  Grid (row chunks, rows).
+template <typename T>
+__global__ void __launch_bounds__(256) k_symmetrize(int n, const T* __restrict__ A, const T* __restrict__ AT,
+                                                    T* __restrict__ F, double* __restrict__ As64) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N;
+    const int i = blockIdx.y;
+    const size_t rowoff = (size_t)i * n;
+    if ((n % VN) == 0) {
+        const int j = (blockIdx.x * blockDim.x + threadIdx.x) * VN;
+        if (j >= n) return;
+        const V a = *(const V*)(A + rowoff + j), at = *(const V*)(AT + rowoff + j);
+#pragma unroll
+        for (int u = 0; u < VN; ++u) {
+            const double v = 0.5 * ((double)vget<T>(a, u) + (double)vget<T>(at, u));
+            As64[rowoff + j + u] = v;
+            if (j + u <= i) F[rowoff + j + u] = (T)v;
+        }
+    } else {
+        for (int u = 0; u < VN; ++u) {
+            const int j = (blockIdx.x * blockDim.x + threadIdx.x) * VN + u;
+            if (j >= n) return;
+            const double v = 0.5 * ((double)A[rowoff + j] + (double)AT[rowoff + j]);
+            As64[rowoff + j] = v;
+            if (j <= i) F[rowoff + j] = (T)v;
+        }
+    }
+}
+
+// MIXED tier: the lower triangle of D As D, As = (A + A^T)/2, in FP32 from A
+// and A^T, four entries per thread (16-byte loads and stores); no FP64
+// arithmetic (FP64 runs at 1/64 of the FP32 rate on this GPU).  Grid (column
+// chunks of 1024, rows); chunks above the diagonal return at once.
+__global__ void __launch_bounds__(256) k_symmetrize_lower_f(int n, const float* __restrict__ A,
+                                                            const float* __restrict__ AT, float* __restrict__ F,
+                                                            const float* __restrict__ dscale) {
+    const int i = blockIdx.y;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (j > i) return;
+    const size_t rowoff = (size_t)i * n;
+    const float di = 0.5f * dscale[i];
+    if ((n & 3) == 0 && j + 3 <= i) {
+        const float4 a = *(const float4*)(A + rowoff + j), at = *(const float4*)(AT + rowoff + j);
+        const float4 dj = *(const float4*)(dscale + j);
+        float4 v;
+        v.x = (a.x + at.x) * di * dj.x;
+        v.y = (a.y + at.y) * di * dj.y;
+        v.z = (a.z + at.z) * di * dj.z;
+        v.w = (a.w + at.w) * di * dj.w;
+        *(float4*)(F + rowoff + j) = v;
+    } else {
+        for (int u = 0; u < 4 && j + u <= i && j + u < n; ++u)
+            F[rowoff + j + u] = (A[rowoff + j + u] + AT[rowoff + j + u]) * di * dscale[j + u];
+    }
+}
 
 // Panel step at column k0 (width kb).  CTA 0 factors the 64 x 64 diagonal
 // block and stores L11; CTA b >= 1 factors the tall block made of the
@@ -873,6 +911,100 @@ __global__ void __launch_bounds__(kNormThreads) k_norms(int n, const double* __r
     }
 }
 
+// MIXED tier residual without FP64 arithmetic: r = beta - As alpha with
+// As = (A + A^T)/2 read from the FP32 A and A^T, in float-float arithmetic
+// (pairs hi + lo carrying about 48 bits).  Per entry: t = a + a' exactly as a
+// pair (two-sum), the product with alpha_j = ah + al (the exact product th ah
+// by a fused multiply-add, the cross terms rounded) and a two-sum into the
+// running pair.  One warp per row, lanes over 4-column groups in order, then
+// a fixed shuffle tree of pair additions: deterministic.  The final
+// conversion r_i = beta_i - (sh + sl)/2 is the only FP64 arithmetic (once per
+// row).  alpha_ff holds alpha as (hi, lo) pairs, [NR][n].
+// (the _rn intrinsics keep the compiler from contracting these into FMAs,
+// which would break the error-free transforms)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a), av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+__device__ __forceinline__ void ff_add(float& sh, float& sl, float ph, float pl) {
+    float s, e;
+    two_sum(sh, ph, s, e);
+    sh = s;
+    sl += e + pl;
+}
+
+__global__ void k_split_alpha(int cnt, const double* __restrict__ alpha, float2* __restrict__ aff) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cnt) return;
+    const double a = alpha[q];
+    const float h = (float)a;
+    aff[q] = make_float2(h, (float)(a - (double)h));
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256) k_resid_ff(int n, const float* __restrict__ A, const float* __restrict__ AT,
+                                                  const float2* __restrict__ aff, const double* __restrict__ beta,
+                                                  double* __restrict__ r) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+    if (warp >= n) return;
+    const int i = warp;
+    const float* a_row = A + (size_t)i * n;
+    const float* t_row = AT + (size_t)i * n;
+    float sh[NR], sl[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) sh[k] = sl[k] = 0.0f;
+    auto term = [&](float a, float at, int j) {
+        float th, tl;
+        two_sum(a, at, th, tl);
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const float2 al = aff[(size_t)k * n + j];
+            const float ph = __fmul_rn(th, al.x);
+            const float pl = fmaf(th, al.y, fmaf(tl, al.x, fmaf(th, al.x, -ph)));
+            ff_add(sh[k], sl[k], ph, pl);
+        }
+    };
+    if ((n & 3) == 0) {
+        for (int j = 4 * lane; j < n; j += 128) {
+            const float4 a = *(const float4*)(a_row + j), at = *(const float4*)(t_row + j);
+            term(a.x, at.x, j);
+            term(a.y, at.y, j + 1);
+            term(a.z, at.z, j + 2);
+            term(a.w, at.w, j + 3);
+        }
+    } else {
+        for (int j = lane; j < n; j += 32) term(a_row[j], t_row[j], j);
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        float h = sh[k], l = sl[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+            ff_add(h, l, oh, ol);
+        }
+        if (lane == 0) r[(size_t)k * n + i] = beta[(size_t)k * n + i] - 0.5 * ((double)h + (double)l);
+    }
+}
+
+static void launch_resid_ff(int n, int nrhs, const float* A, const float* AT, const double* alpha, float2* aff,
+                            const double* beta, double* r, double* norms, cudaStream_t s) {
+    k_split_alpha<<<(n * nrhs + 255) / 256, 256, 0, s>>>(n * nrhs, alpha, aff);
+    const dim3 g((n * 32 + 255) / 256), b(256);
+    switch (nrhs) {
+        case 1: k_resid_ff<1><<<g, b, 0, s>>>(n, A, AT, aff, beta, r); break;
+        case 2: k_resid_ff<2><<<g, b, 0, s>>>(n, A, AT, aff, beta, r); break;
+        case 3: k_resid_ff<3><<<g, b, 0, s>>>(n, A, AT, aff, beta, r); break;
+        case 4: k_resid_ff<4><<<g, b, 0, s>>>(n, A, AT, aff, beta, r); break;
+        case 5: k_resid_ff<5><<<g, b, 0, s>>>(n, A, AT, aff, beta, r); break;
+        case 6: k_resid_ff<6><<<g, b, 0, s>>>(n, A, AT, aff, beta, r); break;
+        case 7: k_resid_ff<7><<<g, b, 0, s>>>(n, A, AT, aff, beta, r); break;
+        default: k_resid_ff<8><<<g, b, 0, s>>>(n, A, AT, aff, beta, r); break;
+    }
+    k_norms<<<nrhs, kNormThreads, 0, s>>>(n, r, beta, norms);
+}
+
+
 static void launch_resid(int n, int nrhs, const double* As, const double* alpha, const double* beta, double* r,
                          double* norms, cudaStream_t s) {
     const dim3 g((n * 32 + 255) / 256), b(256);
@@ -894,24 +1026,24 @@ static void launch_resid(int n, int nrhs, const double* As, const double* alpha,
 // D As D, multiplied by D (dscale, if given).
 template <typename T>
 __global__ void k_cast_in(int cnt, const double* __restrict__ src, T* __restrict__ dst, const double* __restrict__ scale,
-                          int n, const double* __restrict__ dscale) {
+                          int n, const float* __restrict__ dscale) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= cnt) return;
     const double sc = scale ? scale[2 * (q / n)] : 0.0;
     const double inv = (sc > 0) ? 1.0 / sqrt(sc) : 1.0;
-    const double dv = dscale ? dscale[q % n] : 1.0;
+    const double dv = dscale ? (double)dscale[q % n] : 1.0;
     dst[q] = (T)(src[q] * inv * dv);
 }
 
 // x += D dx times the residual norm (the correction of one refinement step).
 template <typename T>
 __global__ void k_accum(int cnt, const T* __restrict__ dx, double* __restrict__ x, const double* __restrict__ scale,
-                        int n, int first, const double* __restrict__ dscale) {
+                        int n, int first, const float* __restrict__ dscale) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= cnt) return;
     const double sc = scale ? scale[2 * (q / n)] : 0.0;
     const double f = (sc > 0) ? sqrt(sc) : 1.0;
-    const double dv = dscale ? dscale[q % n] : 1.0;
+    const double dv = dscale ? (double)dscale[q % n] : 1.0;
     const double v = (double)dx[q] * f * dv;
     x[q] = first ? v : x[q] + v;
 }
@@ -1088,12 +1220,12 @@ __global__ void __launch_bounds__(256) k_syrk_tc(int n, float* __restrict__ F, i
 // of D As D, every entry at most 1 in magnitude), as FP16 high and low parts
 // x = hi + lo + O(2^-22 |x| + 2^-25), in the shared-memory image the MMA
 // descriptors read: K-major core matrices of 8 rows x 16 bytes, element (r, l)
-// of a 64-row group and a chunk of kKC = 64 columns at half offset
-// (((r/8)*8 + l/8)*8 + r%8)*8 + l%8.  img[(kc*2 + part)*G2 + g] is the 8 KB
+// of a 64-row group and a chunk of kKC = 32 columns at half offset
+// (((r/8)*4 + l/8)*8 + r%8)*8 + l%8.  img[(kc*2 + part)*G2 + g] is the 4 KB
 // image of row group g, K chunk kc, part 0 = high, 1 = low; rows >= n and
 // columns >= K0 + kbo are zero.  Grid (G2, chunks).
-constexpr int kKC = 64;                     // factor columns per K chunk (128 bytes of FP16 per row)
-constexpr int kImgHalves = 64 * kKC;        // one 64-row group of one chunk and part (8 KB)
+constexpr int kKC = 32;                     // factor columns per K chunk (64 bytes of FP16 per row)
+constexpr int kImgHalves = 64 * kKC;        // one 64-row group of one chunk and part (4 KB)
 __global__ void __launch_bounds__(256) k_split_panel(int n, const float* __restrict__ F, int K0, int kbo, int base,
                                                      int G2, __half* __restrict__ img) {
     const int g = blockIdx.x, kc = blockIdx.y;
@@ -1118,22 +1250,25 @@ __global__ void __launch_bounds__(256) k_split_panel(int n, const float* __restr
 
 
 // Persistent, warp-specialised form of the outer-block update (MIXED tier,
-// n >= 4096): one CTA per SM walks its share of the 128 x 128 lower-triangle
-// tiles (column tiles tj_off .. ntc-1; in column tile tj the row tiles
-// tj .. ntr-1) in column order.  Warp 0 issues the bulk copies of the split
-// operand images into kTcpStages 64 KB stages, warp 1 issues the MMAs of the
-// three-term FP16 split (hi.hi + hi.lo + lo.hi, FP32 accumulation; kind::f16
-// runs at twice the TF32 rate on half the operand bytes; N = 128) into one of
-// two TMEM accumulators, warps 4-7 read the other
-// accumulator back (one tile row per lane, two halves of 64 columns) and
-// apply C -= D, so a tile's epilogue runs under the next tile's copies and
-// MMAs.  Every wait is bounded: on a timeout (or after another role's
-// timeout) the kernel sets *flag |= 2 and skips the rest.
-constexpr int kTcpStages = 3;
-constexpr uint32_t kTN = 128;                                  // tile columns (MMA N)
-constexpr uint32_t kTcpPartBytes = tc::kM * kKC * 2;           // 128 rows x one chunk of FP16 (16 KB)
-constexpr uint32_t kTcpStageBytes = 4 * kTcpPartBytes;         // A hi, A lo, B hi, B lo (kTN == kM)
-constexpr size_t tcp_smem_bytes() { return (size_t)kTcpStages * kTcpStageBytes + 128; }
+// n >= 4096): one CTA per SM walks its share of the 128 x 256 lower-triangle
+// tiles (column tiles tj_off .. ntc-1 of 256 columns; in column tile tj the
+// 128-row tiles 2 tj .. ntr-1) in column order.  Warp 0 issues the bulk
+// copies of the split operand images into kTcpStages 48 KB stages, warp 1
+// issues the MMAs of the three-term FP16 split (hi.hi + hi.lo + lo.hi, FP32
+// accumulation; kind::f16 runs at twice the TF32 rate on half the operand
+// bytes; M = 128, N = 256: each operand byte serves 1.33x the flops of a
+// 128 x 128 tile) into one of two TMEM accumulators (2 x 256 columns), warps
+// 4-11 read the other accumulator back (one tile row per lane, one 128-column
+// half per warp) and apply C -= D, so a tile's epilogue runs under the next
+// tile's copies and MMAs.  Every wait is bounded: on a timeout (or after
+// another role's timeout) the kernel sets *flag |= 2 and skips the rest.
+constexpr int kTcpStages = 4;
+constexpr uint32_t kTN = 256;                                  // tile columns (MMA N)
+constexpr uint32_t kTcpPartA = tc::kM * kKC * 2;               // 128 rows x one chunk of FP16 (8 KB)
+constexpr uint32_t kTcpPartB = kTN * kKC * 2;                  // 256 rows x one chunk of FP16 (16 KB)
+constexpr uint32_t kTcpStageBytes = 2 * kTcpPartA + 2 * kTcpPartB;   // A hi, A lo, B hi, B lo (48 KB)
+constexpr uint32_t kTcpBufBytes = 32 * 33 * 4;                // per epilogue warp: 32 x 32 block, padded rows
+constexpr size_t tcp_smem_bytes() { return (size_t)kTcpStages * kTcpStageBytes + 8 * kTcpBufBytes + 128; }
 // D F32, A and B F16, both K-major, N = kTN, M = 128
 __host__ __device__ constexpr uint32_t tcp_idesc() {
     return (1u << 4) | (0u << 7) | (0u << 10) | ((kTN >> 3) << 17) | ((tc::kM >> 4) << 24);
@@ -1147,9 +1282,9 @@ __device__ __forceinline__ void tcp_mma(uint32_t d, uint64_t a, uint64_t b, uint
 // first row tile of column tile tj is tj.
 struct TcpIter {
     int tj, ti, t;
-    __device__ void init(int tj_off) { tj = tj_off; ti = tj_off; t = 0; }
+    __device__ void init(int tj_off) { tj = tj_off; ti = 2 * tj_off; t = 0; }
     __device__ void seek(int target, int ntr) {
-        while (target - t >= ntr - ti) { t += ntr - ti; ++tj; ti = tj; }
+        while (target - t >= ntr - ti) { t += ntr - ti; ++tj; ti = 2 * tj; }
         ti += target - t;
         t = target;
     }
@@ -1170,13 +1305,14 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity
     return false;
 }
 
-__global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ F, const __half* __restrict__ img,
+constexpr int kTcpThreads = 384;              // warp 0 copies, warp 1 MMAs, warps 4-11 epilogue
+__global__ void __launch_bounds__(kTcpThreads, 1) k_syrk_tcp(int n, float* __restrict__ F, const __half* __restrict__ img,
                                                      int K0, int kbo, int G2, int tj_off, int ntc, int ntr, int ntiles,
                                                      int* __restrict__ flag) {
     using namespace tc;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* stages = smem_raw;
-    uint64_t* bars = (uint64_t*)(stages + (size_t)kTcpStages * kTcpStageBytes);
+    uint64_t* bars = (uint64_t*)(stages + (size_t)kTcpStages * kTcpStageBytes + 8 * kTcpBufBytes);
     uint64_t* full = bars;                         // [kTcpStages]
     uint64_t* empty = bars + kTcpStages;           // [kTcpStages]
     uint64_t* accf = bars + 2 * kTcpStages;        // [2]
@@ -1197,7 +1333,7 @@ __global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ 
         }
         for (int a = 0; a < 2; ++a) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(accf + a)), "r"(1));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(acce + a)), "r"(4));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(acce + a)), "r"(8));
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
         *s_abort = 0;
@@ -1225,15 +1361,18 @@ __global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ 
                 unsigned char* sA = stages + (size_t)s * kTcpStageBytes;
                 const uint32_t fb = su32(full + s);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"(kTcpStageBytes) : "memory");
-                // two consecutive 64-row groups (8 KB each) per operand part: 16 KB contiguous
+                // A: two consecutive 64-row groups (4 KB each) per part, 8 KB contiguous;
+                // B: four groups, 16 KB contiguous
                 const __half* srcs[4] = {img + ((size_t)(kc * 2 + 0) * G2 + 2 * it.ti) * kImgHalves,
                                          img + ((size_t)(kc * 2 + 1) * G2 + 2 * it.ti) * kImgHalves,
-                                         img + ((size_t)(kc * 2 + 0) * G2 + 2 * it.tj) * kImgHalves,
-                                         img + ((size_t)(kc * 2 + 1) * G2 + 2 * it.tj) * kImgHalves};
+                                         img + ((size_t)(kc * 2 + 0) * G2 + 4 * it.tj) * kImgHalves,
+                                         img + ((size_t)(kc * 2 + 1) * G2 + 4 * it.tj) * kImgHalves};
+                const uint32_t offs[4] = {0, kTcpPartA, 2 * kTcpPartA, 2 * kTcpPartA + kTcpPartB};
+                const uint32_t sizes[4] = {kTcpPartA, kTcpPartA, kTcpPartB, kTcpPartB};
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                                 :: "r"(su32(sA + q * kTcpPartBytes)), "l"(srcs[q]), "r"(kTcpPartBytes), "r"(fb) : "memory");
+                                 :: "r"(su32(sA + offs[q])), "l"(srcs[q]), "r"(sizes[q]), "r"(fb) : "memory");
             }
         }
     } else if (warp == 1 && lane == 0) {
@@ -1252,8 +1391,8 @@ __global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ 
                 if (!mbar_wait_or_abort(su32(full + s), (uint32_t)((g / kTcpStages) & 1), s_abort)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const unsigned char* sA = stages + (size_t)s * kTcpStageBytes;
-                const uint32_t aH = su32(sA), aL = su32(sA + kTcpPartBytes), bH = su32(sA + 2 * kTcpPartBytes),
-                               bL = su32(sA + 3 * kTcpPartBytes);
+                const uint32_t aH = su32(sA), aL = su32(sA + kTcpPartA), bH = su32(sA + 2 * kTcpPartA),
+                               bL = su32(sA + 2 * kTcpPartA + kTcpPartB);
                 for (uint32_t ks = 0; ks < kKC / 16; ++ks) {                  // K = 16 halves (32 bytes) per MMA
                     const uint32_t koff = ks * 256;
                     const uint64_t ah = sdesc(aH + koff, lbo, sbo), al = sdesc(aL + koff, lbo, sbo);
@@ -1270,13 +1409,34 @@ __global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ 
                          :: "r"(su32(accf + a)) : "memory");
         }
     } else if (warp >= 4) {
-        // epilogue: lane = tile row (warp - 4) * 32 + lane, 64 columns from TMEM
-        const int rw = warp - 4;
+        // epilogue: warp 4 + q + 4 h reads TMEM lane quadrant q (= warp % 4, the
+        // quadrant a warp may access) and column half h: tile rows 32 q .. +31,
+        // columns 128 h .. +127, in four passes of 32 columns.  A pass loads the
+        // 32 x 32 block from TMEM (lane = row), transposes it through the warp's
+        // padded shared-memory buffer and applies C -= D with lanes spread as 4
+        // rows x 8 float4 per instruction (4 cache lines per access instead of
+        // 32).  The first pass's C values are loaded before the accumulator wait.
+        const int q4 = (warp - 4) % 4, h = (warp - 4) / 4;
+        float (*buf)[33] = (float (*)[33])(stages + (size_t)kTcpStages * kTcpStageBytes + (size_t)(warp - 4) * kTcpBufBytes);
+        const int rl = lane / 8, c4 = lane % 8;                 // row-in-quad, float4 column of a pass
         TcpIter it;
         it.init(tj_off);
         int lt = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
             const int a = lt & 1, use = lt / 2;
+            it.seek(t, ntr);
+            const int i0 = base + it.ti * (int)kM, j0 = base + it.tj * (int)kTN;
+            const int ib = i0 + q4 * 32;                          // first row of this warp
+            float4 cv[8];
+            auto prefetch = [&](int ps) {
+                const int jc = j0 + h * 128 + ps * 32 + 4 * c4;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int i = ib + 4 * q + rl;
+                    if ((n & 3) == 0 && i < n && jc + 3 <= i) cv[q] = *(const float4*)(F + (size_t)i * n + jc);
+                }
+            };
+            prefetch(0);
             bool ok = mbar_wait_or_abort(su32(accf + a), (uint32_t)(use & 1), s_abort);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
@@ -1284,43 +1444,50 @@ __global__ void __launch_bounds__(256, 1) k_syrk_tcp(int n, float* __restrict__ 
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            it.seek(t, ntr);
-            const int i0 = base + it.ti * (int)kM, j0 = base + it.tj * (int)kTN;
-            const int i = i0 + rw * 32 + lane;
-            for (int h = 0; h < 2; ++h) {
-                float dv[64];
-#pragma unroll
-                for (int c0 = 0; c0 < 64; c0 += 16) {
-                    uint32_t r[16];
-                    const uint32_t addr = taddr + ((uint32_t)(rw * 32) << 16) + (uint32_t)(a * kTN + h * 64 + c0);
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                                 : "r"(addr));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) dv[c0 + q] = __uint_as_float(r[q]);
-                }
-                if (h == 1) {
-                    // the accumulator is free for the tile after next
+            for (int ps = 0; ps < 4; ++ps) {
+                uint32_t r[32];
+                const uint32_t addr = taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(a * kTN + h * 128 + ps * 32);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                               "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                               "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                             : "r"(addr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (ps == 3) {
+                    // this warp's share of the accumulator is read: free it for the tile after next
                     asm volatile("tcgen05.fence::before_thread_sync;");
                     __syncwarp();
                     if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(su32(acce + a)) : "memory");
                 }
-                const int jh = j0 + h * 64;
-                if (i < n && jh <= i) {
-                    float* row = F + (size_t)i * n + jh;
-                    if ((n & 3) == 0 && jh + 63 <= i) {
+                __syncwarp();                                     // the previous pass's reads of buf are done
 #pragma unroll
-                        for (int c = 0; c < 64; c += 4) {
-                            float4 v = *(const float4*)(row + c);
-                            v.x -= dv[c]; v.y -= dv[c + 1]; v.z -= dv[c + 2]; v.w -= dv[c + 3];
-                            *(float4*)(row + c) = v;
-                        }
-                    } else {
+                for (int c = 0; c < 32; ++c) buf[lane][c] = __uint_as_float(r[c]);
+                __syncwarp();
+                const int jc = j0 + h * 128 + ps * 32 + 4 * c4;
+                float4 w[8];
+                bool whole[8];
 #pragma unroll
-                        for (int c = 0; c < 64; ++c)
-                            if (jh + c <= i && jh + c < n) row[c] -= dv[c];
+                for (int q = 0; q < 8; ++q) {
+                    const int rr = 4 * q + rl, i = ib + rr;
+                    whole[q] = (n & 3) == 0 && i < n && jc + 3 <= i;
+                    w[q] = cv[q];
+                    w[q].x -= buf[rr][4 * c4];
+                    w[q].y -= buf[rr][4 * c4 + 1];
+                    w[q].z -= buf[rr][4 * c4 + 2];
+                    w[q].w -= buf[rr][4 * c4 + 3];
+                }
+                if (ps < 3) prefetch(ps + 1);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int rr = 4 * q + rl, i = ib + rr;
+                    if (whole[q]) {
+                        *(float4*)(F + (size_t)i * n + jc) = w[q];
+                    } else if (i < n) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (jc + u <= i && jc + u < n) F[(size_t)i * n + jc + u] -= buf[rr][4 * c4 + u];
                     }
                 }
             }
@@ -1426,7 +1593,9 @@ constexpr int kBlockedMinN = 4096;
 // The image buffers hold two outer blocks (alternating), so the split of
 // block k+1 does not overwrite what the rest-update of block k still reads;
 // the split of block k+2 comes after the s0 wait on that rest-update.
-static int tcb_groups(int n) { return 2 * ((n + (int)tc::kM - 1) / (int)tc::kM); }
+// 64-row groups of the split images: four per 256-column tile (which also
+// covers the two per 128-row tile)
+static int tcb_groups(int n) { return 4 * ((n + (int)kTN - 1) / (int)kTN); }
 static size_t tcb_image_halves(int n) { return (size_t)(kOB / kKC) * 2 * tcb_groups(n) * kImgHalves; }
 
 static void tcb_launch(int n, float* F, const __half* img, int K0, int kbo, int tj_off, int tcols, int* flag,
@@ -1435,8 +1604,9 @@ static void tcb_launch(int n, float* F, const __half* img, int K0, int kbo, int 
     const int ntr = (rem + (int)tc::kM - 1) / (int)tc::kM;
     if (tcols <= 0 || ntr <= 0) return;
     const int ntc = tj_off + tcols;
+    const int G2 = tcb_groups(rem);
     int ntiles = 0;
-    for (int tj = tj_off; tj < ntc; ++tj) ntiles += ntr - tj;
+    for (int tj = tj_off; tj < ntc; ++tj) ntiles += ntr - 2 * tj;     // row tiles 2 tj .. ntr - 1
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -1444,7 +1614,7 @@ static void tcb_launch(int n, float* F, const __half* img, int K0, int kbo, int 
         IGS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     }
     const int grid = std::max(1, std::min(ntiles, sms));
-    k_syrk_tcp<<<grid, 256, tcp_smem_bytes(), s>>>(n, F, img, K0, kbo, 2 * ntr, tj_off, ntc, ntr, ntiles, flag);
+    k_syrk_tcp<<<grid, kTcpThreads, tcp_smem_bytes(), s>>>(n, F, img, K0, kbo, G2, tj_off, ntc, ntr, ntiles, flag);
 }
 
 static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evP, cudaEvent_t evB,
@@ -1468,8 +1638,8 @@ static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, c
         }
         const int rem = n - K0 - kbo;
         if (rem <= 0) continue;
-        const int ntc = (rem + (int)kTN - 1) / (int)kTN;             // 128-column tiles
-        const int G2 = 2 * ((rem + (int)tc::kM - 1) / (int)tc::kM);
+        const int ntc = (rem + (int)kTN - 1) / (int)kTN;             // 256-column tiles
+        const int G2 = tcb_groups(rem);
         __half* img = reinterpret_cast<__half*>(p->d_timg) + (size_t)((K0 / kOB) & 1) * tcb_image_halves(n);
         k_split_panel<<<dim3(G2, (kbo + kKC - 1) / kKC), 256, 0, s0>>>(n, F, K0, kbo, K0 + kbo, G2, img);
         const int first = std::min(ntc, kOB / (int)kTN);             // the next outer block's column tiles
@@ -1624,19 +1794,28 @@ static void prepare_factor(igs_prob p, cudaStream_t s) {
         // the factor graph captures these pointers: allocate before capture, keep for the problem's life
         IGS_CUDA(cudaStreamSynchronize(s));
     }
-    if (!p->d_As64) p->d_As64 = (double*)dev_alloc(p, sizeof(double) * (size_t)n * n);
-    // MIXED tier: factor D As D with unit diagonal (D = diag(As_ii^-1/2)), so that
-    // every factor entry is at most 1 in magnitude (the tensor-core update's split)
-    const bool scaled = std::is_same<T, float>::value;
-    if (scaled) {
-        if (!p->d_dscale) p->d_dscale = (double*)dev_alloc(p, sizeof(double) * (size_t)n);
-        k_diag_scale<T><<<(n + 255) / 256, 256, 0, s>>>(n, (const T*)p->d_A, p->d_dscale);
+    if (!p->at_ready) {
+        if (!p->d_AT) p->d_AT = dev_alloc(p, sizeof(T) * (size_t)n * n);
+        k_transpose<T><<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, s>>>(n, (const T*)p->d_A, (T*)p->d_AT);
+        p->launches++;
+        p->at_ready = 1;
+    }
+    if (std::is_same<T, float>::value) {
+        // MIXED tier: factor D As D with unit diagonal (D = diag(As_ii^-1/2)), so that
+        // every factor entry is at most 1 in magnitude (the tensor-core update's
+        // FP16 split); the refinement residual reads A and A^T (no FP64 copy of As)
+        if (!p->d_dscale) p->d_dscale = (float*)dev_alloc(p, sizeof(float) * (size_t)n);
+        k_diag_scale<<<(n + 255) / 256, 256, 0, s>>>(n, (const float*)p->d_A, p->d_dscale);
+        k_symmetrize_lower_f<<<dim3((n + 1023) / 1024, n), 256, 0, s>>>(n, (const float*)p->d_A, (const float*)p->d_AT,
+                                                                         (float*)p->d_F, p->d_dscale);
+        p->launches += 2;
+    } else {
+        if (!p->d_As64) p->d_As64 = (double*)dev_alloc(p, sizeof(double) * (size_t)n * n);
+        constexpr int VN = Vec16<T>::N;
+        k_symmetrize<T><<<dim3((n + 256 * VN - 1) / (256 * VN), n), 256, 0, s>>>(
+            n, (const T*)p->d_A, (const T*)p->d_AT, (T*)p->d_F, p->d_As64);
         p->launches++;
     }
-    const int nst = (n + sym_tile<T>() - 1) / sym_tile<T>();
-    k_symmetrize<T><<<nst * (nst + 1) / 2, 256, 0, s>>>(n, (const T*)p->d_A, (T*)p->d_F, p->d_As64,
-                                                       scaled ? p->d_dscale : nullptr);
-    p->launches++;
     IGS_CUDA(cudaGetLastError());
     factor<T>(p, s);
     p->factored = 1;
@@ -1650,13 +1829,14 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
     T* d_x = (T*)dev_alloc(p, sizeof(T) * cnt);
     double* d_r = (double*)dev_alloc(p, sizeof(double) * cnt);
     double* d_norm = (double*)dev_alloc(p, sizeof(double) * 2 * nrhs);
+    float2* d_aff = std::is_same<T, float>::value ? (float2*)dev_alloc(p, sizeof(float2) * cnt) : nullptr;
     std::vector<double> hn(2 * nrhs);
     int it = 0;
     const double* src = d_beta;
     const double* scale = nullptr;
     IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s));
     for (;;) {
-        const double* dsc = std::is_same<T, float>::value ? p->d_dscale : nullptr;
+        const float* dsc = std::is_same<T, float>::value ? p->d_dscale : nullptr;
         k_cast_in<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, src, d_x, scale, n, dsc);
         if (std::is_same<T, float>::value && p->coop_ok) {
             launch_trsv_pk(n, (const float*)p->d_F, (const float*)p->d_diagLinv, (float*)d_x, nrhs, 1, p->d_tpub,
@@ -1673,8 +1853,11 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
             launch_trsv<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 0, s);
         }
         k_accum<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, d_x, d_alpha, scale, n, it == 0, dsc);
-        launch_resid(n, nrhs, p->d_As64, d_alpha, d_beta, d_r, d_norm, s);
-        p->launches += 6;
+        if (std::is_same<T, float>::value)
+            launch_resid_ff(n, nrhs, (const float*)p->d_A, (const float*)p->d_AT, d_alpha, d_aff, d_beta, d_r, d_norm, s);
+        else
+            launch_resid(n, nrhs, p->d_As64, d_alpha, d_beta, d_r, d_norm, s);
+        p->launches += std::is_same<T, float>::value ? 7 : 6;
         IGS_CUDA(cudaGetLastError());
         if (it == 0 && max_it > 1) {
             // an FP32 factor never meets the tolerance after one step: go on to the
@@ -1693,6 +1876,7 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
             dev_free(p, d_x);
             dev_free(p, d_r);
             dev_free(p, d_norm);
+            if (d_aff) dev_free(p, d_aff);
             throw Error(IGS_E_TIMEOUT, "triangular solve: a block waited past its budget");
         }
         ++it;
@@ -1710,6 +1894,7 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
     dev_free(p, d_x);
     dev_free(p, d_r);
     dev_free(p, d_norm);
+    if (d_aff) dev_free(p, d_aff);
     double worst = 0;
     for (int k = 0; k < nrhs; ++k) worst = std::max(worst, hn[2 * k + 1] > 0 ? std::sqrt(hn[2 * k] / hn[2 * k + 1]) : 0.0);
     if (worst > tol && max_it > 1) throw Error(IGS_E_NOT_CONVERGED, "iterative refinement did not reach 1e-10");
