@@ -1598,6 +1598,7 @@ constexpr int kBlockedMinN = 4096;
 static int tcb_groups(int n) { return 4 * ((n + (int)kTN - 1) / (int)kTN); }
 static size_t tcb_image_halves(int n) { return (size_t)(kOB / kKC) * 2 * tcb_groups(n) * kImgHalves; }
 
+constexpr int kTcpReserveSMs = 64;
 static void tcb_launch(int n, float* F, const __half* img, int K0, int kbo, int tj_off, int tcols, int* flag,
                        cudaStream_t s) {
     const int rem = n - K0 - kbo;
@@ -1613,7 +1614,11 @@ static void tcb_launch(int n, float* F, const __half* img, int K0, int kbo, int 
         IGS_CUDA(cudaGetDevice(&dev));
         IGS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     }
-    const int grid = std::max(1, std::min(ntiles, sms));
+    // a CTA of this kernel fills an SM's shared memory: the update of the columns
+    // beyond the next outer block (tj_off > 0, on the second stream) leaves
+    // kTcpReserveSMs SMs to the next outer block's panel chain, so the two overlap
+    const int avail = tj_off > 0 ? std::max(1, sms - kTcpReserveSMs) : sms;
+    const int grid = std::max(1, std::min(ntiles, avail));
     k_syrk_tcp<<<grid, kTcpThreads, tcp_smem_bytes(), s>>>(n, F, img, K0, kbo, G2, tj_off, ntc, ntr, ntiles, flag);
 }
 
