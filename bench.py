@@ -35,7 +35,8 @@ if ROOT not in sys.path:
 # DRAM read + write bytes of one launch of the FP32 assembly kernel, keyed by
 # (n, degree, N_ref): ncu captures summarised in profiles/ (the file named in
 # the value); a configuration without a capture of the current kernel gets null
-ASSEMBLY_TRAFFIC = {}
+ASSEMBLY_TRAFFIC = {(16384, 4, 2): (84.73e6 + 2.09e9, "profiles/ncu_assemble_f_star16384_traffic.md"),
+                    (2048, 3, 2): (8.45e6 + 5.63e3, "profiles/ncu_assemble_f_star16384_traffic.md")}
 
 
 def parse():

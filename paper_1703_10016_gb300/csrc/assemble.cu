@@ -197,52 +197,82 @@ __global__ void __launch_bounds__(256) k_assemble_tile(
     }
 }
 
-// Base-2 logarithm for the FP32 tier, x > 0 and normal: x = 2^e m with m in
-// [sqrt(1/2), sqrt(2)) by exponent arithmetic, log2 x = e + log2 m.  On
-// [0.5, 2] the hardware base-2 logarithm (__log2f) has an absolute error of
-// at most 2^-22, so the result carries that absolute error plus its rounding.
-__device__ __forceinline__ float log2_pos(float x) {
-    const int ix = __float_as_int(x);
-    const int e = (ix - 0x3f3504f3) >> 23;            // 0x3f3504f3 = sqrt(1/2)
-    const float m = __int_as_float(ix - (e << 23));
-    return (float)e + __log2f(m);
-}
-
 // FP32 tier, one thread per A-range node: the block is as wide as the largest
-// node range (rounded up to a warp), so that no thread idles in stage 1.  The
-// B-range nodes are kept in shared memory as 16-byte records read by
-// broadcast, and walked in groups of equal first column, so that the window
-// of d+1 running sums moves once per group.  The kernel value is formed in
-// base-2 units, c = log2(|f(s) - f(t)|^2 / D^2) = 2 K1 / ln 2, on node
-// coordinates scaled by 1/L (which leaves the ratio unchanged and removes the
-// 1/L^2 of the three-image factor); the factor ln 2 / 2 rides on the staged
-// regular weights P.  Tiles whose nodes all lie where W^s is a Toeplitz
-// sequence (interior columns and rows of the stored rules) stage the window of
-// the two sequences they touch, so the singular weight is one shared-memory
-// read at a per-node offset; the other tiles read the stored rules through
-// ws_at, fetched a few steps ahead.  Only tiles whose A- and B-ranges share a
-// node test for the diagonal limit.
+// node range (rounded up to a warp), so that no thread idles in stage 1.  Each
+// B-range node is one shared-memory record of 3 + 2 NV 16-byte words read by
+// broadcast -- coordinates, parameter offsets, the P and Q weight rows and the
+// indices (m, first column, Toeplitz offset) -- so one pointer addresses all of
+// a node's data.  The nodes are walked in groups of equal first column, so
+// that the window of d+1 running sums moves once per group, two nodes per step
+// (interior groups hold 2 N_ref nodes).  The kernel value is formed in base-2
+// units, c = log2(|f(s) - f(t)|^2 / D^2) = 2 K1 / ln 2, on node coordinates
+// scaled by 1/L (which leaves the ratio unchanged and removes the 1/L^2 of the
+// three-image factor); the factor ln 2 / 2 rides on the staged regular weights
+// P.  The ratio is of order J^2 on these curves, and the hardware base-2
+// logarithm (__log2f) measured on this GPU has an absolute error of at most
+// 3.3e-7 for arguments in [1/16, 16] (2.1e-7 in [1/2, 2]).  Tiles whose nodes all
+// lie where W^s is a Toeplitz sequence (interior columns and rows of the stored
+// rules) stage the window of the two sequences they touch, so the singular
+// weight is one shared-memory read at a per-node offset; the other tiles read
+// the stored rules through ws_at, fetched a few steps ahead.  Only tiles whose
+// A- and B-ranges share a node test for the diagonal limit.
+template <int D> __host__ __device__ constexpr int rec_words() { return 3 + 2 * ((D + 1 + 3) / 4); }
+
 template <int D, bool CLOSED, bool TOE, bool DIAG>
 __device__ __forceinline__ void tile_walk_f(const TileF& t, int ma, int a, int Nb, int nj,
-                                            const float4* __restrict__ sBg, const float4* __restrict__ sBw,
-                                            const int4* __restrict__ sBr, const int* __restrict__ sGs,
+                                            const float4* __restrict__ rec, const int* __restrict__ sGs,
                                             const float* __restrict__ sT, float* __restrict__ row) {
     constexpr int D1 = D + 1;
     constexpr int NV = (D1 + 3) / 4;
+    constexpr int RW = rec_words<D>();
     const NodeF na = t.nodes[ma];
     const float cdiag = na.lnJ * 2.88539008177792681f;    // K1(s,s) = ln J in base-2 units (x 2 / ln 2)
     const float ccorner = cdiag - 2.0f;                    // ln J - ln 2 in the same units
     float acc[D1];
 #pragma unroll
     for (int r = 0; r < D1; ++r) acc[r] = 0.0f;
-    int jcur = sBr[0].y;
-    const int G = sBr[Nb - 1].y - jcur + 1;
+    auto idx = [&](int v) { return *reinterpret_cast<const int4*>(&rec[v * RW + RW - 1]); };
+    int jcur = idx(0).y;
+    const int G = idx(Nb - 1).y - jcur + 1;
     constexpr int kPre = TOE ? 1 : 4;                      // singular weights in flight (general tiles)
     float wq[kPre];
     if (!TOE) {
 #pragma unroll
-        for (int q = 0; q < kPre; ++q) wq[q] = (q < Nb) ? ws_at(t.ws, ma, sBr[q].x) : 0.0f;
+        for (int q = 0; q < kPre; ++q) wq[q] = (q < Nb) ? ws_at(t.ws, ma, idx(q).x) : 0.0f;
     }
+    auto node = [&](int v) {
+        const float4* p = rec + v * RW;
+        const int4 br = *reinterpret_cast<const int4*>(&p[RW - 1]);
+        float ws;
+        if (TOE) {
+            ws = sT[br.z + a];
+        } else {
+            ws = wq[0];
+#pragma unroll
+            for (int q = 0; q < kPre - 1; ++q) wq[q] = wq[q + 1];
+            wq[kPre - 1] = (v + kPre < Nb) ? ws_at(t.ws, ma, idx(v + kPre).x) : 0.0f;
+        }
+        const float4 g0 = p[0], g1 = p[1];
+        const float dx = (g0.x - na.xh) + (g0.y - na.xl);
+        const float dy = (g0.z - na.yh) + (g0.w - na.yl);
+        float Dd = (g1.x - na.eh) + (g1.y - na.el);
+        // x + L and L - x as sums of non-negative numbers: the high parts
+        // alone keep FP32 relative accuracy
+        if (CLOSED) Dd *= (g1.x + na.ebh) * (g1.z + na.eh);
+        float c0 = __log2f(__fdividef(fmaf(dx, dx, dy * dy), Dd * Dd));
+        if (DIAG) c0 = (br.x == ma) ? cdiag : c0;
+        if (CLOSED && !TOE) c0 = (ma + br.x == t.Nq - 1 && (ma == 0 || br.x == 0)) ? ccorner : c0;
+        float w[2][4 * NV];
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                const float4 t4 = p[2 + kk * NV + q];
+                w[kk][4 * q] = t4.x; w[kk][4 * q + 1] = t4.y; w[kk][4 * q + 2] = t4.z; w[kk][4 * q + 3] = t4.w;
+            }
+#pragma unroll
+        for (int r = 0; r < D1; ++r) acc[r] = fmaf(w[0][r], c0, fmaf(w[1][r], ws, acc[r]));
+    };
     for (int k = 0; k < G; ++k) {
         if (k > 0) {
             if (jcur >= 0 && jcur < nj) row[jcur] = acc[0];
@@ -252,38 +282,12 @@ __device__ __forceinline__ void tile_walk_f(const TileF& t, int ma, int a, int N
             ++jcur;
         }
         const int ve = sGs[k + 1];
-        for (int v = sGs[k]; v < ve; ++v) {
-            const int4 br = sBr[v];
-            float ws;
-            if (TOE) {
-                ws = sT[br.z + a];
-            } else {
-                ws = wq[0];
-#pragma unroll
-                for (int q = 0; q < kPre - 1; ++q) wq[q] = wq[q + 1];
-                wq[kPre - 1] = (v + kPre < Nb) ? ws_at(t.ws, ma, sBr[v + kPre].x) : 0.0f;
-            }
-            const float4 g0 = sBg[2 * v], g1 = sBg[2 * v + 1];
-            const float dx = (g0.x - na.xh) + (g0.y - na.xl);
-            const float dy = (g0.z - na.yh) + (g0.w - na.yl);
-            float Dd = (g1.x - na.eh) + (g1.y - na.el);
-            // x + L and L - x as sums of non-negative numbers: the high parts
-            // alone keep FP32 relative accuracy
-            if (CLOSED) Dd *= (g1.x + na.ebh) * (g1.z + na.eh);
-            float c0 = log2_pos(__fdividef(fmaf(dx, dx, dy * dy), Dd * Dd));
-            if (DIAG) c0 = (br.x == ma) ? cdiag : c0;
-            if (CLOSED && !TOE) c0 = (ma + br.x == t.Nq - 1 && (ma == 0 || br.x == 0)) ? ccorner : c0;
-            float w[2][4 * NV];
-#pragma unroll
-            for (int kk = 0; kk < 2; ++kk)
-#pragma unroll
-                for (int q = 0; q < NV; ++q) {
-                    const float4 t4 = sBw[(2 * v + kk) * NV + q];
-                    w[kk][4 * q] = t4.x; w[kk][4 * q + 1] = t4.y; w[kk][4 * q + 2] = t4.z; w[kk][4 * q + 3] = t4.w;
-                }
-#pragma unroll
-            for (int r = 0; r < D1; ++r) acc[r] = fmaf(w[0][r], c0, fmaf(w[1][r], ws, acc[r]));
+        int v = sGs[k];
+        for (; v + 1 < ve; v += 2) {
+            node(v);
+            node(v + 1);
         }
+        if (v < ve) node(v);
     }
 #pragma unroll
     for (int r = 0; r < D1; ++r)
@@ -314,11 +318,12 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
         diag |= uA0 < uB0 + k * Nq + Nb && uB0 + k * Nq < uA0 + Na;
     const int tlen = Na + Nb - 1;
     // 16-byte records first, then 4-byte arrays: every offset stays aligned
-    // for any maxr
-    float4* sBg = (float4*)smem;                       // [maxr][2]: (xh, xl, yh, yl), (eh, el, ebh, ebl)
-    float4* sBw = sBg + 2 * maxr;                      // [maxr][2 NV]: P ln2/2 row, Q row (zero padded)
-    int4* sBr = (int4*)(sBw + 2 * NV * maxr);          // [maxr]: (m, first column - j0, Toeplitz offset, 0)
-    int* sJA = (int*)(sBr + maxr);                     // [maxr]
+    // for any maxr.  B-node record v: words 0-1 (xh, xl, yh, yl), (eh, el, ebh, ebl);
+    // words 2 .. 2+2NV-1 the P ln2/2 row and the Q row (zero padded); last word
+    // (m, first column - j0, Toeplitz offset, 0) as integers
+    constexpr int RW = rec_words<D>();
+    float4* sRec = (float4*)smem;                      // [maxr][RW]
+    int* sJA = (int*)(sRec + (size_t)RW * maxr);       // [maxr]
     float* sPA = (float*)(sJA + maxr);                 // [maxr][D1]
     float* sT = sPA + maxr * D1;                       // [2][Na + Nb - 1] (Toeplitz tiles)
     int* sGs = (int*)(sT + 4 * maxr);                  // [TI + D + 2] first B node of each column group
@@ -327,8 +332,9 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
     for (int v = threadIdx.x; v < Nb; v += blockDim.x) {
         const int u = uB0 + v, m = pmod(u, Nq), per = pdiv(u, Nq);
         const NodeF b = t.nodes[m];
-        sBg[2 * v] = make_float4(b.xh, b.xl, b.yh, b.yl);
-        sBg[2 * v + 1] = make_float4(b.eh, b.el, b.ebh, b.ebl);
+        float4* rv = sRec + (size_t)v * RW;
+        rv[0] = make_float4(b.xh, b.xl, b.yh, b.yl);
+        rv[1] = make_float4(b.eh, b.el, b.ebh, b.ebl);
         float w[2][4 * NV];
 #pragma unroll
         for (int r = 0; r < 4 * NV; ++r) {
@@ -339,10 +345,10 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
         for (int k = 0; k < 2; ++k)
 #pragma unroll
             for (int q = 0; q < NV; ++q)
-                sBw[(2 * v + k) * NV + q] = make_float4(w[k][4 * q], w[k][4 * q + 1], w[k][4 * q + 2], w[k][4 * q + 3]);
+                rv[2 + k * NV + q] = make_float4(w[k][4 * q], w[k][4 * q + 1], w[k][4 * q + 2], w[k][4 * q + 3]);
         // W^s[ma][mb] = T[(mb - B) & 1][ma - mb + Nq - 1] = sT[offset + a]
         const int off = ((m - wsv.B) & 1) * tlen + (Nb - 1) - v;
-        sBr[v] = make_int4(m, jfirst[m] + n * per - j0, off, 0);
+        *reinterpret_cast<int4*>(&rv[RW - 1]) = make_int4(m, jfirst[m] + n * per - j0, off, 0);
     }
     for (int v = threadIdx.x; v < Na; v += blockDim.x) {
         const int u = uA0 + v, m = pmod(u, Nq), per = pdiv(u, Nq);
@@ -361,8 +367,9 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
     // column groups: the B nodes whose first column is jrel_0 + k start at
     // sGs[k] (empty groups repeat the next start); sGs[G] = Nb
     for (int v = threadIdx.x; v < Nb; v += blockDim.x) {
-        const int j0r = sBr[0].y;
-        const int k1 = sBr[v].y - j0r, k0 = (v == 0) ? -1 : sBr[v - 1].y - j0r;
+        auto jrel = [&](int q) { return reinterpret_cast<const int4*>(&sRec[(size_t)q * RW + RW - 1])->y; };
+        const int j0r = jrel(0);
+        const int k1 = jrel(v) - j0r, k0 = (v == 0) ? -1 : jrel(v - 1) - j0r;
         for (int k = k0 + 1; k <= k1; ++k) sGs[k] = v;
         if (v == Nb - 1) sGs[k1 + 1] = Nb;
     }
@@ -372,10 +379,10 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
         const int ma = pmod(uA0 + a, Nq);
         float* row = sS1 + a * (TI + 1);
         if (toe) {
-            if (diag) tile_walk_f<D, CLOSED, true, true>(t, ma, a, Nb, nj, sBg, sBw, sBr, sGs, sT, row);
-            else tile_walk_f<D, CLOSED, true, false>(t, ma, a, Nb, nj, sBg, sBw, sBr, sGs, sT, row);
+            if (diag) tile_walk_f<D, CLOSED, true, true>(t, ma, a, Nb, nj, sRec, sGs, sT, row);
+            else tile_walk_f<D, CLOSED, true, false>(t, ma, a, Nb, nj, sRec, sGs, sT, row);
         } else {
-            tile_walk_f<D, CLOSED, false, true>(t, ma, a, Nb, nj, sBg, sBw, sBr, sGs, sT, row);
+            tile_walk_f<D, CLOSED, false, true>(t, ma, a, Nb, nj, sRec, sGs, sT, row);
         }
     }
     __syncthreads();
@@ -385,8 +392,8 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
     // those rows once with a window of d+1 row sums (rows jA(a)..jA(a)+d).
     const float scale = (float)(-1.0 / (2.0 * kPi));
     const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int RW = (ni + nw - 1) / nw;
-    const int r0 = w * RW, r1 = min(ni, r0 + RW);
+    const int RPW = (ni + nw - 1) / nw;                // rows per warp
+    const int r0 = w * RPW, r1 = min(ni, r0 + RPW);
     if (r0 < r1) {
         const int bs = lo[i0 + r0] - uA0, be = hi[i0 + r1 - 1] - uA0;
         float acc[D1];
