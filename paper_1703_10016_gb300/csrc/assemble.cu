@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256) k_assemble_tile(
 // scaled by 1/L (which leaves the ratio unchanged and removes the 1/L^2 of the
 // three-image factor); the factor ln 2 / 2 rides on the staged regular weights
 // P.  The ratio is of order J^2 on these curves, and the hardware base-2
-// logarithm (__log2f) measured on this GPU has an absolute error of at most
+// logarithm (lg2.approx) measured on this GPU has an absolute error of at most
 // 3.3e-7 for arguments in [1/16, 16] (2.1e-7 in [1/2, 2]).  Tiles whose nodes all
 // lie where W^s is a Toeplitz sequence (interior columns and rows of the stored
 // rules) stage the window of the two sequences they touch, so the singular
@@ -259,7 +259,7 @@ __device__ __forceinline__ void tile_walk_f(const TileF& t, int ma, int a, int N
         // x + L and L - x as sums of non-negative numbers: the high parts
         // alone keep FP32 relative accuracy
         if (CLOSED) Dd *= (g1.x + na.ebh) * (g1.z + na.eh);
-        float c0 = __log2f(__fdividef(fmaf(dx, dx, dy * dy), Dd * Dd));
+        float c0 = lg2_ftz(div_ftz(fmaf(dx, dx, dy * dy), Dd * Dd));
         if (DIAG) c0 = (br.x == ma) ? cdiag : c0;
         if (CLOSED && !TOE) c0 = (ma + br.x == t.Nq - 1 && (ma == 0 || br.x == 0)) ? ccorner : c0;
         float w[2][4 * NV];

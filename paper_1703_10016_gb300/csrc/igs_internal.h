@@ -168,6 +168,25 @@ __host__ __device__ __forceinline__ T ws_at(const WsView<T>& v, int ma, int mb) 
     if (ma >= v.Nq - v.R) return v.row[(size_t)(ma - v.Nq + 2 * v.R) * v.Nq + mb];
     return v.toe[(size_t)((mb - v.B) & 1) * (2 * (size_t)v.Nq - 1) + (ma - mb + v.Nq - 1)];
 }
+
+#ifdef __CUDACC__
+// The PTX approximate base-2 logarithm and quotient with subnormal inputs and
+// results flushed to zero: one special-function instruction (and one multiply
+// for the quotient), without the rescaling a subnormal-preserving form adds.
+// Every argument these kernels pass is a normal number (squared distances and
+// parameter differences of distinct nodes), where both agree with the
+// subnormal-preserving forms bit for bit.
+__device__ __forceinline__ float lg2_ftz(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float div_ftz(float x, float y) {
+    float r;
+    asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(y));
+    return r;
+}
+#endif
 }  // namespace igs
 
 namespace igs {

@@ -49,22 +49,23 @@ __device__ __forceinline__ float kb32_pair(float gxh, float gxl, float gyh, floa
     const float dy = __fadd_rn(__fsub_rn(gyh, yh), __fsub_rn(gyl, yl));
     const float num = __fmaf_rn(dy, b, __fmul_rn(dx, a));
     const float r2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
-    return __fdividef(num, r2);
+    return div_ftz(num, r2);
 }
 
 // MIXED far field: partial sums over Gauss slice blockIdx.y, FP32, every pair
 // (the near pairs are replaced by k_double_layer_near).  Gauss data in shared
 // memory as 16-byte coordinate records and 8-byte (a, b) records.  A block
-// holds kFarNodes nodes: thread (j, p), j < kFarLanes, p < kFarParts, keeps
-// the float-float coordinates of the kFarNN nodes j + kFarLanes k in
+// holds 32 NN nodes: thread (j, p), j < kFarLanes, p < kFarParts, keeps
+// the float-float coordinates of the NN nodes j + kFarLanes k in
 // registers and sums the chunk's Gauss points q = p (mod kFarParts) for all of
-// them, so one shared-memory read of a Gauss point serves kFarNN pairs (one
+// them, so one shared-memory read of a Gauss point serves NN pairs (one
 // warp = 32 node groups of one part: every read is a broadcast).  The parts
 // are added in a fixed order at the end.
-constexpr int kFarLanes = 32, kFarParts = 8, kFarNN = 4;
-constexpr int kFarNodes = kFarLanes * kFarNN;
+// (NN = 4; small problems take NN = 2, which doubles the grid: a node block of
+// 64 instead of 128 nodes keeps every SM busy when N_quad is a few thousand)
+constexpr int kFarLanes = 32, kFarParts = 8;
 
-template <int NR>
+template <int NR, int kFarNN>
 __global__ void __launch_bounds__(kFarLanes * kFarParts) k_double_layer_f(int Nq, int Ng, const double* __restrict__ geo,
                                                                           const double* __restrict__ rgeo,
                                                                           const double* __restrict__ rw,
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(kFarLanes * kFarParts) k_double_layer_f(int Nq
     __shared__ float4 sg[kRhsChunk];
     __shared__ float2 sab[kRhsChunk];
     __shared__ float su[NR][kRhsChunk];
+    constexpr int kFarNodes = kFarLanes * kFarNN;
     __shared__ float red[kFarParts][NR][kFarNodes];
     const int lane = threadIdx.x % kFarLanes, prt = threadIdx.x / kFarLanes;
     const int m0 = blockIdx.x * kFarNodes + lane;
@@ -318,9 +320,15 @@ int rhs_slots(const igs_prob p) {
 template <int NR>
 static void launch_far(igs_prob p, const double* d_uD, int ldu, double* part, cudaStream_t s) {
     const Plan& P = p->plan;
-    if (p->precision == IGS_MIXED)
-        k_double_layer_f<NR><<<dim3((P.Nq + kFarNodes - 1) / kFarNodes, kSplit), kFarLanes * kFarParts, 0, s>>>(
-            P.Nq, p->Ng, p->d_geo, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, part);
+    if (p->precision == IGS_MIXED) {
+        // four nodes per thread, or two when that would leave SMs without a block
+        if ((P.Nq + 127) / 128 * kSplit >= 4 * 152)
+            k_double_layer_f<NR, 4><<<dim3((P.Nq + 127) / 128, kSplit), kFarLanes * kFarParts, 0, s>>>(
+                P.Nq, p->Ng, p->d_geo, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, part);
+        else
+            k_double_layer_f<NR, 2><<<dim3((P.Nq + 63) / 64, kSplit), kFarLanes * kFarParts, 0, s>>>(
+                P.Nq, p->Ng, p->d_geo, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, part);
+    }
     else
         k_double_layer_d<NR><<<dim3((P.Nq + 255) / 256, kSplit), 256, 0, s>>>(P.Nq, p->Ng, p->d_geo, p->d_rhs_geo,
                                                                             p->d_rhs_w, d_uD, ldu, P.Nq, part);

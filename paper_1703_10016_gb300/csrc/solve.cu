@@ -1499,20 +1499,43 @@ __global__ void __launch_bounds__(kTcpThreads, 1) k_syrk_tcp(int n, float* __res
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(2 * kTN));
 }
 
-// Launch with programmatic stream serialisation (see pdl_wait).
+// The factorisation's critical chain (panels, the next column block's or outer
+// block's update, the operand split) launches at the device's highest
+// scheduling priority: when SM resources free up, its CTAs go before those of
+// concurrent work (the right-hand side of igs_solve_data, the update of the
+// columns beyond the next outer block), which has the default priority.
+static int chain_priority() {
+    static int prio = 1;
+    if (prio == 1) {
+        int least = 0, greatest = 0;
+        IGS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        prio = greatest;
+    }
+    return prio;
+}
+
+// Launch at the chain priority, with programmatic stream serialisation if pdl
+// (see pdl_wait).
 template <typename... KArgs, typename... Args>
-static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+static void launch_chain(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                         Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = chain_priority();
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 2 : 1;
     IGS_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+}
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    launch_chain(true, kern, grid, block, smem, s, args...);
 }
 
 template <typename T>
@@ -1619,7 +1642,11 @@ static void tcb_launch(int n, float* F, const __half* img, int K0, int kbo, int 
     // kTcpReserveSMs SMs to the next outer block's panel chain, so the two overlap
     const int avail = tj_off > 0 ? std::max(1, sms - kTcpReserveSMs) : sms;
     const int grid = std::max(1, std::min(ntiles, avail));
-    k_syrk_tcp<<<grid, kTcpThreads, tcp_smem_bytes(), s>>>(n, F, img, K0, kbo, G2, tj_off, ntc, ntr, ntiles, flag);
+    if (tj_off == 0)        // the next outer block's columns: on the chain
+        launch_chain(false, k_syrk_tcp, dim3(grid), dim3(kTcpThreads), tcp_smem_bytes(), s, n, F, img, K0, kbo, G2,
+                     tj_off, ntc, ntr, ntiles, flag);
+    else
+        k_syrk_tcp<<<grid, kTcpThreads, tcp_smem_bytes(), s>>>(n, F, img, K0, kbo, G2, tj_off, ntc, ntr, ntiles, flag);
 }
 
 static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evP, cudaEvent_t evB,
@@ -1646,7 +1673,8 @@ static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, c
         const int ntc = (rem + (int)kTN - 1) / (int)kTN;             // 256-column tiles
         const int G2 = tcb_groups(rem);
         __half* img = reinterpret_cast<__half*>(p->d_timg) + (size_t)((K0 / kOB) & 1) * tcb_image_halves(n);
-        k_split_panel<<<dim3(G2, (kbo + kKC - 1) / kKC), 256, 0, s0>>>(n, F, K0, kbo, K0 + kbo, G2, img);
+        launch_chain(false, k_split_panel, dim3(G2, (kbo + kKC - 1) / kKC), dim3(256), 0, s0, n, (const float*)F, K0, kbo,
+                     K0 + kbo, G2, img);
         const int first = std::min(ntc, kOB / (int)kTN);             // the next outer block's column tiles
         if (ntc > first) IGS_CUDA(cudaEventRecord(evP, s0));
         if (pending) {
