@@ -81,6 +81,8 @@ typedef struct igs_info {
     int32_t closed;     /* 1 for a closed curve (interior problem), 0 for an open arc     */
     int32_t precision;  /* IGS_FP64 or IGS_MIXED                                          */
     int32_t rules_ready, assembled, factored;
+    int32_t rhs_slots;  /* scratch of the double-layer sum per data set, in units of     */
+                        /* n_quad doubles (igs_build_rhs_noalloc limit); 0: open arc      */
     int64_t device_bytes; /* device memory currently held by the problem                  */
 } igs_info;
 
@@ -192,10 +194,12 @@ int igs_build_rhs(igs_prob prob, const double* uD, int nrhs, double* beta_out, i
  * allocating library routine.
  *   uD:       DEVICE, nrhs x n_rhs_pts (layout of igs_build_rhs)
  *   beta_out: DEVICE, nrhs x n, written (the problem's own beta is not changed)
- * Limits: 1 <= nrhs <= 8 and slots * n_quad * nrhs <= 2097152 doubles (else
- * INVALID_ARG), with slots = 9 for a MIXED closed curve, 8 for an FP64 closed
- * curve and 0 for an open arc (no double-layer term, so no scratch and no
- * size limit beyond nrhs).
+ * Limits: 1 <= nrhs <= 8 and rhs_slots * n_quad * nrhs <= 2097152 doubles
+ * (else INVALID_ARG), with rhs_slots from igs_problem_info: 8 for an FP64
+ * closed curve (partial sums of 8 Gauss slices), 1 + ceil(S / n_quad) for a
+ * MIXED closed curve (the potentials, then S doubles of treecode moments and
+ * FP32 data products; S is about 8 n_quad), 0 for an open arc (no
+ * double-layer term, so no scratch and no size limit beyond nrhs).
  * Preconditions: the rules, the node geometry and the rhs points exist (call
  * igs_assemble and igs_rhs_points first), else STATE.  The work is queued on
  * the context stream and not waited for.  The first call on a device looks up

@@ -279,7 +279,7 @@ int igs_destroy_problem(igs_prob p) {
                      p->d_WsT32, p->d_WsRow, p->d_WsRow32, p->d_WsToe, p->d_WsToe32,
                      p->d_flag, p->d_geo, p->d_nodes,
                      p->d_P, p->d_Q, p->d_A, p->d_AT, p->d_F, p->d_As64, p->d_dscale, p->d_diagL, p->d_diagLinv, p->d_tflags, p->d_tpub, p->d_timg,
-                     p->d_beta, p->d_rhs_geo, p->d_rhs_w, p->d_rhs_t};
+                     p->d_beta, p->d_rhs_geo, p->d_rhs_w, p->d_rhs_t, p->d_tree};
     if (p->aux_stream) {
         cudaStreamSynchronize(p->aux_stream);
         cudaStreamDestroy(p->aux_stream);
@@ -308,7 +308,10 @@ int igs_set_geometry(igs_prob p, igs_geom g) {
         p->assembled = 0;
         p->factored = 0;
         p->rhs_n = 0;
-        if (p->d_rhs_geo) geometry_eval(g, p->d_rhs_t, p->Ng, p->d_rhs_geo, g->ctx->stream);
+        if (p->d_rhs_geo) {
+            geometry_eval(g, p->d_rhs_t, p->Ng, p->d_rhs_geo, g->ctx->stream);
+            rhs_tree_geometry(p, g->ctx->stream);
+        }
     }
     API_END
 }
@@ -321,7 +324,7 @@ int igs_problem_info(igs_prob p, igs_info* out) {
     out->n = P.n; out->degree = P.d; out->n_elems = P.Nh; out->n_ref = P.Nref; out->n_quad = P.Nq;
     out->n_exact = P.NE; out->n_rhs_pts = P.Nq + P.M * kGaussRhs; out->closed = P.closed;
     out->precision = p->precision; out->rules_ready = p->rules_ready; out->assembled = p->assembled;
-    out->factored = p->factored; out->device_bytes = p->bytes;
+    out->factored = p->factored; out->rhs_slots = rhs_slots(p); out->device_bytes = p->bytes;
     API_END
 }
 

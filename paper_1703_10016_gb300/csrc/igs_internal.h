@@ -15,6 +15,7 @@ constexpr int kMaxDegree = 5;
 constexpr int kMaxNref = 4;
 constexpr int kMaxGeomDegree = 7;
 constexpr int kGaussRhs = 8;          // Gauss points per refined element for the b2 inner rule
+constexpr int kTreeMaxLevels = 30;    // levels of the double-layer treecode (MIXED tier)
 constexpr double kPi = 3.14159265358979323846;
 
 // ------------------------------------------------------------------ errors
@@ -148,6 +149,11 @@ struct igs_prob_s {
     double* d_rhs_w = nullptr;    // [Ng] Gauss weights
     double* d_rhs_t = nullptr;    // [Ng] Gauss abscissae
     int Ng = 0;
+    // treecode of the double-layer sum (MIXED tier, closed curves): clusters of
+    // the rhs Gauss points, level 0 = leaves; geometry in one buffer
+    int tree_L = 0, tree_C = 0;
+    int tree_off[igs::kTreeMaxLevels] = {}, tree_cnt[igs::kTreeMaxLevels] = {};
+    void* d_tree = nullptr;
 };
 
 namespace igs {
@@ -206,9 +212,10 @@ void geometry_eval(igs_geom g, const double* d_t, int count, double* d_out, cuda
 void geometry_nodes(igs_prob p);
 void assemble_matrix(igs_prob p);
 void rhs_prepare(igs_prob p);
+void rhs_tree_geometry(igs_prob p, cudaStream_t s);   // treecode clusters after a geometry change
 void rhs_build(igs_prob p, const double* d_uD, int nrhs);
 void rhs_build_noalloc(igs_prob p, const double* d_uD, int nrhs, double* d_beta);
-int rhs_slots(const igs_prob p);   // partial-sum slots (each nrhs x N_quad doubles) of the node potentials
+int rhs_slots(const igs_prob p);   // scratch slots (each nrhs x N_quad doubles) of the node potentials
 void rhs_node_potentials(igs_prob p, const double* d_uD, int nrhs, double* scratch, const double** vsum, int* np,
                          cudaStream_t s);
 void rhs_compute(igs_prob p, const double* d_uD, int nrhs, double* d_beta, double* scratch, cudaStream_t s);

@@ -6,16 +6,15 @@
 // interior problem (eq. seconda_BIE), beta = b1 for an open arc (eq. prima_BIE).
 //
 // The double-layer potentials v_k(eta_m) = sum_g w_g Kbar(eta_m, t_g) u_k(t_g) are
-// an N_quad x N_GQ kernel sum.  The Gauss range is split in kSplit slices, one
-// grid row each, so that every node has kSplit partial sums (reduced in a fixed
-// order, by k_double_layer_near in the MIXED tier and by k_beta in the FP64
-// tier: results do not depend on scheduling).  MIXED tier: FP32 with
-// float-float coordinate differences for every pair.  At the Gauss points of
-// the node's refined element and its two neighbours the numerator
-// (f(t)-f(s)).n(t) is second-order small and the FP32 value is poor, so
-// k_double_layer_near recomputes those pairs in FP64 and, in one more partial
-// slot, replaces their FP32 contributions (reproduced bit for bit by the same
-// FP32 operations, kb32_pair) by the FP64 ones.  FP64 tier: every pair in FP64.
+// an N_quad x N_GQ kernel sum.  FP64 tier: every pair in FP64; the Gauss range
+// is split in kSplit slices, one grid row each, so that every node has kSplit
+// partial sums, added in a fixed order by k_beta.  MIXED tier: the same sum by
+// a treecode (multipole moments of clusters of Gauss points, FP32 with
+// float-float coordinate differences, truncation below the FP32 rounding),
+// except at the Gauss points of the node's refined element and its two
+// neighbours, where the numerator (f(t)-f(s)).n(t) is second-order small and
+// k_double_layer_near adds the pairs in FP64.  Every sum runs in a fixed order:
+// results do not depend on scheduling.
 #include <mutex>
 
 #include "igs_internal.h"
@@ -52,89 +51,243 @@ __device__ __forceinline__ float kb32_pair(float gxh, float gxl, float gyh, floa
     return div_ftz(num, r2);
 }
 
-// MIXED far field: partial sums over Gauss slice blockIdx.y, FP32, every pair
-// (the near pairs are replaced by k_double_layer_near).  Gauss data in shared
-// memory as 16-byte coordinate records and 8-byte (a, b) records.  A block
-// holds 32 NN nodes: thread (j, p), j < kFarLanes, p < kFarParts, keeps
-// the float-float coordinates of the NN nodes j + kFarLanes k in
-// registers and sums the chunk's Gauss points q = p (mod kFarParts) for all of
-// them, so one shared-memory read of a Gauss point serves NN pairs (one
-// warp = 32 node groups of one part: every read is a broadcast).  The parts
-// are added in a fixed order at the end.
-// (NN = 4; small problems take NN = 2, which doubles the grid: a node block of
-// 64 instead of 128 nodes keeps every SM busy when N_quad is a few thousand)
-constexpr int kFarLanes = 32, kFarParts = 8;
+// MIXED tier: the double-layer sum by a treecode over the Gauss points.  In
+// complex notation, with z = f(t) - f(s) and nu(t) = f2'(t) - i f1'(t),
+// Kbar(s,t) = Re(nu / z), so v_k(eta) = Re sum_g c_g / (y_g - x) with charges
+// c_g = w_g u_k(t_g) nu(t_g), y_g = f(t_g) and x = f(eta): a Cauchy sum.  The
+// Gauss points, in parameter order, are grouped in leaves of kLeaf points and
+// a binary tree of leaves; each cluster holds the scaled moments
+//   M_j = sum_{g in cluster} c_g ((y_g - z_c) / rho)^j,  j < kTerms,
+// about the centre z_c of its bounding box (rho = half its diagonal; the
+// scaling keeps every moment within sum |c_g| in FP32).  For
+// |x - z_c| >= rho / theta the cluster's share of the sum is
+//   -(1 / (x - z_c)) sum_j M_j (rho / (x - z_c))^j,
+// with a truncation error below theta^kTerms / (1 - theta) times
+// sum |c_g| / |x - z_c| (theta = 1/2, kTerms = 28: 7.5e-9, under the FP32
+// rounding of the sum itself).  The moments of a leaf are summed from its
+// points, those of a parent by the binomial shift of its two children's:
+// M^P_j = sum_l C(j, l) (rho_c / rho_P)^l M^c_l ((z_c - z_P) / rho_P)^(j - l),
+// whose terms are bounded by 2^j sum |c_g| and enter the sum with weight at
+// most theta^j = 2^-j.
+// A warp takes 32 consecutive nodes and walks the tree from the root with one
+// stack: a cluster is expanded for all 32 when every node is separated from
+// it and none has its own or a neighbouring element in it, else its children
+// are visited; leaves that are reached are summed point by point in FP32 with
+// float-float coordinate differences (kb32_pair).  Every node thus gets every
+// Gauss point once, except those of its element and its two neighbours,
+// which k_double_layer_near adds in FP64.  All sums run in a fixed order.
+constexpr int kLeaf = 32;
+constexpr int kTerms = 28;
+constexpr double kTheta = 0.5;
 
-template <int NR, int kFarNN>
-__global__ void __launch_bounds__(kFarLanes * kFarParts) k_double_layer_f(int Nq, int Ng, const double* __restrict__ geo,
-                                                                          const double* __restrict__ rgeo,
-                                                                          const double* __restrict__ rw,
-                                                                          const double* __restrict__ uD, int ldu, int off,
-                                                                          double* __restrict__ part) {
-    __shared__ float4 sg[kRhsChunk];
-    __shared__ float2 sab[kRhsChunk];
-    __shared__ float su[NR][kRhsChunk];
-    constexpr int kFarNodes = kFarLanes * kFarNN;
-    __shared__ float red[kFarParts][NR][kFarNodes];
-    const int lane = threadIdx.x % kFarLanes, prt = threadIdx.x / kFarLanes;
-    const int m0 = blockIdx.x * kFarNodes + lane;
-    float xh[kFarNN], xl[kFarNN], yh[kFarNN], yl[kFarNN];
-#pragma unroll
-    for (int k = 0; k < kFarNN; ++k) {
-        const int m = min(m0 + kFarLanes * k, Nq - 1);
-        split2(geo[m], xh[k], xl[k]);
-        split2(geo[Nq + m], yh[k], yl[k]);
+struct TreeArgs {
+    int L, C;                          // levels (leaves = level 0), clusters
+    int off[kTreeMaxLevels];           // first cluster of each level
+    int cnt[kTreeMaxLevels];           // clusters per level
+    const float4* ctr;                 // [C] centre, float-float (xh, xl, yh, yl)
+    const float* thr;                  // [C] (rho / theta)^2
+    const float* rs;                   // [C] moment scale rho (positive)
+    const int2* erng;                  // [C] first and last refined element
+    const float4* src;                 // [Ng] Gauss point, float-float (xh, xl, yh, yl)
+    const float2* ab;                  // [Ng] (f2', -f1') at the Gauss point
+};
+
+__device__ __forceinline__ void tree_finish(const double* bx, float4& ctr, float& thr, float& rs) {
+    const double cx = 0.5 * (bx[0] + bx[1]), cy = 0.5 * (bx[2] + bx[3]);
+    const double hx = bx[1] - bx[0], hy = bx[3] - bx[2];
+    const double rho2 = 0.25 * (hx * hx + hy * hy);
+    float a, b, c, d;
+    split2(cx, a, b);
+    split2(cy, c, d);
+    ctr = make_float4(a, b, c, d);
+    // a small margin for the FP32 distance test; a positive floor for one-point clusters
+    thr = (float)fmax(rho2 / (kTheta * kTheta) * (1.0 + 1e-4), 1e-30);
+    rs = (float)fmax(sqrt(rho2), 1e-30);
+}
+
+// Leaves: bounding box, centre, threshold, element range, and the FP32 images
+// of the Gauss points (coordinates as float-float, normal direction).
+__global__ void k_tree_leaves(int Ng, int nleaf, const double* __restrict__ rgeo, double* __restrict__ box,
+                              float4* __restrict__ ctr, float* __restrict__ thr, float* __restrict__ rs,
+                              int2* __restrict__ erng, float4* __restrict__ src, float2* __restrict__ ab) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nleaf) return;
+    const int g0 = c * kLeaf, g1 = min(Ng, g0 + kLeaf);
+    double bx[4] = {rgeo[g0], rgeo[g0], rgeo[Ng + g0], rgeo[Ng + g0]};
+    for (int g = g0; g < g1; ++g) {
+        const double x = rgeo[g], y = rgeo[Ng + g];
+        bx[0] = fmin(bx[0], x); bx[1] = fmax(bx[1], x);
+        bx[2] = fmin(bx[2], y); bx[3] = fmax(bx[3], y);
+        float4 q;
+        split2(x, q.x, q.y);
+        split2(y, q.z, q.w);
+        src[g] = q;
+        ab[g] = make_float2((float)rgeo[3 * Ng + g], (float)(-rgeo[2 * Ng + g]));
     }
-    float acc[kFarNN][NR];
+    for (int k = 0; k < 4; ++k) box[4 * (size_t)c + k] = bx[k];
+    tree_finish(bx, ctr[c], thr[c], rs[c]);
+    erng[c] = make_int2(g0 / kGaussRhs, (g1 - 1) / kGaussRhs);
+}
+
+// One level up: a parent's box is the union of its children's.
+__global__ void k_tree_up(int offc, int cntc, int offp, int cntp, double* __restrict__ box, float4* __restrict__ ctr,
+                          float* __restrict__ thr, float* __restrict__ rs, int2* __restrict__ erng) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cntp) return;
+    const int c0 = offc + 2 * i, c1 = (2 * i + 1 < cntc) ? c0 + 1 : c0;
+    double bx[4];
+    bx[0] = fmin(box[4 * (size_t)c0], box[4 * (size_t)c1]);
+    bx[1] = fmax(box[4 * (size_t)c0 + 1], box[4 * (size_t)c1 + 1]);
+    bx[2] = fmin(box[4 * (size_t)c0 + 2], box[4 * (size_t)c1 + 2]);
+    bx[3] = fmax(box[4 * (size_t)c0 + 3], box[4 * (size_t)c1 + 3]);
+    const int P = offp + i;
+    for (int k = 0; k < 4; ++k) box[4 * (size_t)P + k] = bx[k];
+    tree_finish(bx, ctr[P], thr[P], rs[P]);
+    erng[P] = make_int2(erng[c0].x, erng[c1].y);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Leaf moments for data set r (thread per (leaf, r)); also the FP32 products
+// w_g u_r(t_g) the direct sums use.
+__global__ void k_tree_leaf_moments(int Ng, int nleaf, int nrhs, int C, const double* __restrict__ rgeo,
+                                    const double* __restrict__ rw, const double* __restrict__ uD, int ldu, int off,
+                                    const float4* __restrict__ ctr, const float* __restrict__ rs,
+                                    const float2* __restrict__ ab, float2* __restrict__ mom, float* __restrict__ wu) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = idx % nleaf, r = idx / nleaf;
+    if (r >= nrhs) return;
+    const float4 z = ctr[c];
+    const double zx = (double)z.x + (double)z.y, zy = (double)z.z + (double)z.w;
+    const double ir = 1.0 / (double)rs[c];
+    float2 M[kTerms];
 #pragma unroll
-    for (int k = 0; k < kFarNN; ++k)
+    for (int j = 0; j < kTerms; ++j) M[j] = make_float2(0.f, 0.f);
+    const int g0 = c * kLeaf, g1 = min(Ng, g0 + kLeaf);
+    for (int g = g0; g < g1; ++g) {
+        const float w = (float)(rw[g] * uD[(size_t)r * ldu + off + g]);
+        wu[(size_t)r * Ng + g] = w;
+        const float2 nu = ab[g];
+        const float2 t = make_float2((float)((rgeo[g] - zx) * ir), (float)((rgeo[Ng + g] - zy) * ir));
+        float2 pw = make_float2(w * nu.x, w * nu.y);
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[k][r] = 0.f;
-    const int per = (Ng + kSplit - 1) / kSplit;
-    const int g_lo = blockIdx.y * per, g_hi = min(Ng, g_lo + per);
-    for (int g0 = g_lo; g0 < g_hi; g0 += kRhsChunk) {
-        const int cn = min(kRhsChunk, g_hi - g0);
-        __syncthreads();
-        for (int q = threadIdx.x; q < cn; q += blockDim.x) {
-            const int g = g0 + q;
-            float4 c;
-            split2(rgeo[g], c.x, c.y);
-            split2(rgeo[Ng + g], c.z, c.w);
-            sg[q] = c;
-            sab[q] = make_float2((float)rgeo[3 * Ng + g], (float)(-rgeo[2 * Ng + g]));   // f2'(t), -f1'(t)
-            const double w = rw[g];
-#pragma unroll
-            for (int r = 0; r < NR; ++r) su[r][q] = (float)(w * uD[(size_t)r * ldu + off + g]);
+        for (int j = 0; j < kTerms; ++j) {
+            M[j].x += pw.x;
+            M[j].y += pw.y;
+            pw = cmul(pw, t);
         }
-        __syncthreads();
-#pragma unroll 2
-        for (int q = prt; q < cn; q += kFarParts) {
-            const float4 c = sg[q];
-            const float2 ab = sab[q];
-            float u[NR];
+    }
+    float2* out = mom + ((size_t)r * C + c) * kTerms;
 #pragma unroll
-            for (int r = 0; r < NR; ++r) u[r] = su[r][q];
+    for (int j = 0; j < kTerms; ++j) out[j] = M[j];
+}
+
+// Parent moments from the children's (thread per (parent, j, r)), the sum
+// over l by Horner's rule in tau = (z_c - z_P) / rho_P, l ascending.
+__global__ void k_tree_shift(int offc, int cntc, int offp, int cntp, int nrhs, int C, const float4* __restrict__ ctr,
+                             const float* __restrict__ rs, float2* __restrict__ mom) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = idx % kTerms, i = (idx / kTerms) % cntp, r = idx / (kTerms * cntp);
+    if (r >= nrhs) return;
+    const int P = offp + i;
+    const float4 zp = ctr[P];
+    const double px = (double)zp.x + (double)zp.y, py = (double)zp.z + (double)zp.w;
+    const double irp = 1.0 / (double)rs[P];
+    float2 acc = make_float2(0.f, 0.f);
+    for (int ch = 2 * i; ch <= 2 * i + 1 && ch < cntc; ++ch) {
+        const int c = offc + ch;
+        const float4 zc = ctr[c];
+        const float2 tau = make_float2((float)(((double)zc.x + (double)zc.y - px) * irp),
+                                       (float)(((double)zc.z + (double)zc.w - py) * irp));
+        const float sig = (float)((double)rs[c] * irp);
+        const float2* Mc = mom + ((size_t)r * C + c) * kTerms;
+        float2 sacc = make_float2(0.f, 0.f);
+        float b = 1.f, sl = 1.f;                         // C(j, l), sig^l
+        for (int l = 0; l <= j; ++l) {
+            const float2 m = Mc[l];
+            const float f = b * sl;
+            sacc = cmul(sacc, tau);
+            sacc.x = fmaf(f, m.x, sacc.x);
+            sacc.y = fmaf(f, m.y, sacc.y);
+            sl *= sig;
+            b = b * (float)(j - l) / (float)(l + 1);
+        }
+        acc.x += sacc.x;
+        acc.y += sacc.y;
+    }
+    mom[((size_t)r * C + P) * kTerms + j] = acc;
+}
+
+// The treecode sum at the nodes (warp per 32 consecutive nodes): out[r][m] =
+// the FP32 double-layer potential of data set r at eta_m without the Gauss
+// points of the node's element and its two neighbours.
+template <int NR>
+__global__ void __launch_bounds__(128) k_tree_eval(int Nq, int Ng, int M, const double* __restrict__ geo,
+                                                   const int* __restrict__ fspan, const TreeArgs T,
+                                                   const float2* __restrict__ mom, const float* __restrict__ wu,
+                                                   double* __restrict__ out) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = m < Nq;
+    const int mm = live ? m : Nq - 1;
+    float xh, xl, yh, yl;
+    split2(geo[mm], xh, xl);
+    split2(geo[Nq + mm], yh, yl);
+    const int em = fspan[mm];
+    const int ea = em == 0 ? M - 1 : em - 1, eb = em == M - 1 ? 0 : em + 1;
+    float acc[NR];
 #pragma unroll
-            for (int k = 0; k < kFarNN; ++k) {
-                const float kb = kb32_pair(c.x, c.y, c.z, c.w, ab.x, ab.y, xh[k], xl[k], yh[k], yl[k]);
+    for (int r = 0; r < NR; ++r) acc[r] = 0.f;
+    int stk[2 * kTreeMaxLevels + 2];
+    int sp = 0;
+    stk[sp++] = (T.L - 1) << 24;
+    while (sp > 0) {
+        const int e = stk[--sp];
+        const int lvl = e >> 24, i = e & 0xffffff;
+        const int id = T.off[lvl] + i;
+        const float4 z = T.ctr[id];
+        const int2 er = T.erng[id];
+        const float dx = (xh - z.x) + (xl - z.y), dy = (yh - z.z) + (yl - z.w);
+        const bool adj = (em >= er.x && em <= er.y) || (ea >= er.x && ea <= er.y) || (eb >= er.x && eb <= er.y);
+        const float d2 = fmaf(dx, dx, dy * dy);
+        if (__all_sync(0xffffffffu, !adj && d2 >= T.thr[id])) {
+            // -Re (1/d) sum_j M_j (rho/d)^j, d = x - z_c, by Horner in rho/d
+            const float inv = 1.0f / d2;
+            const float2 w = make_float2(dx * inv, -dy * inv);          // 1 / d
+            const float rsc = T.rs[id];
+            const float2 v = make_float2(rsc * w.x, rsc * w.y);         // rho / d
 #pragma unroll
-                for (int r = 0; r < NR; ++r) acc[k][r] = fmaf(kb, u[r], acc[k][r]);
+            for (int r = 0; r < NR; ++r) {
+                const float2* Mr = mom + ((size_t)r * T.C + id) * kTerms;
+                float2 sacc = Mr[kTerms - 1];
+#pragma unroll
+                for (int j = kTerms - 2; j >= 0; --j) {
+                    const float2 mj = Mr[j];
+                    sacc = make_float2(fmaf(sacc.x, v.x, fmaf(-sacc.y, v.y, mj.x)), fmaf(sacc.x, v.y, fmaf(sacc.y, v.x, mj.y)));
+                }
+                acc[r] -= fmaf(sacc.x, w.x, -sacc.y * w.y);
             }
+        } else if (lvl == 0) {
+            const int g0 = i * kLeaf, g1 = min(Ng, g0 + kLeaf);
+            for (int g = g0; g < g1; ++g) {
+                const int eg = g / kGaussRhs;
+                if (eg == em || eg == ea || eg == eb) continue;
+                const float4 q = T.src[g];
+                const float2 nu = T.ab[g];
+                const float kb = kb32_pair(q.x, q.y, q.z, q.w, nu.x, nu.y, xh, xl, yh, yl);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] = fmaf(kb, wu[(size_t)r * Ng + g], acc[r]);
+            }
+        } else {
+            const int cl = T.cnt[lvl - 1];
+            if (2 * i + 1 < cl) stk[sp++] = ((lvl - 1) << 24) | (2 * i + 1);
+            stk[sp++] = ((lvl - 1) << 24) | (2 * i);
         }
     }
+    if (live) {
 #pragma unroll
-    for (int k = 0; k < kFarNN; ++k)
-#pragma unroll
-        for (int r = 0; r < NR; ++r) red[prt][r][lane + kFarLanes * k] = acc[k][r];
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < NR * kFarNodes; idx += blockDim.x) {
-        const int r = idx / kFarNodes, j = idx % kFarNodes;
-        const int m = blockIdx.x * kFarNodes + j;
-        if (m >= Nq) continue;
-        float v = red[0][r][j];
-#pragma unroll
-        for (int q = 1; q < kFarParts; ++q) v += red[q][r][j];
-        part[((size_t)blockIdx.y * NR + r) * Nq + m] = (double)v;
+        for (int r = 0; r < NR; ++r) out[(size_t)r * Nq + m] = (double)acc[r];
     }
 }
 
@@ -180,27 +333,22 @@ __global__ void __launch_bounds__(256) k_double_layer_d(int Nq, int Ng, const do
     }
 }
 
-// MIXED near field: Gauss points of the node's element and its two neighbours.
-// Adds their FP64 contributions and removes the FP32 ones the far-field kernel
-// summed (same bits from kb32_pair; the product of two floats is exact in FP64).
+// MIXED near field: the Gauss points of the node's element and its two
+// neighbours, where the numerator (f(t)-f(s)).n(t) is second-order small and an
+// FP32 value would be poor, in FP64, added to the treecode sum in `out`.
 // kNearLanes consecutive lanes share a node (pairs j = lane, lane + kNearLanes,
-// ... of the 3 kGaussRhs near pairs), reduced by a fixed shuffle tree; the
-// first lane adds the kSplit far-field partial sums (in slice order) and
-// writes the node's whole potential v_k(eta_m) into `out`.
+// ... of the 3 kGaussRhs near pairs), reduced by a fixed shuffle tree.
 constexpr int kNearLanes = 4;
 
 __global__ void k_double_layer_near(int Nq, int Ng, int M, int nrhs, const double* __restrict__ geo,
                                     const int* __restrict__ fspan, const double* __restrict__ rgeo,
                                     const double* __restrict__ rw, const double* __restrict__ uD, int ldu, int off,
-                                    const double* __restrict__ far, double* __restrict__ out) {
+                                    double* __restrict__ out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int m = t / kNearLanes, lane = t % kNearLanes;
     const bool live = m < Nq;
     const int mm = live ? m : Nq - 1;
     const double xm = geo[mm], ym = geo[Nq + mm];
-    float xh, xl, yh, yl;
-    split2(xm, xh, xl);
-    split2(ym, yh, yl);
     const int em = fspan[mm];
     double acc[kMaxRhs];
     for (int k = 0; k < kMaxRhs; ++k) acc[k] = 0.0;
@@ -211,26 +359,14 @@ __global__ void k_double_layer_near(int Nq, int Ng, int M, int nrhs, const doubl
         const int g = e * kGaussRhs + j % kGaussRhs;
         const double dx = rgeo[g] - xm, dy = rgeo[Ng + g] - ym;
         const double kb = (dx * rgeo[3 * Ng + g] - dy * rgeo[2 * Ng + g]) / (dx * dx + dy * dy);
-        float gxh, gxl, gyh, gyl;
-        split2(rgeo[g], gxh, gxl);
-        split2(rgeo[Ng + g], gyh, gyl);
-        const float kb32 = kb32_pair(gxh, gxl, gyh, gyl, (float)rgeo[3 * Ng + g], (float)(-rgeo[2 * Ng + g]), xh,
-                                     xl, yh, yl);
         const double w = rw[g];
-        for (int k = 0; k < nrhs; ++k) {
-            const double u = uD[(size_t)k * ldu + off + g];
-            acc[k] += kb * w * u - (double)kb32 * (double)(float)(w * u);
-        }
+        for (int k = 0; k < nrhs; ++k) acc[k] += kb * w * uD[(size_t)k * ldu + off + g];
     }
     for (int k = 0; k < nrhs; ++k) {
         double v = acc[k];
 #pragma unroll
         for (int o = 1; o < kNearLanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (live && lane == 0) {
-            double tot = 0.0;
-            for (int sl = 0; sl < kSplit; ++sl) tot += far[((size_t)sl * nrhs + k) * Nq + m];
-            out[(size_t)k * Nq + m] = tot + v;
-        }
+        if (live && lane == 0) out[(size_t)k * Nq + m] += v;
     }
 }
 
@@ -273,6 +409,95 @@ __global__ void k_beta(int n, int Nq, int d, int nrhs, int closed, const int* __
     if (live && lane == 0) beta[(size_t)k * n + i] = closed ? 0.5 * b1 - b2 / (2.0 * kPi) : b1;
 }
 
+// Levels of the treecode: ceil(Ng / kLeaf) leaves, then halving to one root.
+static void tree_plan(igs_prob p) {
+    int* cnt = p->tree_cnt;
+    int* off = p->tree_off;
+    cnt[0] = (p->Ng + kLeaf - 1) / kLeaf;
+    off[0] = 0;
+    int L = 1, C = cnt[0];
+    while (cnt[L - 1] > 1) {
+        if (L == kTreeMaxLevels) throw Error(IGS_E_INVALID_ARG, "too many Gauss points for the treecode");
+        cnt[L] = (cnt[L - 1] + 1) / 2;
+        off[L] = C;
+        C += cnt[L];
+        ++L;
+    }
+    p->tree_L = L;
+    p->tree_C = C;
+}
+
+// Byte offsets of the tree arrays in d_tree (16-byte aligned).
+struct TreeLayout {
+    size_t box, ctr, erng, thr, rs, src, ab, total;
+};
+static size_t up16(size_t b) { return (b + 15) & ~(size_t)15; }
+static TreeLayout tree_layout(int C, int Ng) {
+    TreeLayout t;
+    t.box = 0;
+    t.ctr = up16(t.box + sizeof(double) * 4 * (size_t)C);
+    t.erng = up16(t.ctr + sizeof(float4) * (size_t)C);
+    t.thr = up16(t.erng + sizeof(int2) * (size_t)C);
+    t.rs = up16(t.thr + sizeof(float) * (size_t)C);
+    t.src = up16(t.rs + sizeof(float) * (size_t)C);
+    t.ab = up16(t.src + sizeof(float4) * (size_t)Ng);
+    t.total = up16(t.ab + sizeof(float2) * (size_t)Ng);
+    return t;
+}
+
+static TreeArgs tree_args(const igs_prob p) {
+    const TreeLayout t = tree_layout(p->tree_C, p->Ng);
+    unsigned char* b = (unsigned char*)p->d_tree;
+    TreeArgs a;
+    a.L = p->tree_L;
+    a.C = p->tree_C;
+    for (int l = 0; l < kTreeMaxLevels; ++l) {
+        a.off[l] = p->tree_off[l];
+        a.cnt[l] = p->tree_cnt[l];
+    }
+    a.ctr = (const float4*)(b + t.ctr);
+    a.thr = (const float*)(b + t.thr);
+    a.rs = (const float*)(b + t.rs);
+    a.erng = (const int2*)(b + t.erng);
+    a.src = (const float4*)(b + t.src);
+    a.ab = (const float2*)(b + t.ab);
+    return a;
+}
+
+// Cluster geometry of the treecode from the Gauss points (after any change of
+// the geometry; no allocation).
+void rhs_tree_geometry(igs_prob p, cudaStream_t s) {
+    if (!p->d_tree) return;
+    const TreeLayout t = tree_layout(p->tree_C, p->Ng);
+    unsigned char* b = (unsigned char*)p->d_tree;
+    double* box = (double*)(b + t.box);
+    float4* ctr = (float4*)(b + t.ctr);
+    float* thr = (float*)(b + t.thr);
+    float* rs = (float*)(b + t.rs);
+    int2* erng = (int2*)(b + t.erng);
+    const int nleaf = p->tree_cnt[0];
+    k_tree_leaves<<<(nleaf + 127) / 128, 128, 0, s>>>(p->Ng, nleaf, p->d_rhs_geo, box, ctr, thr, rs, erng,
+                                                      (float4*)(b + t.src), (float2*)(b + t.ab));
+    for (int l = 1; l < p->tree_L; ++l)
+        k_tree_up<<<(p->tree_cnt[l] + 127) / 128, 128, 0, s>>>(p->tree_off[l - 1], p->tree_cnt[l - 1], p->tree_off[l],
+                                                               p->tree_cnt[l], box, ctr, thr, rs, erng);
+    IGS_CUDA(cudaGetLastError());
+    p->launches += p->tree_L;
+}
+
+// Doubles of per-call scratch one data set needs beside its N_quad potentials
+// (MIXED tier): the moments (kTerms float2 per cluster) and the FP32 w u_D
+// products at the Gauss points.
+static size_t tree_scratch_doubles(const igs_prob p) {
+    const int Ng = p->plan.M * kGaussRhs;
+    size_t C = 0;
+    for (int c = (Ng + kLeaf - 1) / kLeaf;; c = (c + 1) / 2) {
+        C += c;
+        if (c <= 1) break;
+    }
+    return C * kTerms + ((size_t)Ng + 1) / 2;
+}
+
 void rhs_prepare(igs_prob p) {
     // Gauss points of the b2 inner rule and the geometry there
     const Plan& P = p->plan;
@@ -307,6 +532,11 @@ void rhs_prepare(igs_prob p) {
     IGS_CUDA(cudaGetLastError());
     geometry_eval(p->geom, p->d_rhs_t, p->Ng, p->d_rhs_geo, s);
     p->launches += 2;
+    if (P.closed && p->precision == IGS_MIXED) {
+        tree_plan(p);
+        p->d_tree = dev_alloc(p, tree_layout(p->tree_C, p->Ng).total);
+        rhs_tree_geometry(p, s);
+    }
     IGS_CUDA(cudaStreamSynchronize(s));
     dev_free(p, d_g);
 }
@@ -314,25 +544,41 @@ void rhs_prepare(igs_prob p) {
 // Number of partial-sum slots (each nrhs x N_quad doubles) the kernels need.
 int rhs_slots(const igs_prob p) {
     if (!p->plan.closed) return 0;
-    return kSplit + (p->precision == IGS_MIXED ? 1 : 0);
+    if (p->precision == IGS_MIXED) {
+        const size_t Nq = (size_t)p->plan.Nq;
+        return 1 + (int)((tree_scratch_doubles(p) + Nq - 1) / Nq);
+    }
+    return kSplit;
 }
 
+// FP64 tier: kSplit partial sums of every pair.
 template <int NR>
-static void launch_far(igs_prob p, const double* d_uD, int ldu, double* part, cudaStream_t s) {
+static void launch_far_d(igs_prob p, const double* d_uD, int ldu, double* part, cudaStream_t s) {
     const Plan& P = p->plan;
-    if (p->precision == IGS_MIXED) {
-        // four nodes per thread, or two when that would leave SMs without a block
-        if ((P.Nq + 127) / 128 * kSplit >= 4 * 152)
-            k_double_layer_f<NR, 4><<<dim3((P.Nq + 127) / 128, kSplit), kFarLanes * kFarParts, 0, s>>>(
-                P.Nq, p->Ng, p->d_geo, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, part);
-        else
-            k_double_layer_f<NR, 2><<<dim3((P.Nq + 63) / 64, kSplit), kFarLanes * kFarParts, 0, s>>>(
-                P.Nq, p->Ng, p->d_geo, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, part);
-    }
-    else
-        k_double_layer_d<NR><<<dim3((P.Nq + 255) / 256, kSplit), 256, 0, s>>>(P.Nq, p->Ng, p->d_geo, p->d_rhs_geo,
-                                                                            p->d_rhs_w, d_uD, ldu, P.Nq, part);
+    k_double_layer_d<NR><<<dim3((P.Nq + 255) / 256, kSplit), 256, 0, s>>>(P.Nq, p->Ng, p->d_geo, p->d_rhs_geo,
+                                                                        p->d_rhs_w, d_uD, ldu, P.Nq, part);
     IGS_CUDA(cudaGetLastError());
+}
+
+// MIXED tier: treecode sum into out[nrhs][N_quad], moments and w u_D products
+// in `work` (tree_scratch_doubles per data set).
+template <int NR>
+static void launch_tree(igs_prob p, const double* d_uD, int ldu, double* out, double* work, cudaStream_t s) {
+    const Plan& P = p->plan;
+    const TreeArgs T = tree_args(p);
+    float2* mom = (float2*)work;
+    float* wu = (float*)(work + (size_t)NR * T.C * kTerms);
+    const int nleaf = T.cnt[0];
+    k_tree_leaf_moments<<<(nleaf * NR + 127) / 128, 128, 0, s>>>(p->Ng, nleaf, NR, T.C, p->d_rhs_geo, p->d_rhs_w,
+                                                                 d_uD, ldu, P.Nq, T.ctr, T.rs, T.ab, mom, wu);
+    for (int l = 1; l < T.L; ++l) {
+        const int th = T.cnt[l] * kTerms * NR;
+        k_tree_shift<<<(th + 127) / 128, 128, 0, s>>>(T.off[l - 1], T.cnt[l - 1], T.off[l], T.cnt[l], NR, T.C,
+                                                      T.ctr, T.rs, mom);
+    }
+    k_tree_eval<NR><<<(P.Nq + 127) / 128, 128, 0, s>>>(P.Nq, p->Ng, P.M, p->d_geo, p->d_fspan, T, mom, wu, out);
+    IGS_CUDA(cudaGetLastError());
+    p->launches += T.L + 1;
 }
 
 // Double-layer potentials v_k(eta_m) at the nodes of a closed curve, as
@@ -342,31 +588,40 @@ void rhs_node_potentials(igs_prob p, const double* d_uD, int nrhs, double* scrat
                          cudaStream_t s) {
     const Plan& P = p->plan;
     const int ldu = P.Nq + p->Ng;
-    *np = rhs_slots(p);
     *vsum = scratch;
-    switch (nrhs) {
-        case 1: launch_far<1>(p, d_uD, ldu, scratch, s); break;
-        case 2: launch_far<2>(p, d_uD, ldu, scratch, s); break;
-        case 3: launch_far<3>(p, d_uD, ldu, scratch, s); break;
-        case 4: launch_far<4>(p, d_uD, ldu, scratch, s); break;
-        case 5: launch_far<5>(p, d_uD, ldu, scratch, s); break;
-        case 6: launch_far<6>(p, d_uD, ldu, scratch, s); break;
-        case 7: launch_far<7>(p, d_uD, ldu, scratch, s); break;
-        default: launch_far<8>(p, d_uD, ldu, scratch, s); break;
-    }
-    p->launches++;
     if (p->precision == IGS_MIXED) {
-        // the near kernel writes the whole potential (far slices + near correction) into the last slot
-        double* whole = scratch + (size_t)kSplit * nrhs * P.Nq;
+        // the whole potential in the first nrhs x N_quad doubles: treecode, then the FP64 near pairs
+        double* work = scratch + (size_t)nrhs * P.Nq;
+        switch (nrhs) {
+            case 1: launch_tree<1>(p, d_uD, ldu, scratch, work, s); break;
+            case 2: launch_tree<2>(p, d_uD, ldu, scratch, work, s); break;
+            case 3: launch_tree<3>(p, d_uD, ldu, scratch, work, s); break;
+            case 4: launch_tree<4>(p, d_uD, ldu, scratch, work, s); break;
+            case 5: launch_tree<5>(p, d_uD, ldu, scratch, work, s); break;
+            case 6: launch_tree<6>(p, d_uD, ldu, scratch, work, s); break;
+            case 7: launch_tree<7>(p, d_uD, ldu, scratch, work, s); break;
+            default: launch_tree<8>(p, d_uD, ldu, scratch, work, s); break;
+        }
         const int nt = P.Nq * kNearLanes;
         k_double_layer_near<<<(nt + 127) / 128, 128, 0, s>>>(P.Nq, p->Ng, P.M, nrhs, p->d_geo, p->d_fspan,
-                                                             p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, scratch,
-                                                             whole);
+                                                             p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, scratch);
         IGS_CUDA(cudaGetLastError());
         p->launches++;
-        *vsum = whole;
         *np = 1;
+        return;
     }
+    *np = kSplit;
+    switch (nrhs) {
+        case 1: launch_far_d<1>(p, d_uD, ldu, scratch, s); break;
+        case 2: launch_far_d<2>(p, d_uD, ldu, scratch, s); break;
+        case 3: launch_far_d<3>(p, d_uD, ldu, scratch, s); break;
+        case 4: launch_far_d<4>(p, d_uD, ldu, scratch, s); break;
+        case 5: launch_far_d<5>(p, d_uD, ldu, scratch, s); break;
+        case 6: launch_far_d<6>(p, d_uD, ldu, scratch, s); break;
+        case 7: launch_far_d<7>(p, d_uD, ldu, scratch, s); break;
+        default: launch_far_d<8>(p, d_uD, ldu, scratch, s); break;
+    }
+    p->launches++;
 }
 
 // beta for nrhs data sets into d_beta, partial sums in `scratch` (rhs_slots x nrhs x N_quad doubles),

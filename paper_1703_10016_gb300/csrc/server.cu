@@ -60,8 +60,8 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 // Device bytes a request holds at its peak: the matrix, its transpose and the
 // factor (n^2 each in the tier type) and, in the FP64 tier, the symmetric copy
 // for the residuals (n^2 FP64), the stored
-// rules and their construction work arrays, node data and the right-hand
-// sides; 25% margin.
+// rules and their construction work arrays, node data, the right-hand sides
+// and the double-layer scratch; 25% margin.
 int64_t estimate_bytes(const igs_request& r) {
     const int64_t d = r.degree, Nh = r.n_elems, M = (int64_t)r.n_ref * Nh;
     const int64_t n = r.closed ? Nh : Nh + d;
@@ -74,6 +74,8 @@ int64_t estimate_bytes(const igs_request& r) {
     b += 2 * M * 2 * D1 * D1 * 8;                       // element-moment table
     b += Nq * 160 + n * 64 * 2 * tsz + (int64_t)r.nrhs * (n * 40 + M * 40);
     b += M * igs::kGaussRhs * (7 * 8 + (int64_t)r.nrhs * 8);  // b2 rule: points, weights, geometry, u_D there
+    if (r.closed)                                        // double-layer scratch (FP64 slices or treecode moments)
+        b += M * igs::kGaussRhs * 28 + (int64_t)r.nrhs * 12 * Nq * 8;
     b += n * 8 * 8;                                      // published solution words
     if (r.precision == IGS_MIXED && n >= 4096)           // split operand images of two outer blocks
         b += (int64_t)2 * 8 * 2 * ((n + 127) / 128) * 2048 * 4;

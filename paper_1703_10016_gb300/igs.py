@@ -56,7 +56,7 @@ class igs_info(C.Structure):
     _fields_ = [("n", C.c_int32), ("degree", C.c_int32), ("n_elems", C.c_int32), ("n_ref", C.c_int32),
                 ("n_quad", C.c_int32), ("n_exact", C.c_int32), ("n_rhs_pts", C.c_int32), ("closed", C.c_int32),
                 ("precision", C.c_int32), ("rules_ready", C.c_int32), ("assembled", C.c_int32),
-                ("factored", C.c_int32), ("device_bytes", C.c_int64)]
+                ("factored", C.c_int32), ("rhs_slots", C.c_int32), ("device_bytes", C.c_int64)]
 
 
 class igs_timing(C.Structure):

@@ -74,7 +74,9 @@ def test_noalloc_rhs_open_arc(ctx):
         g.igs_destroy_geometry(geom)
 
 
-@pytest.mark.parametrize("tier,slots,n", [("MIXED", 9, 3641), ("FP64", 8, 4096)])
+# MIXED: the potentials plus the treecode's moments and FP32 data products,
+# 1 + ceil((28 C + N_GQ / 2) / n_quad) slots (C clusters); FP64: 8 Gauss slices
+@pytest.mark.parametrize("tier,slots,n", [("MIXED", 11, 3000), ("FP64", 8, 4096)])
 def test_noalloc_rhs_limit(ctx, tier, slots, n):
     """Sizes just above the fixed array are refused with INVALID_ARG, one data
     set fewer fits; the preconditions are reported, not worked around."""
@@ -87,6 +89,7 @@ def test_noalloc_rhs_limit(ctx, tier, slots, n):
     fresh = g.igs_create_problem(geom, 3, 64, 2, g.IGS_FP64)
     try:
         info = g.igs_problem_info(prob)
+        assert info.rhs_slots == slots
         assert slots * info.n_quad * 8 > SCRATCH_DOUBLES >= slots * info.n_quad * 7
         xy = g.igs_rhs_points(prob)                    # rules, node geometry, rhs points
         u = torch.tensor(np.stack([wl.rhs_source(k, 8).value(xy[:, 0], xy[:, 1]) for k in range(8)]),
