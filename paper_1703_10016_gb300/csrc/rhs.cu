@@ -150,85 +150,147 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// Leaf moments for data set r (thread per (leaf, r)); also the FP32 products
+// 1 / (l + 1), l < kTerms: the binomial coefficients of the moment shift by a
+// running product (uniform index across a warp: constant-cache broadcast).
+__constant__ float c_recip[kTerms + 1] = {
+    1.f / 1,  1.f / 2,  1.f / 3,  1.f / 4,  1.f / 5,  1.f / 6,  1.f / 7,  1.f / 8,  1.f / 9,  1.f / 10,
+    1.f / 11, 1.f / 12, 1.f / 13, 1.f / 14, 1.f / 15, 1.f / 16, 1.f / 17, 1.f / 18, 1.f / 19, 1.f / 20,
+    1.f / 21, 1.f / 22, 1.f / 23, 1.f / 24, 1.f / 25, 1.f / 26, 1.f / 27, 1.f / 28, 1.f / 29};
+
+// Moments of leaf c for data set r, one warp, one lane per Gauss point: each
+// lane forms c_g ((y_g - z_c) / rho)^j and the warp adds them by a fixed
+// butterfly; lane j < kTerms returns M_j.  Writes the FP32 products
 // w_g u_r(t_g) the direct sums use.
-__global__ void k_tree_leaf_moments(int Ng, int nleaf, int nrhs, int C, const double* __restrict__ rgeo,
-                                    const double* __restrict__ rw, const double* __restrict__ uD, int ldu, int off,
-                                    const float4* __restrict__ ctr, const float* __restrict__ rs,
-                                    const float2* __restrict__ ab, float2* __restrict__ mom, float* __restrict__ wu) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = idx % nleaf, r = idx / nleaf;
-    if (r >= nrhs) return;
+static_assert(kLeaf == 32, "one lane per Gauss point of a leaf");
+__device__ __forceinline__ void leaf_moments_warp(int c, int r, int lane, int Ng, int C, const double* __restrict__ rgeo,
+                                                  const double* __restrict__ rw, const double* __restrict__ uD,
+                                                  int ldu, int off, const float4* __restrict__ ctr,
+                                                  const float* __restrict__ rs, const float2* __restrict__ ab,
+                                                  float2* __restrict__ mom, float* __restrict__ wu) {
     const float4 z = ctr[c];
     const double zx = (double)z.x + (double)z.y, zy = (double)z.z + (double)z.w;
-    const double ir = 1.0 / (double)rs[c];
-    float2 M[kTerms];
-#pragma unroll
-    for (int j = 0; j < kTerms; ++j) M[j] = make_float2(0.f, 0.f);
-    const int g0 = c * kLeaf, g1 = min(Ng, g0 + kLeaf);
-    for (int g = g0; g < g1; ++g) {
+    const float ir = 1.0f / rs[c];
+    const int g = c * kLeaf + lane;
+    float2 pw = make_float2(0.f, 0.f), t = make_float2(0.f, 0.f);
+    if (g < Ng) {
         const float w = (float)(rw[g] * uD[(size_t)r * ldu + off + g]);
         wu[(size_t)r * Ng + g] = w;
         const float2 nu = ab[g];
-        const float2 t = make_float2((float)((rgeo[g] - zx) * ir), (float)((rgeo[Ng + g] - zy) * ir));
-        float2 pw = make_float2(w * nu.x, w * nu.y);
-#pragma unroll
-        for (int j = 0; j < kTerms; ++j) {
-            M[j].x += pw.x;
-            M[j].y += pw.y;
-            pw = cmul(pw, t);
-        }
+        t = make_float2((float)(rgeo[g] - zx) * ir, (float)(rgeo[Ng + g] - zy) * ir);
+        pw = make_float2(w * nu.x, w * nu.y);
     }
-    float2* out = mom + ((size_t)r * C + c) * kTerms;
+    float2 mine = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int j = 0; j < kTerms; ++j) {
+        float sx = pw.x, sy = pw.y;
 #pragma unroll
-    for (int j = 0; j < kTerms; ++j) out[j] = M[j];
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        }
+        if (lane == j) mine = make_float2(sx, sy);
+        pw = cmul(pw, t);
+    }
+    if (lane < kTerms) mom[((size_t)r * C + c) * kTerms + lane] = mine;
 }
 
-// Parent moments from the children's (thread per (parent, j, r)), the sum
-// over l by Horner's rule in tau = (z_c - z_P) / rho_P, l ascending.
-__global__ void k_tree_shift(int offc, int cntc, int offp, int cntp, int nrhs, int C, const float4* __restrict__ ctr,
-                             const float* __restrict__ rs, float2* __restrict__ mom) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = idx % kTerms, i = (idx / kTerms) % cntp, r = idx / (kTerms * cntp);
-    if (r >= nrhs) return;
-    const int P = offp + i;
+// Moments of parent P (children c0 and, if c1 != c0, c1) for data set r, one
+// warp, lane j for M^P_j: the sum over l by Horner's rule in
+// tau = (z_c - z_P) / rho_P, l ascending, the children's moments broadcast
+// from lane l.
+__device__ __forceinline__ void shift_warp(int P, int c0, int c1, int r, int j, int C, const float4* __restrict__ ctr,
+                                           const float* __restrict__ rs, float2* __restrict__ mom) {
     const float4 zp = ctr[P];
     const double px = (double)zp.x + (double)zp.y, py = (double)zp.z + (double)zp.w;
-    const double irp = 1.0 / (double)rs[P];
+    const float irp = 1.0f / rs[P];
     float2 acc = make_float2(0.f, 0.f);
-    for (int ch = 2 * i; ch <= 2 * i + 1 && ch < cntc; ++ch) {
-        const int c = offc + ch;
+    for (int c = c0; c <= c1; ++c) {
         const float4 zc = ctr[c];
-        const float2 tau = make_float2((float)(((double)zc.x + (double)zc.y - px) * irp),
-                                       (float)(((double)zc.z + (double)zc.w - py) * irp));
-        const float sig = (float)((double)rs[c] * irp);
-        const float2* Mc = mom + ((size_t)r * C + c) * kTerms;
+        const float2 tau = make_float2((float)((double)zc.x + (double)zc.y - px) * irp,
+                                       (float)((double)zc.z + (double)zc.w - py) * irp);
+        const float sig = rs[c] * irp;
+        const float2 ml = j < kTerms ? mom[((size_t)r * C + c) * kTerms + j] : make_float2(0.f, 0.f);
         float2 sacc = make_float2(0.f, 0.f);
         float b = 1.f, sl = 1.f;                         // C(j, l), sig^l
-        for (int l = 0; l <= j; ++l) {
-            const float2 m = Mc[l];
-            const float f = b * sl;
-            sacc = cmul(sacc, tau);
-            sacc.x = fmaf(f, m.x, sacc.x);
-            sacc.y = fmaf(f, m.y, sacc.y);
-            sl *= sig;
-            b = b * (float)(j - l) / (float)(l + 1);
+#pragma unroll 4
+        for (int l = 0; l < kTerms; ++l) {
+            const float mx = __shfl_sync(0xffffffffu, ml.x, l), my = __shfl_sync(0xffffffffu, ml.y, l);
+            if (l <= j) {
+                const float f = b * sl;
+                sacc = cmul(sacc, tau);
+                sacc.x = fmaf(f, mx, sacc.x);
+                sacc.y = fmaf(f, my, sacc.y);
+                sl *= sig;
+                b *= (float)(j - l) * c_recip[l];
+            }
         }
         acc.x += sacc.x;
         acc.y += sacc.y;
     }
-    mom[((size_t)r * C + P) * kTerms + j] = acc;
+    if (j < kTerms) mom[((size_t)r * C + P) * kTerms + j] = acc;
+}
+
+// Leaves and the kSubLevels levels above them, one CTA per subtree of
+// 2^kSubLevels leaves (one warp per leaf, then per parent; the levels are
+// separated by block barriers, which also order the global moments).
+constexpr int kSubLevels = 4;
+constexpr int kSubLeaves = 1 << kSubLevels;
+__global__ void __launch_bounds__(32 * kSubLeaves) k_tree_subtree(int Ng, int nrhs, TreeArgs T, const double* __restrict__ rgeo,
+                                                                  const double* __restrict__ rw,
+                                                                  const double* __restrict__ uD, int ldu, int off,
+                                                                  float2* __restrict__ mom, float* __restrict__ wu) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kSubLeaves + w;
+    if (c < T.cnt[0])
+        for (int r = 0; r < nrhs; ++r)
+            leaf_moments_warp(c, r, lane, Ng, T.C, rgeo, rw, uD, ldu, off, T.ctr, T.rs, T.ab, mom, wu);
+    for (int l = 1; l <= kSubLevels && l < T.L; ++l) {
+        __syncthreads();
+        const int per = kSubLeaves >> l;                 // parents of this subtree at level l
+        const int i = blockIdx.x * per + w;
+        if (w < per && i < T.cnt[l]) {
+            const int c0 = T.off[l - 1] + 2 * i, c1 = (2 * i + 1 < T.cnt[l - 1]) ? c0 + 1 : c0;
+            for (int r = 0; r < nrhs; ++r) shift_warp(T.off[l] + i, c0, c1, r, lane, T.C, T.ctr, T.rs, mom);
+        }
+    }
+}
+
+// One level of the moment shifts, one warp per (parent, r).
+__global__ void __launch_bounds__(128) k_tree_shift(int l, int nrhs, TreeArgs T, float2* __restrict__ mom) {
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int cntp = T.cnt[l];
+    const int i = wid % cntp, r = wid / cntp;
+    if (r >= nrhs) return;                               // whole warps
+    const int c0 = T.off[l - 1] + 2 * i, c1 = (2 * i + 1 < T.cnt[l - 1]) ? c0 + 1 : c0;
+    shift_warp(T.off[l] + i, c0, c1, r, lane, T.C, T.ctr, T.rs, mom);
+}
+
+// The levels from l0 to the root in one CTA (each has at most 32 clusters):
+// warps stride over (parent, r), levels separated by block barriers.
+__global__ void __launch_bounds__(1024) k_tree_top(int l0, int nrhs, TreeArgs T, float2* __restrict__ mom) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int l = l0; l < T.L; ++l) {
+        if (l > l0) __syncthreads();
+        const int cntp = T.cnt[l];
+        for (int it = w; it < cntp * nrhs; it += nw) {
+            const int i = it % cntp, r = it / cntp;
+            const int c0 = T.off[l - 1] + 2 * i, c1 = (2 * i + 1 < T.cnt[l - 1]) ? c0 + 1 : c0;
+            shift_warp(T.off[l] + i, c0, c1, r, lane, T.C, T.ctr, T.rs, mom);
+        }
+    }
 }
 
 // The treecode sum at the nodes (warp per 32 consecutive nodes): out[r][m] =
 // the FP32 double-layer potential of data set r at eta_m without the Gauss
-// points of the node's element and its two neighbours.
+// points of the node's element and its two neighbours.  A cluster's moments
+// and a leaf's Gauss points are loaded once per warp (lane j holds M_j, lane g
+// point g of the leaf) and passed to every lane by shuffles.
 template <int NR>
 __global__ void __launch_bounds__(128) k_tree_eval(int Nq, int Ng, int M, const double* __restrict__ geo,
                                                    const int* __restrict__ fspan, const TreeArgs T,
                                                    const float2* __restrict__ mom, const float* __restrict__ wu,
                                                    double* __restrict__ out) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
     const bool live = m < Nq;
     const int mm = live ? m : Nq - 1;
     float xh, xl, yh, yl;
@@ -259,25 +321,38 @@ __global__ void __launch_bounds__(128) k_tree_eval(int Nq, int Ng, int M, const 
             const float2 v = make_float2(rsc * w.x, rsc * w.y);         // rho / d
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                const float2* Mr = mom + ((size_t)r * T.C + id) * kTerms;
-                float2 sacc = Mr[kTerms - 1];
+                const float2 ml = lane < kTerms ? mom[((size_t)r * T.C + id) * kTerms + lane] : make_float2(0.f, 0.f);
+                float2 sacc = make_float2(__shfl_sync(0xffffffffu, ml.x, kTerms - 1),
+                                          __shfl_sync(0xffffffffu, ml.y, kTerms - 1));
 #pragma unroll
                 for (int j = kTerms - 2; j >= 0; --j) {
-                    const float2 mj = Mr[j];
-                    sacc = make_float2(fmaf(sacc.x, v.x, fmaf(-sacc.y, v.y, mj.x)), fmaf(sacc.x, v.y, fmaf(sacc.y, v.x, mj.y)));
+                    const float mx = __shfl_sync(0xffffffffu, ml.x, j), my = __shfl_sync(0xffffffffu, ml.y, j);
+                    sacc = make_float2(fmaf(sacc.x, v.x, fmaf(-sacc.y, v.y, mx)), fmaf(sacc.x, v.y, fmaf(sacc.y, v.x, my)));
                 }
                 acc[r] -= fmaf(sacc.x, w.x, -sacc.y * w.y);
             }
         } else if (lvl == 0) {
-            const int g0 = i * kLeaf, g1 = min(Ng, g0 + kLeaf);
-            for (int g = g0; g < g1; ++g) {
-                const int eg = g / kGaussRhs;
-                if (eg == em || eg == ea || eg == eb) continue;
-                const float4 q = T.src[g];
-                const float2 nu = T.ab[g];
-                const float kb = kb32_pair(q.x, q.y, q.z, q.w, nu.x, nu.y, xh, xl, yh, yl);
+            const int g0 = i * kLeaf, gl = g0 + lane;
+            const bool have = gl < Ng;
+            const float4 q = have ? T.src[gl] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float2 nu = have ? T.ab[gl] : make_float2(0.f, 0.f);
+            float wl[NR];
 #pragma unroll
-                for (int r = 0; r < NR; ++r) acc[r] = fmaf(kb, wu[(size_t)r * Ng + g], acc[r]);
+            for (int r = 0; r < NR; ++r) wl[r] = have ? wu[(size_t)r * Ng + gl] : 0.f;
+#pragma unroll 4
+            for (int k = 0; k < kLeaf; ++k) {
+                const float qx = __shfl_sync(0xffffffffu, q.x, k), qxl = __shfl_sync(0xffffffffu, q.y, k);
+                const float qy = __shfl_sync(0xffffffffu, q.z, k), qyl = __shfl_sync(0xffffffffu, q.w, k);
+                const float a = __shfl_sync(0xffffffffu, nu.x, k), b = __shfl_sync(0xffffffffu, nu.y, k);
+                float wk[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) wk[r] = __shfl_sync(0xffffffffu, wl[r], k);
+                const int eg = (g0 + k) / kGaussRhs;
+                if (g0 + k < Ng && eg != em && eg != ea && eg != eb) {
+                    const float kb = kb32_pair(qx, qxl, qy, qyl, a, b, xh, xl, yh, yl);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) acc[r] = fmaf(kb, wk[r], acc[r]);
+                }
             }
         } else {
             const int cl = T.cnt[lvl - 1];
@@ -568,17 +643,20 @@ static void launch_tree(igs_prob p, const double* d_uD, int ldu, double* out, do
     const TreeArgs T = tree_args(p);
     float2* mom = (float2*)work;
     float* wu = (float*)(work + (size_t)NR * T.C * kTerms);
-    const int nleaf = T.cnt[0];
-    k_tree_leaf_moments<<<(nleaf * NR + 127) / 128, 128, 0, s>>>(p->Ng, nleaf, NR, T.C, p->d_rhs_geo, p->d_rhs_w,
-                                                                 d_uD, ldu, P.Nq, T.ctr, T.rs, T.ab, mom, wu);
-    for (int l = 1; l < T.L; ++l) {
-        const int th = T.cnt[l] * kTerms * NR;
-        k_tree_shift<<<(th + 127) / 128, 128, 0, s>>>(T.off[l - 1], T.cnt[l - 1], T.off[l], T.cnt[l], NR, T.C,
-                                                      T.ctr, T.rs, mom);
+    // leaves and kSubLevels levels per subtree; one launch per level while a
+    // level has more than 32 clusters; the rest to the root in one CTA
+    k_tree_subtree<<<(T.cnt[0] + kSubLeaves - 1) / kSubLeaves, 32 * kSubLeaves, 0, s>>>(
+        p->Ng, NR, T, p->d_rhs_geo, p->d_rhs_w, d_uD, ldu, P.Nq, mom, wu);
+    int l = kSubLevels + 1, launches = 1;
+    for (; l < T.L && T.cnt[l] > 32; ++l, ++launches)
+        k_tree_shift<<<(T.cnt[l] * NR + 3) / 4, 128, 0, s>>>(l, NR, T, mom);
+    if (l < T.L) {
+        k_tree_top<<<1, 1024, 0, s>>>(l, NR, T, mom);
+        ++launches;
     }
     k_tree_eval<NR><<<(P.Nq + 127) / 128, 128, 0, s>>>(P.Nq, p->Ng, P.M, p->d_geo, p->d_fspan, T, mom, wu, out);
     IGS_CUDA(cudaGetLastError());
-    p->launches += T.L + 1;
+    p->launches += launches + 1;
 }
 
 // Double-layer potentials v_k(eta_m) at the nodes of a closed curve, as

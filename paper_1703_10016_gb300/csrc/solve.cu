@@ -732,12 +732,31 @@ __global__ void k_wait_probe(const unsigned long long* w, unsigned long long ns,
     *status = wait_word(w, 0xabcd000000000000ull, v, 1LL << 40, ns) ? 0 : 1;
 }
 
-template <int NR>
+// The dependency tiles F[b0.., d0..] (64 x 64) do not depend on the published
+// values, so they are fetched kTrsvStages - 1 tiles ahead into a shared-memory
+// ring by cp.async (16-byte copies, zero fill outside the matrix; rows padded
+// to kTrsvLd floats: the four column phases of eight rows hit distinct banks).
+// A row of F must start on 16 bytes (n % 4 == 0); otherwise (ASYNC = false)
+// the next tile is held in registers.
+constexpr int kTrsvStages = 6;
+constexpr int kTrsvLd = kNB + 4;
+constexpr size_t kTrsvSmem = (size_t)kTrsvStages * kNB * kTrsvLd * sizeof(float);
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int NR, bool ASYNC>
 __global__ void __launch_bounds__(256) k_trsv_pk(int n, const float* __restrict__ F, const float* __restrict__ Linv,
                                                  float* __restrict__ X, int lower, unsigned long long* pub,
                                                  int epoch, int* __restrict__ err) {
     __shared__ float acc[NR][kNB];
     __shared__ float yin[NR][kNB];
+    extern __shared__ __align__(16) float ring[];       // [kTrsvStages][kNB][kTrsvLd] (ASYNC)
     const int tid = threadIdx.x;
     const int nblk = (n + kNB - 1) / kNB;
     const int i = tid / 4, part = tid % 4;          // row of the block, column phase
@@ -760,7 +779,7 @@ __global__ void __launch_bounds__(256) k_trsv_pk(int n, const float* __restrict_
         }
         const int ndep = lower ? blk : nblk - 1 - blk;
         float fr[kNB / 4];                          // F[b0 + i][d0 + part + 4 m] of the next dependency
-        auto fetch = [&](int q) {
+        auto fetch = [&](int q) {                   // register path
             const int D = lower ? q : nblk - 1 - q;
             const int d0 = D * kNB, dn = min(kNB, n - d0);
 #pragma unroll
@@ -769,11 +788,31 @@ __global__ void __launch_bounds__(256) k_trsv_pk(int n, const float* __restrict_
                 fr[m] = (i < bn && c < dn) ? F[(size_t)(b0 + i) * n + d0 + c] : 0.0f;
             }
         };
-        if (ndep > 0) fetch(0);
+        auto issue = [&](int q) {                   // ring path: tile q into stage q % kTrsvStages
+            if (q < ndep) {
+                const int D = lower ? q : nblk - 1 - q;
+                const int d0 = D * kNB, dn = min(kNB, n - d0);
+                float* st = ring + (size_t)(q % kTrsvStages) * kNB * kTrsvLd;
+#pragma unroll
+                for (int u = 0; u < kNB * kNB / 4 / 256; ++u) {
+                    const int ch = tid + 256 * u, row = ch / (kNB / 4), c4 = 4 * (ch % (kNB / 4));
+                    const bool ok = row < bn && c4 < dn;
+                    cp_async16(st + row * kTrsvLd + c4, ok ? F + (size_t)(b0 + row) * n + d0 + c4 : F, ok ? 16 : 0);
+                }
+            }
+            cp_async_commit();                      // empty groups keep the count uniform
+        };
+        if (ASYNC) {
+#pragma unroll
+            for (int q = 0; q < kTrsvStages - 1; ++q) issue(q);
+        } else if (ndep > 0) {
+            fetch(0);
+        }
         __syncthreads();
         for (int q = 0; q < ndep; ++q) {
             const int D = lower ? q : nblk - 1 - q;
             const int d0 = D * kNB, dn = min(kNB, n - d0);
+            if (ASYNC) issue(q + kTrsvStages - 1);
             int bad = 0;
             for (int idx = tid; idx < NR * kNB; idx += blockDim.x) {
                 const int k = idx / kNB, c = idx % kNB;
@@ -785,9 +824,16 @@ __global__ void __launch_bounds__(256) k_trsv_pk(int n, const float* __restrict_
                 }
                 yin[k][c] = y;
             }
+            if (ASYNC) cp_async_wait<kTrsvStages - 1>();    // tile q has landed (this thread's part)
             if (__syncthreads_or(bad)) {
+                if (ASYNC) cp_async_wait<0>();
                 if (tid == 0) atomicOr(err, 1);
                 return;
+            }
+            if (ASYNC) {
+                const float* row = ring + (size_t)(q % kTrsvStages) * kNB * kTrsvLd + i * kTrsvLd;
+#pragma unroll
+                for (int m = 0; m < kNB / 4; ++m) fr[m] = row[part + 4 * m];
             }
             // acc[k][i] -= sum_c F[b0+i][d0+c] yin[k][c]  (four threads per row)
             float sk[NR];
@@ -798,7 +844,7 @@ __global__ void __launch_bounds__(256) k_trsv_pk(int n, const float* __restrict_
                 for (int m = 0; m < kNB / 4; ++m) v += fr[m] * yin[k][part + 4 * m];
                 sk[k] = v;
             }
-            if (q + 1 < ndep) fetch(q + 1);
+            if (!ASYNC && q + 1 < ndep) fetch(q + 1);
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
                 float v = sk[k];
@@ -808,6 +854,7 @@ __global__ void __launch_bounds__(256) k_trsv_pk(int n, const float* __restrict_
             }
             __syncthreads();
         }
+        if (ASYNC) cp_async_wait<0>();              // no copy outlives its block (empty groups only)
         // own block: y = Linv acc (lower) or Linv^T acc (upper), stored and published
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
@@ -828,19 +875,23 @@ __global__ void __launch_bounds__(256) k_trsv_pk(int n, const float* __restrict_
 template <int NR>
 static void pk_launch(int n, const float* F, const float* Linv, float* X, int lower, unsigned long long* pub,
                       int epoch, int* err, cudaStream_t s) {
-    static int max_blocks = -1;                   // co-resident CTAs of this instantiation
-    if (max_blocks < 0) {
+    const bool async = (n % 4) == 0;
+    static int max_blocks[2] = {-1, -1};          // co-resident CTAs of each instantiation
+    auto kern = async ? k_trsv_pk<NR, true> : k_trsv_pk<NR, false>;
+    const size_t smem = async ? kTrsvSmem : 0;
+    if (max_blocks[async] < 0) {
         int dev = 0, sms = 0, per = 0;
         IGS_CUDA(cudaGetDevice(&dev));
         IGS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        IGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trsv_pk<NR>, 256, 0));
-        max_blocks = sms * per;
+        if (async) ensure_dyn_smem((const void*)kern, smem);
+        IGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem));
+        max_blocks[async] = sms * per;
     }
     const int nblk = (n + kNB - 1) / kNB;
-    const int grid = std::max(1, std::min(nblk, max_blocks));
+    const int grid = std::max(1, std::min(nblk, max_blocks[async]));
     void* args[] = {(void*)&n, (void*)&F, (void*)&Linv, (void*)&X, (void*)&lower, (void*)&pub, (void*)&epoch,
                     (void*)&err};
-    IGS_CUDA(cudaLaunchCooperativeKernel((void*)k_trsv_pk<NR>, dim3(grid), dim3(256), args, 0, s));
+    IGS_CUDA(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(256), args, smem, s));
 }
 
 static void launch_trsv_pk(int n, const float* F, const float* Linv, float* X, int nrhs, int lower,
