@@ -260,9 +260,8 @@ int igs_collocation(igs_prob prob, const double* uD, int nrhs, double* alpha_out
                     int mem);
 
 /* Right-hand side and solve in one call: the same computation as
- * igs_build_rhs followed by igs_solve(prob, NULL, ...) (the refinement's
- * residual norms are atomic sums, so solutions agree to the refinement's
- * accuracy, not bit for bit).  The right-hand side
+ * igs_build_rhs followed by igs_solve(prob, NULL, ...), with the same bits
+ * (every reduction on the path has a fixed order).  The right-hand side
  * (Sect. 5) is computed on an auxiliary stream of the problem while the
  * factorisation (eq. sistlin) runs on the context stream, so the two
  * overlap when the problem is not yet factored.
