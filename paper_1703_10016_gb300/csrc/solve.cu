@@ -1654,14 +1654,14 @@ static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent
 }
 
 // MIXED tier, large n: the same panels, with the trailing update blocked by
-// outer column blocks of kOB = 4 panels.  Inside an outer block each panel
+// outer column blocks of kOB = 8 panels.  Inside an outer block each panel
 // updates only the remaining columns of that block (SIMT, mode 3); after the
 // block's last panel the rest of the matrix is updated once with K = kOB on
 // the tensor cores.  Look-ahead as in issue_factor, one level up: the next
 // outer block's columns are updated first on s0; the rest of the outer update
 // runs on s1 beside the next outer block's panels, and the next outer step's
 // s0 update waits for it (both touch the columns after the next block).
-constexpr int kOB = 4 * kNB;
+constexpr int kOB = 8 * kNB;
 constexpr int kBlockedMinN = 4096;
 
 // The image buffers hold two outer blocks (alternating), so the split of
@@ -1672,7 +1672,7 @@ constexpr int kBlockedMinN = 4096;
 static int tcb_groups(int n) { return 4 * ((n + (int)kTN - 1) / (int)kTN); }
 static size_t tcb_image_halves(int n) { return (size_t)(kOB / kKC) * 2 * tcb_groups(n) * kImgHalves; }
 
-constexpr int kTcpReserveSMs = 64;
+constexpr int kTcpReserveSMs = 80;
 static void tcb_launch(int n, float* F, const __half* img, int K0, int kbo, int tj_off, int tcols, int* flag,
                        cudaStream_t s) {
     const int rem = n - K0 - kbo;
