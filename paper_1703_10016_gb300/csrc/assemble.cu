@@ -215,17 +215,27 @@ __global__ void __launch_bounds__(256) k_assemble_tile(
 // rules) stage the window of the two sequences they touch, so the singular
 // weight is one shared-memory read at a per-node offset; the other tiles read
 // the stored rules through ws_at, fetched a few steps ahead.  Only tiles whose
-// A- and B-ranges share a node test for the diagonal limit.
+// A- and B-ranges share a node test for the diagonal limit.  Far tiles (the
+// bounding boxes of the A- and B-range nodes at least twice the larger box
+// diagonal apart, most tiles of a large problem) take the coordinate and
+// parameter differences in plain FP32 from positions relative to the tile's
+// first B node: every relative position is off by at most eps times its size,
+// and the sizes are at most the difference plus one box diagonal, so the
+// difference keeps a relative error below 3 eps (float-float keeps about 1 eps);
+// three additions per pair instead of nine.
 template <int D> __host__ __device__ constexpr int rec_words() { return 3 + 2 * ((D + 1 + 3) / 4); }
 
-template <int D, bool CLOSED, bool TOE, bool DIAG>
+template <int D, bool CLOSED, bool TOE, bool DIAG, bool FAR>
 __device__ __forceinline__ void tile_walk_f(const TileF& t, int ma, int a, int Nb, int nj,
                                             const float4* __restrict__ rec, const int* __restrict__ sGs,
-                                            const float* __restrict__ sT, float* __restrict__ row) {
+                                            const float* __restrict__ sT, float* __restrict__ row, const NodeF& org) {
     constexpr int D1 = D + 1;
     constexpr int NV = (D1 + 3) / 4;
     constexpr int RW = rec_words<D>();
     const NodeF na = t.nodes[ma];
+    // this node relative to the tile's first B node (far tiles)
+    const float xr = (na.xh - org.xh) + (na.xl - org.xl), yr = (na.yh - org.yh) + (na.yl - org.yl);
+    const float er = (na.eh - org.eh) + (na.el - org.el);
     const float cdiag = na.lnJ * 2.88539008177792681f;    // K1(s,s) = ln J in base-2 units (x 2 / ln 2)
     const float ccorner = cdiag - 2.0f;                    // ln J - ln 2 in the same units
     float acc[D1];
@@ -252,10 +262,19 @@ __device__ __forceinline__ void tile_walk_f(const TileF& t, int ma, int a, int N
             for (int q = 0; q < kPre - 1; ++q) wq[q] = wq[q + 1];
             wq[kPre - 1] = (v + kPre < Nb) ? ws_at(t.ws, ma, idx(v + kPre).x) : 0.0f;
         }
-        const float4 g0 = p[0], g1 = p[1];
-        const float dx = (g0.x - na.xh) + (g0.y - na.xl);
-        const float dy = (g0.z - na.yh) + (g0.w - na.yl);
-        float Dd = (g1.x - na.eh) + (g1.y - na.el);
+        const float4 g1 = p[1];
+        float dx, dy, Dd;
+        if (FAR) {
+            const float4 gr = p[0];
+            dx = gr.x - xr;
+            dy = gr.y - yr;
+            Dd = gr.z - er;
+        } else {
+            const float4 g0 = p[0];
+            dx = (g0.x - na.xh) + (g0.y - na.xl);
+            dy = (g0.z - na.yh) + (g0.w - na.yl);
+            Dd = (g1.x - na.eh) + (g1.y - na.el);
+        }
         // x + L and L - x as sums of non-negative numbers: the high parts
         // alone keep FP32 relative accuracy
         if (CLOSED) Dd *= (g1.x + na.ebh) * (g1.z + na.eh);
@@ -320,7 +339,8 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
     // 16-byte records first, then 4-byte arrays: every offset stays aligned
     // for any maxr.  B-node record v: words 0-1 (xh, xl, yh, yl), (eh, el, ebh, ebl);
     // words 2 .. 2+2NV-1 the P ln2/2 row and the Q row (zero padded); last word
-    // (m, first column - j0, Toeplitz offset, 0) as integers
+    // (m, first column - j0, Toeplitz offset, 0) as integers.  Far tiles then
+    // replace word 0 by (x, y, e) relative to B node 0 in plain FP32.
     constexpr int RW = rec_words<D>();
     float4* sRec = (float4*)smem;                      // [maxr][RW]
     int* sJA = (int*)(sRec + (size_t)RW * maxr);       // [maxr]
@@ -328,10 +348,21 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
     float* sT = sPA + maxr * D1;                       // [2][Na + Nb - 1] (Toeplitz tiles)
     int* sGs = (int*)(sT + 4 * maxr);                  // [TI + D + 2] first B node of each column group
     float* sS1 = (float*)(sGs + TI + D + 2);           // [maxr][TI + 1]
+    float (*sBox)[8] = (float (*)[8])(sS1 + maxr * (TI + 1));   // [warps][8] node bounding boxes
 
+    // bounding boxes of the A- and B-range nodes (high parts), for the far test
+    const NodeF org = t.nodes[pmod(uB0, Nq)];
+    float bx[8] = {3e38f, -3e38f, 3e38f, -3e38f, 3e38f, -3e38f, 3e38f, -3e38f};
+    if ((int)threadIdx.x < Na) {
+        const NodeF na = t.nodes[pmod(uA0 + (int)threadIdx.x, Nq)];
+        bx[0] = bx[1] = na.xh;
+        bx[2] = bx[3] = na.yh;
+    }
     for (int v = threadIdx.x; v < Nb; v += blockDim.x) {
         const int u = uB0 + v, m = pmod(u, Nq), per = pdiv(u, Nq);
         const NodeF b = t.nodes[m];
+        bx[4] = fminf(bx[4], b.xh); bx[5] = fmaxf(bx[5], b.xh);
+        bx[6] = fminf(bx[6], b.yh); bx[7] = fmaxf(bx[7], b.yh);
         float4* rv = sRec + (size_t)v * RW;
         rv[0] = make_float4(b.xh, b.xl, b.yh, b.yl);
         rv[1] = make_float4(b.eh, b.el, b.ebh, b.ebl);
@@ -355,6 +386,16 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
         sJA[v] = jfirst[m] + n * per - i0;
         for (int r = 0; r < D1; ++r) sPA[v * D1 + r] = P[m * D1 + r];
     }
+#pragma unroll
+    for (int k = 0; k < 8; k += 2)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bx[k] = fminf(bx[k], __shfl_xor_sync(0xffffffffu, bx[k], o));
+            bx[k + 1] = fmaxf(bx[k + 1], __shfl_xor_sync(0xffffffffu, bx[k + 1], o));
+        }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sBox[threadIdx.x >> 5][k] = bx[k];
     if (toe) {
         const int tbase = (uA0 - uB0) - (Nb - 1) + Nq - 1;      // sequence index of window entry 0
         const size_t slen = 2 * (size_t)Nq - 1;
@@ -364,6 +405,33 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
         }
     }
     __syncthreads();
+    // far tile: box gap at least twice the larger box diagonal (block-uniform)
+    bool far = false;
+    if (toe && !diag) {
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+            bx[k] = sBox[0][k];
+            bx[k + 1] = sBox[0][k + 1];
+        }
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+                bx[k] = fminf(bx[k], sBox[w][k]);
+                bx[k + 1] = fmaxf(bx[k + 1], sBox[w][k + 1]);
+            }
+        const float gx = fmaxf(0.0f, fmaxf(bx[0] - bx[5], bx[4] - bx[1]));
+        const float gy = fmaxf(0.0f, fmaxf(bx[2] - bx[7], bx[6] - bx[3]));
+        const float da = (bx[1] - bx[0]) * (bx[1] - bx[0]) + (bx[3] - bx[2]) * (bx[3] - bx[2]);
+        const float db = (bx[5] - bx[4]) * (bx[5] - bx[4]) + (bx[7] - bx[6]) * (bx[7] - bx[6]);
+        far = gx * gx + gy * gy >= 4.0f * fmaxf(da, db);
+    }
+    if (far)
+        for (int v = threadIdx.x; v < Nb; v += blockDim.x) {
+            float4* rv = sRec + (size_t)v * RW;
+            const float4 g0 = rv[0], g1 = rv[1];
+            rv[0] = make_float4((g0.x - org.xh) + (g0.y - org.xl), (g0.z - org.yh) + (g0.w - org.yl),
+                                (g1.x - org.eh) + (g1.y - org.el), 0.0f);
+        }
     // column groups: the B nodes whose first column is jrel_0 + k start at
     // sGs[k] (empty groups repeat the next start); sGs[G] = Nb
     for (int v = threadIdx.x; v < Nb; v += blockDim.x) {
@@ -379,10 +447,11 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
         const int ma = pmod(uA0 + a, Nq);
         float* row = sS1 + a * (TI + 1);
         if (toe) {
-            if (diag) tile_walk_f<D, CLOSED, true, true>(t, ma, a, Nb, nj, sRec, sGs, sT, row);
-            else tile_walk_f<D, CLOSED, true, false>(t, ma, a, Nb, nj, sRec, sGs, sT, row);
+            if (diag) tile_walk_f<D, CLOSED, true, true, false>(t, ma, a, Nb, nj, sRec, sGs, sT, row, org);
+            else if (far) tile_walk_f<D, CLOSED, true, false, true>(t, ma, a, Nb, nj, sRec, sGs, sT, row, org);
+            else tile_walk_f<D, CLOSED, true, false, false>(t, ma, a, Nb, nj, sRec, sGs, sT, row, org);
         } else {
-            tile_walk_f<D, CLOSED, false, true>(t, ma, a, Nb, nj, sRec, sGs, sT, row);
+            tile_walk_f<D, CLOSED, false, true, false>(t, ma, a, Nb, nj, sRec, sGs, sT, row, org);
         }
     }
     __syncthreads();
@@ -439,7 +508,8 @@ __global__ void __launch_bounds__(1024) k_assemble_f(const TileF t) {
 size_t tile_smem_f(int maxr, int d, int TI) {
     const int NV = (d + 1 + 3) / 4;
     return (size_t)maxr * (2 + 2 * NV) * 16 + (size_t)maxr * 16 + (size_t)maxr * 4 + (size_t)maxr * (d + 1) * 4 +
-           (size_t)maxr * 4 * 4 + (size_t)(TI + d + 2) * 4 + (size_t)maxr * (TI + 1) * 4 + 64;
+           (size_t)maxr * 4 * 4 + (size_t)(TI + d + 2) * 4 + (size_t)maxr * (TI + 1) * 4 +
+           (size_t)((maxr + 31) / 32) * 8 * 4 + 64;
 }
 
 TileF tile_args_f(igs_prob p, int maxr) {
