@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256) k_assemble_tile(
 
 // FP32 tier, one thread per A-range node: the block is as wide as the largest
 // node range (rounded up to a warp), so that no thread idles in stage 1.  Each
-// B-range node is one shared-memory record of 3 + 2 NV 16-byte words read by
+// B-range node is one shared-memory record of 3 + NW 16-byte words read by
 // broadcast -- coordinates, parameter offsets, the P and Q weight rows and the
 // indices (m, first column, Toeplitz offset) -- so one pointer addresses all of
 // a node's data.  The nodes are walked in groups of equal first column, so
@@ -223,14 +223,16 @@ __global__ void __launch_bounds__(256) k_assemble_tile(
 // and the sizes are at most the difference plus one box diagonal, so the
 // difference keeps a relative error below 3 eps (float-float keeps about 1 eps);
 // three additions per pair instead of nine.
-template <int D> __host__ __device__ constexpr int rec_words() { return 3 + 2 * ((D + 1 + 3) / 4); }
+// 16-byte words of the P ln2/2 and Q rows of a node, packed back to back
+template <int D> __host__ __device__ constexpr int wt_words() { return (2 * (D + 1) + 3) / 4; }
+template <int D> __host__ __device__ constexpr int rec_words() { return 3 + wt_words<D>(); }
 
 template <int D, bool CLOSED, bool TOE, bool DIAG, bool FAR>
 __device__ __forceinline__ void tile_walk_f(const TileF& t, int ma, int a, int Nb, int nj,
                                             const float4* __restrict__ rec, const int* __restrict__ sGs,
                                             const float* __restrict__ sT, float* __restrict__ row, const NodeF& org) {
     constexpr int D1 = D + 1;
-    constexpr int NV = (D1 + 3) / 4;
+    constexpr int NW = wt_words<D>();
     constexpr int RW = rec_words<D>();
     const NodeF na = t.nodes[ma];
     // this node relative to the tile's first B node (far tiles)
@@ -262,35 +264,36 @@ __device__ __forceinline__ void tile_walk_f(const TileF& t, int ma, int a, int N
             for (int q = 0; q < kPre - 1; ++q) wq[q] = wq[q + 1];
             wq[kPre - 1] = (v + kPre < Nb) ? ws_at(t.ws, ma, idx(v + kPre).x) : 0.0f;
         }
-        const float4 g1 = p[1];
-        float dx, dy, Dd;
+        float dx, dy, Dd, eb, ebb;                     // eb, ebb: high parts of x and L - x at node b
         if (FAR) {
             const float4 gr = p[0];
             dx = gr.x - xr;
             dy = gr.y - yr;
             Dd = gr.z - er;
+            eb = gr.w;
+            ebb = __int_as_float(br.w);
         } else {
-            const float4 g0 = p[0];
+            const float4 g0 = p[0], g1 = p[1];
             dx = (g0.x - na.xh) + (g0.y - na.xl);
             dy = (g0.z - na.yh) + (g0.w - na.yl);
             Dd = (g1.x - na.eh) + (g1.y - na.el);
+            eb = g1.x;
+            ebb = g1.z;
         }
         // x + L and L - x as sums of non-negative numbers: the high parts
         // alone keep FP32 relative accuracy
-        if (CLOSED) Dd *= (g1.x + na.ebh) * (g1.z + na.eh);
+        if (CLOSED) Dd *= (eb + na.ebh) * (ebb + na.eh);
         float c0 = lg2_ftz(div_ftz(fmaf(dx, dx, dy * dy), Dd * Dd));
         if (DIAG) c0 = (br.x == ma) ? cdiag : c0;
         if (CLOSED && !TOE) c0 = (ma + br.x == t.Nq - 1 && (ma == 0 || br.x == 0)) ? ccorner : c0;
-        float w[2][4 * NV];
+        float w[4 * NW];
 #pragma unroll
-        for (int kk = 0; kk < 2; ++kk)
+        for (int q = 0; q < NW; ++q) {
+            const float4 t4 = p[2 + q];
+            w[4 * q] = t4.x; w[4 * q + 1] = t4.y; w[4 * q + 2] = t4.z; w[4 * q + 3] = t4.w;
+        }
 #pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                const float4 t4 = p[2 + kk * NV + q];
-                w[kk][4 * q] = t4.x; w[kk][4 * q + 1] = t4.y; w[kk][4 * q + 2] = t4.z; w[kk][4 * q + 3] = t4.w;
-            }
-#pragma unroll
-        for (int r = 0; r < D1; ++r) acc[r] = fmaf(w[0][r], c0, fmaf(w[1][r], ws, acc[r]));
+        for (int r = 0; r < D1; ++r) acc[r] = fmaf(w[r], c0, fmaf(w[D1 + r], ws, acc[r]));
     };
     for (int k = 0; k < G; ++k) {
         if (k > 0) {
@@ -317,7 +320,6 @@ template <int D, bool CLOSED, int TI>
 __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned char* smem) {
     static_assert(TI <= 32, "stage 2 maps one lane to one column of the tile");
     constexpr int D1 = D + 1;
-    constexpr int NV = (D1 + 3) / 4;                   // float4s per weight row
     const int n = t.n, Nq = t.Nq, maxr = t.maxr;
     const int* __restrict__ lo = t.lo;
     const int* __restrict__ hi = t.hi;
@@ -338,9 +340,10 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
     const int tlen = Na + Nb - 1;
     // 16-byte records first, then 4-byte arrays: every offset stays aligned
     // for any maxr.  B-node record v: words 0-1 (xh, xl, yh, yl), (eh, el, ebh, ebl);
-    // words 2 .. 2+2NV-1 the P ln2/2 row and the Q row (zero padded); last word
-    // (m, first column - j0, Toeplitz offset, 0) as integers.  Far tiles then
-    // replace word 0 by (x, y, e) relative to B node 0 in plain FP32.
+    // words 2 .. 2+NW-1 the P ln2/2 row and the Q row back to back (zero padded);
+    // last word (m, first column - j0, Toeplitz offset, high part of L - x) as
+    // integers.  Far tiles then replace word 0 by (x, y, e) relative to B node
+    // 0 in plain FP32 and the high part of x.
     constexpr int RW = rec_words<D>();
     float4* sRec = (float4*)smem;                      // [maxr][RW]
     int* sJA = (int*)(sRec + (size_t)RW * maxr);       // [maxr]
@@ -366,20 +369,17 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
         float4* rv = sRec + (size_t)v * RW;
         rv[0] = make_float4(b.xh, b.xl, b.yh, b.yl);
         rv[1] = make_float4(b.eh, b.el, b.ebh, b.ebl);
-        float w[2][4 * NV];
+        constexpr int NW = wt_words<D>();
+        float w[4 * NW];
 #pragma unroll
-        for (int r = 0; r < 4 * NV; ++r) {
-            w[0][r] = r < D1 ? P[m * D1 + r] * 0.346573590279972655f : 0.0f;   // x ln2 / 2
-            w[1][r] = r < D1 ? Q[m * D1 + r] : 0.0f;
-        }
+        for (int r = 0; r < 4 * NW; ++r)
+            w[r] = r < D1 ? P[m * D1 + r] * 0.346573590279972655f                 // x ln2 / 2
+                          : (r < 2 * D1 ? Q[m * D1 + r - D1] : 0.0f);
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
-#pragma unroll
-            for (int q = 0; q < NV; ++q)
-                rv[2 + k * NV + q] = make_float4(w[k][4 * q], w[k][4 * q + 1], w[k][4 * q + 2], w[k][4 * q + 3]);
+        for (int q = 0; q < NW; ++q) rv[2 + q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         // W^s[ma][mb] = T[(mb - B) & 1][ma - mb + Nq - 1] = sT[offset + a]
         const int off = ((m - wsv.B) & 1) * tlen + (Nb - 1) - v;
-        *reinterpret_cast<int4*>(&rv[RW - 1]) = make_int4(m, jfirst[m] + n * per - j0, off, 0);
+        *reinterpret_cast<int4*>(&rv[RW - 1]) = make_int4(m, jfirst[m] + n * per - j0, off, __float_as_int(b.ebh));
     }
     for (int v = threadIdx.x; v < Na; v += blockDim.x) {
         const int u = uA0 + v, m = pmod(u, Nq), per = pdiv(u, Nq);
@@ -430,7 +430,7 @@ __device__ __forceinline__ void tile_f(const TileF& t, int I, int J, unsigned ch
             float4* rv = sRec + (size_t)v * RW;
             const float4 g0 = rv[0], g1 = rv[1];
             rv[0] = make_float4((g0.x - org.xh) + (g0.y - org.xl), (g0.z - org.yh) + (g0.w - org.yl),
-                                (g1.x - org.eh) + (g1.y - org.el), 0.0f);
+                                (g1.x - org.eh) + (g1.y - org.el), g1.x);
         }
     // column groups: the B nodes whose first column is jrel_0 + k start at
     // sGs[k] (empty groups repeat the next start); sGs[G] = Nb
@@ -506,8 +506,8 @@ __global__ void __launch_bounds__(1024) k_assemble_f(const TileF t) {
 }
 
 size_t tile_smem_f(int maxr, int d, int TI) {
-    const int NV = (d + 1 + 3) / 4;
-    return (size_t)maxr * (2 + 2 * NV) * 16 + (size_t)maxr * 16 + (size_t)maxr * 4 + (size_t)maxr * (d + 1) * 4 +
+    const int NW = (2 * (d + 1) + 3) / 4;
+    return (size_t)maxr * (2 + NW) * 16 + (size_t)maxr * 16 + (size_t)maxr * 4 + (size_t)maxr * (d + 1) * 4 +
            (size_t)maxr * 4 * 4 + (size_t)(TI + d + 2) * 4 + (size_t)maxr * (TI + 1) * 4 +
            (size_t)((maxr + 31) / 32) * 8 * 4 + 64;
 }
