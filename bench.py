@@ -36,8 +36,8 @@ if ROOT not in sys.path:
 # DRAM read + write bytes of one launch of the FP32 assembly kernel, keyed by
 # (n, degree, N_ref): ncu captures summarised in profiles/ (the file named in
 # the value); a configuration without a capture of the current kernel gets null
-ASSEMBLY_TRAFFIC = {(16384, 4, 2): (86.08e6 + 2.09e9, "profiles/ncu_assemble_f_traffic_star16384_star2048.md"),
-                    (2048, 3, 2): (8.44e6 + 6.4e3, "profiles/ncu_assemble_f_traffic_star16384_star2048.md")}
+ASSEMBLY_TRAFFIC = {(16384, 4, 2): (86.26e6 + 2.09e9, "profiles/ncu_assemble_f_traffic_star16384_star2048.md"),
+                    (2048, 3, 2): (8.46e6 + 15.1e3, "profiles/ncu_assemble_f_traffic_star16384_star2048.md")}
 
 
 def parse():
