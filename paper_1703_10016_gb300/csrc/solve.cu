@@ -325,6 +325,10 @@ __global__ void __launch_bounds__(256) k_syrk(int n, T* __restrict__ F, int k0, 
         ti = blockIdx.x;
         tj = blockIdx.y;
         if (ti < tj) return;
+    } else if (mode == 4) {                       // column tiles 1 .. gridDim.y, all rows below
+        ti = blockIdx.x;
+        tj = blockIdx.y + 1;
+        if (ti < tj) return;
     } else {
         tri_decode(blockIdx.x, ti, tj);
     }
@@ -1655,7 +1659,10 @@ static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent
 
 // MIXED tier, large n: the same panels, with the trailing update blocked by
 // outer column blocks of kOB = 8 panels.  Inside an outer block each panel
-// updates only the remaining columns of that block (SIMT, mode 3); after the
+// updates only the remaining columns of that block (SIMT): the next panel's
+// columns on s0 (mode 1), the block's later columns on a third stream s2
+// beside the next panel (mode 4; the next mode-1 update waits for it, both
+// touching the columns after the next panel); after the
 // block's last panel the rest of the matrix is updated once with K = kOB on
 // the tensor cores.  Look-ahead as in issue_factor, one level up: the next
 // outer block's columns are updated first on s0; the rest of the outer update
@@ -1700,23 +1707,36 @@ static void tcb_launch(int n, float* F, const __half* img, int K0, int kbo, int 
         k_syrk_tcp<<<grid, kTcpThreads, tcp_smem_bytes(), s>>>(n, F, img, K0, kbo, G2, tj_off, ntc, ntr, ntiles, flag);
 }
 
-static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evP, cudaEvent_t evB,
-                                 cudaEvent_t evJ) {
+static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaStream_t s2, cudaEvent_t evP,
+                                 cudaEvent_t evB, cudaEvent_t evJ, cudaEvent_t evQ, cudaEvent_t evS) {
     const int n = p->plan.n;
     float* F = (float*)p->d_F;
     IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s0));
     bool pending = false, forked = false;
     for (int K0 = 0; K0 < n; K0 += kOB) {
         const int kbo = std::min(kOB, n - K0);
+        bool side = false;                                            // a side update of this block is pending
         for (int k0 = K0; k0 < K0 + kbo; k0 += kNB) {
             const int kb = std::min(kNB, n - k0);
             const int rows = n - k0;
             launch_pdl(k_panel<float>, dim3((rows + kNB - 1) / kNB), dim3(kPanelThreads), panel_smem<float>(), s0, n,
                        F, k0, kb, (float*)p->d_diagL, p->d_flag);
             const int inner = (K0 + kbo - (k0 + kb) + kST - 1) / kST;   // column tiles left in this block
-            if (inner > 0) {
-                const int nt = (n - k0 - kb + kST - 1) / kST;
-                launch_pdl(k_syrk<float>, dim3(nt, inner), dim3(256), syrk_smem<float>(), s0, n, F, k0, kb, 3);
+            if (inner <= 0) continue;
+            const int nt = (n - k0 - kb + kST - 1) / kST;
+            // the next panel's columns on the chain, after the previous panel's side update
+            // (both touch them); the block's later columns on the third stream
+            if (side) {
+                IGS_CUDA(cudaStreamWaitEvent(s0, evS, 0));
+                side = false;
+            }
+            if (inner > 1) IGS_CUDA(cudaEventRecord(evQ, s0));
+            launch_pdl(k_syrk<float>, dim3(nt), dim3(256), syrk_smem<float>(), s0, n, F, k0, kb, 1);
+            if (inner > 1) {
+                IGS_CUDA(cudaStreamWaitEvent(s2, evQ, 0));
+                k_syrk<float><<<dim3(nt, inner - 1), 256, syrk_smem<float>(), s2>>>(n, F, k0, kb, 4);
+                IGS_CUDA(cudaEventRecord(evS, s2));
+                side = true;
             }
         }
         const int rem = n - K0 - kbo;
@@ -1755,7 +1775,8 @@ static int factor_launches_blocked(int n) {
     int c = 2;
     for (int K0 = 0; K0 < n; K0 += kOB) {
         const int kbo = std::min(kOB, n - K0);
-        for (int k0 = K0; k0 < K0 + kbo; k0 += kNB) c += (k0 + kNB < K0 + kbo) ? 2 : 1;
+        for (int k0 = K0; k0 < K0 + kbo; k0 += kNB)
+            c += 1 + (k0 + kNB < K0 + kbo ? 1 : 0) + (k0 + 2 * kNB < K0 + kbo ? 1 : 0);
         const int rem = n - K0 - kbo;
         if (rem > 0) c += (rem > kOB) ? 3 : 2;
     }
@@ -1776,23 +1797,25 @@ static int factor_launches(int n) {
 // two private streams.
 template <typename T>
 static void capture_factor(igs_prob p, bool blocked) {
-    // capture the fixed launch sequence once, on two private streams
-    cudaStream_t cs = nullptr, cs1 = nullptr;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    // capture the fixed launch sequence once, on private streams
+    cudaStream_t cs = nullptr, cs1 = nullptr, cs2 = nullptr;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     auto release = [&]() {
         for (cudaEvent_t& e : ev)
             if (e) cudaEventDestroy(e);
         if (cs1) cudaStreamDestroy(cs1);
+        if (cs2) cudaStreamDestroy(cs2);
         if (cs) cudaStreamDestroy(cs);
     };
     cudaGraph_t graph = nullptr;
     try {
         IGS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         IGS_CUDA(cudaStreamCreateWithFlags(&cs1, cudaStreamNonBlocking));
+        IGS_CUDA(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
         for (cudaEvent_t& e : ev) IGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         IGS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         try {
-            if (blocked) issue_factor_blocked(p, cs, cs1, ev[0], ev[1], ev[2]);
+            if (blocked) issue_factor_blocked(p, cs, cs1, cs2, ev[0], ev[1], ev[2], ev[3], ev[4]);
             else issue_factor<T>(p, cs, cs1, ev[0], ev[1], ev[2]);
         } catch (...) {
             cudaStreamEndCapture(cs, &graph);
@@ -1825,17 +1848,19 @@ static void factor(igs_prob p, cudaStream_t s) {
         // first factorisation of this problem: issue the launch sequence directly
         // (a problem factored once, such as a served request, does not pay for a
         // graph capture); the graph is captured when the problem is factored again
-        cudaStream_t s1 = nullptr;
-        cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+        cudaStream_t s1 = nullptr, s2 = nullptr;
+        cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
         auto release = [&]() {
             for (cudaEvent_t& e : ev)
                 if (e) cudaEventDestroy(e);
             if (s1) cudaStreamDestroy(s1);
+            if (s2) cudaStreamDestroy(s2);
         };
         try {
             IGS_CUDA(cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking));
+            IGS_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
             for (cudaEvent_t& e : ev) IGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-            if (blocked) issue_factor_blocked(p, s, s1, ev[0], ev[1], ev[2]);
+            if (blocked) issue_factor_blocked(p, s, s1, s2, ev[0], ev[1], ev[2], ev[3], ev[4]);
             else issue_factor<T>(p, s, s1, ev[0], ev[1], ev[2]);
         } catch (...) {
             release();
