@@ -164,7 +164,13 @@ int igs_build_weighted_rules(igs_prob prob);
  * The matrix is kept inside the problem for igs_solve.  If A_out != NULL it is
  * also copied out, row-major with leading dimension `ld` >= n (elements), in
  * element type `dtype` (IGS_F64 or IGS_F32) to `mem` (IGS_MEM_HOST/DEVICE).
- * Errors: INVALID_ARG (ld < n, bad dtype/mem), NO_MEMORY, CUDA. */
+ * Without A_out the kernels are queued on the context stream and the call
+ * returns before they finish, so host work (for instance the Dirichlet data at
+ * the igs_rhs_points, downloaded before this call) overlaps them; every later
+ * call on the problem is ordered after them, and igs_problem_timing waits for
+ * them.  With A_out the call returns after the copy.
+ * Errors: INVALID_ARG (ld < n, bad dtype/mem), NO_MEMORY, CUDA (a kernel fault
+ * may surface in a later call). */
 int igs_assemble(igs_prob prob, void* A_out, int64_t ld, int mem, int dtype);
 
 /* Points where the Dirichlet datum u_D must be sampled for igs_build_rhs:

@@ -286,6 +286,8 @@ int igs_destroy_problem(igs_prob p) {
         p->aux_stream = nullptr;
     }
     for (void* q : ptrs) dev_free_raw(p, q);
+    for (cudaEvent_t e : p->asm_ev)
+        if (e) cudaEventDestroy(e);
     if (p->factor_exec) cudaGraphExecDestroy(p->factor_exec);
     cudaStreamSynchronize(p->geom->ctx->stream);
     p->geom->live_probs--;
@@ -328,9 +330,23 @@ int igs_problem_info(igs_prob p, igs_info* out) {
     API_END
 }
 
+// Read the geometry and assembly times of the last igs_assemble once its
+// kernels have finished (igs_assemble without a copy does not wait for them).
+static void finish_assemble_timing(igs_prob p) {
+    if (!p->asm_pending) return;
+    p->asm_pending = false;
+    IGS_CUDA(cudaEventSynchronize(p->asm_ev[2]));
+    float g_ms = 0, a_ms = 0;
+    IGS_CUDA(cudaEventElapsedTime(&g_ms, p->asm_ev[0], p->asm_ev[1]));
+    IGS_CUDA(cudaEventElapsedTime(&a_ms, p->asm_ev[1], p->asm_ev[2]));
+    p->timing.geometry_ms = g_ms;
+    p->timing.assemble_ms = a_ms;
+}
+
 int igs_problem_timing(igs_prob p, igs_timing* out) {
     API_BEGIN
     REQUIRE(p && out, IGS_E_INVALID_ARG, "NULL argument");
+    finish_assemble_timing(p);
     *out = p->timing;
     API_END
 }
@@ -356,25 +372,23 @@ int igs_assemble(igs_prob p, void* A_out, int64_t ld, int mem, int dtype) {
     }
     IGS_CUDA(cudaSetDevice(p->geom->ctx->device));
     cudaStream_t s = p->geom->ctx->stream;
+    finish_assemble_timing(p);
     p->launches = 0;
     ensure_rules(p);
-    cudaEvent_t e0, e1, e2;
-    IGS_CUDA(cudaEventCreate(&e0)); IGS_CUDA(cudaEventCreate(&e1)); IGS_CUDA(cudaEventCreate(&e2));
-    IGS_CUDA(cudaEventRecord(e0, s));
+    for (cudaEvent_t& e : p->asm_ev)
+        if (!e) IGS_CUDA(cudaEventCreate(&e));
+    IGS_CUDA(cudaEventRecord(p->asm_ev[0], s));
     geometry_nodes(p);
-    IGS_CUDA(cudaEventRecord(e1, s));
+    IGS_CUDA(cudaEventRecord(p->asm_ev[1], s));
     assemble_matrix(p);
-    IGS_CUDA(cudaEventRecord(e2, s));
+    IGS_CUDA(cudaEventRecord(p->asm_ev[2], s));
     p->assembled = 1;
     p->factored = 0;
-    if (A_out) copy_matrix(p, A_out, ld, mem, dtype);
-    IGS_CUDA(cudaEventSynchronize(e2));
-    float g_ms = 0, a_ms = 0;
-    cudaEventElapsedTime(&g_ms, e0, e1);
-    cudaEventElapsedTime(&a_ms, e1, e2);
-    p->timing.geometry_ms = g_ms;
-    p->timing.assemble_ms = a_ms;
-    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
+    p->asm_pending = true;
+    if (A_out) {
+        copy_matrix(p, A_out, ld, mem, dtype);
+        finish_assemble_timing(p);
+    }
     p->timing.kernel_launches = p->launches;
     API_END
 }

@@ -134,6 +134,8 @@ struct igs_prob_s {
     void* d_diagL = nullptr;      // [n][64] factored diagonal blocks of L (tier type)
     void* d_diagLinv = nullptr;   // [n][64] inverses of the diagonal blocks of L (tier type)
     cudaGraphExec_t factor_exec = nullptr;   // captured factorisation (fixed pointers and sizes)
+    cudaEvent_t asm_ev[3] = {nullptr, nullptr, nullptr};   // geometry / assembly events of the last igs_assemble
+    bool asm_pending = false;     // those events not yet read into timing
     int factor_runs = 0;                     // factorisations so far (the graph is captured from the second)
     int* d_tflags = nullptr;      // [n/64] per-block completion flags of the triangular solves
     unsigned long long* d_tpub = nullptr;  // [8][n] published FP32 solution words (value, epoch)

@@ -152,6 +152,7 @@ void run_request(igs_server s, int slot, Ticket& t) {
     int rc = igs_create_geometry(ctx, &g, r.geom_degree, t.knots.data(), (int)t.knots.size(), t.ctrl.data(),
                                  t.w.empty() ? nullptr : t.w.data(), r.n_ctrl, r.closed);
     std::vector<double> key, curve;
+    bool need_asm = false;
     if (rc == IGS_OK) {
         key = {(double)r.degree, (double)r.n_elems, (double)r.n_ref, (double)r.precision, (double)r.closed, g->a, g->b};
         curve = {(double)r.geom_degree, (double)r.closed, (double)t.knots.size(), (double)r.n_ctrl};
@@ -172,7 +173,7 @@ void run_request(igs_server s, int slot, Ticket& t) {
                 g = nullptr;
                 res.curve = curve;
                 t.reuse = IGS_REUSE_RULES;
-                rc = igs_assemble(res.p, nullptr, 0, IGS_MEM_HOST, IGS_F64);
+                need_asm = true;
             }
         } else {
             res.key = key;
@@ -181,7 +182,7 @@ void run_request(igs_server s, int slot, Ticket& t) {
             g = nullptr;
             rc = igs_create_problem(res.g, &res.p, r.degree, r.n_elems, r.n_ref, r.precision);
             if (rc == IGS_OK) rc = igs_build_weighted_rules(res.p);
-            if (rc == IGS_OK) rc = igs_assemble(res.p, nullptr, 0, IGS_MEM_HOST, IGS_F64);
+            need_asm = true;
         }
     }
     igs_prob p = res.p;
@@ -194,6 +195,8 @@ void run_request(igs_server s, int slot, Ticket& t) {
         xy.resize(2 * count);
         rc = igs_rhs_points(p, xy.data(), count, &count);
     }
+    // the assembly runs on the device while the data callback runs here
+    if (rc == IGS_OK && need_asm) rc = igs_assemble(p, nullptr, 0, IGS_MEM_HOST, IGS_F64);
     if (rc != IGS_OK) {
         fail(rc, igs_last_error());
     } else {
