@@ -278,7 +278,7 @@ int igs_destroy_problem(igs_prob p) {
                      p->d_Bt, p->d_W, p->d_G, p->d_Z, p->d_WsT,
                      p->d_WsT32, p->d_WsRow, p->d_WsRow32, p->d_WsToe, p->d_WsToe32,
                      p->d_flag, p->d_geo, p->d_nodes,
-                     p->d_P, p->d_Q, p->d_A, p->d_AT, p->d_F, p->d_As64, p->d_dscale, p->d_diagL, p->d_diagLinv, p->d_tflags, p->d_tpub, p->d_timg,
+                     p->d_P, p->d_Q, p->d_A, p->d_AT, p->d_F, p->d_As64, p->d_dscale, p->d_diagL, p->d_diagLinv, p->d_diagLinv128, p->d_tflags, p->d_tpub, p->d_timg,
                      p->d_beta, p->d_rhs_geo, p->d_rhs_w, p->d_rhs_t, p->d_tree};
     if (p->aux_stream) {
         cudaStreamSynchronize(p->aux_stream);

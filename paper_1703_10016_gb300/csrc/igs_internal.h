@@ -133,6 +133,7 @@ struct igs_prob_s {
     void* d_F = nullptr;          // [n][n] Cholesky factor (tier type): lower = L, upper = L^T
     void* d_diagL = nullptr;      // [n][64] factored diagonal blocks of L (tier type)
     void* d_diagLinv = nullptr;   // [n][64] inverses of the diagonal blocks of L (tier type)
+    float* d_diagLinv128 = nullptr;  // [n][128] inverses of the 128-row diagonal blocks (MIXED tier)
     cudaGraphExec_t factor_exec = nullptr;   // captured factorisation (fixed pointers and sizes)
     cudaEvent_t asm_ev[3] = {nullptr, nullptr, nullptr};   // geometry / assembly events of the last igs_assemble
     bool asm_pending = false;     // those events not yet read into timing

@@ -77,6 +77,8 @@ int64_t estimate_bytes(const igs_request& r) {
     if (r.closed)                                        // double-layer scratch (FP64 slices or treecode moments)
         b += M * igs::kGaussRhs * 28 + (int64_t)r.nrhs * 12 * Nq * 8;
     b += n * 8 * 8;                                      // published solution words
+    if (r.precision == IGS_MIXED && n % 4 == 0 && n >= 256)
+        b += n * 128 * 4;                                // inverses of the 128-row diagonal blocks
     if (r.precision == IGS_MIXED && n >= 4096)           // split operand images of two 512-column outer blocks
         b += (int64_t)2 * 16 * 2 * (4 * ((n + 255) / 256)) * 4096;
     return b + b / 4 + (1 << 20);

@@ -458,6 +458,57 @@ __global__ void __launch_bounds__(256) k_diag_inverse(int n, const T* __restrict
     }
 }
 
+// Inverses of the 128 x 128 diagonal blocks of L from those of their two 64 x 64
+// diagonal blocks (MIXED tier, for 128-row substitution blocks):
+// [L0 0; L10 L1]^-1 = [L0^-1 0; -L1^-1 L10 L0^-1  L1^-1], one CTA per block.
+constexpr size_t kInv128Smem = 3 * (size_t)kNB * (kNB + 1) * sizeof(float);
+__global__ void __launch_bounds__(256) k_diag_inverse128(int n, const float* __restrict__ F,
+                                                         const float* __restrict__ Linv, float* __restrict__ Linv128) {
+    extern __shared__ float sm128[];
+    float (*i0s)[kNB + 1] = (float (*)[kNB + 1])sm128;          // L0^-1
+    float (*i1s)[kNB + 1] = i0s + kNB;                          // L1^-1
+    float (*l10)[kNB + 1] = i1s + kNB;                          // L10, then L10 L0^-1
+    const int b0 = blockIdx.x * 128, bs = min(128, n - b0), tid = threadIdx.x;
+    const int b1 = b0 + kNB, bn1 = bs - kNB;                 // rows of the second 64-block (<= 0: none)
+    for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
+        const int r = idx / kNB, c = idx % kNB;
+        i0s[r][c] = r < bs ? Linv[(size_t)(b0 + r) * kNB + c] : 0.0f;
+        i1s[r][c] = r < bn1 ? Linv[(size_t)(b1 + r) * kNB + c] : 0.0f;
+        l10[r][c] = r < bn1 ? F[(size_t)(b1 + r) * n + b0 + c] : 0.0f;
+    }
+    __syncthreads();
+    // T = L10 L0^-1 into l10 (row by row: thread (r, c-quad))
+    const int r = tid / 4, q = tid % 4;
+    float t[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int c = q + 4 * u;
+        float v = 0.0f;
+        for (int l = c; l < kNB; ++l) v += l10[r][l] * i0s[l][c];
+        t[u] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; ++u) l10[r][q + 4 * u] = t[u];
+    __syncthreads();
+    // X = -L1^-1 T
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int c = q + 4 * u;
+        float v = 0.0f;
+        for (int l = 0; l <= r; ++l) v += i1s[r][l] * l10[l][c];
+        t[u] = -v;
+    }
+    for (int idx = tid; idx < kNB * 128; idx += blockDim.x) {
+        const int rr = idx / 128, c = idx % 128;
+        if (rr < bs) Linv128[(size_t)(b0 + rr) * 128 + c] = c < kNB ? i0s[rr][c] : 0.0f;
+        if (rr < bn1 && c >= kNB) Linv128[(size_t)(b1 + rr) * 128 + c] = i1s[rr][c - kNB];
+    }
+    if (r < bn1)
+#pragma unroll
+        for (int u = 0; u < 16; ++u) Linv128[(size_t)(b1 + r) * 128 + q + 4 * u] = t[u];
+}
+
 // Forward (lower=1: L y = b) or backward (lower=0: L^T x = y, U = L^T in the
 // upper triangle) substitution for NR vectors, one CTA of 1024 threads, by
 // 64-row blocks in solve order ("right-looking"): the block is solved with the
@@ -742,9 +793,8 @@ __global__ void k_wait_probe(const unsigned long long* w, unsigned long long ns,
 // to kTrsvLd floats: the four column phases of eight rows hit distinct banks).
 // A row of F must start on 16 bytes (n % 4 == 0); otherwise (ASYNC = false)
 // the next tile is held in registers.
-constexpr int kTrsvStages = 6;
-constexpr int kTrsvLd = kNB + 4;
-constexpr size_t kTrsvSmem = (size_t)kTrsvStages * kNB * kTrsvLd * sizeof(float);
+__host__ __device__ constexpr int trsv_stages(int RB) { return RB == 64 ? 6 : 3; }
+constexpr size_t trsv_smem(int RB) { return (size_t)trsv_stages(RB) * RB * (RB + 4) * sizeof(float); }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -754,72 +804,72 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int NR, bool ASYNC>
-__global__ void __launch_bounds__(256) k_trsv_pk(int n, const float* __restrict__ F, const float* __restrict__ Linv,
+template <int NR, bool ASYNC, int RB>
+__global__ void __launch_bounds__(4 * RB) k_trsv_pk(int n, const float* __restrict__ F, const float* __restrict__ Linv,
                                                  float* __restrict__ X, int lower, unsigned long long* pub,
                                                  int epoch, int* __restrict__ err) {
-    __shared__ float acc[NR][kNB];
-    __shared__ float yin[NR][kNB];
-    extern __shared__ __align__(16) float ring[];       // [kTrsvStages][kNB][kTrsvLd] (ASYNC)
+    __shared__ float acc[NR][RB];
+    __shared__ float yin[NR][RB];
+    extern __shared__ __align__(16) float ring[];       // [trsv_stages(RB)][RB][RB + 4] (ASYNC)
     const int tid = threadIdx.x;
-    const int nblk = (n + kNB - 1) / kNB;
+    const int nblk = (n + RB - 1) / RB;
     const int i = tid / 4, part = tid % 4;          // row of the block, column phase
     const unsigned long long tag = (unsigned long long)(unsigned)epoch << 32;
     for (int J = blockIdx.x; J < nblk; J += gridDim.x) {
         const int blk = lower ? J : nblk - 1 - J;
-        const int b0 = blk * kNB, bn = min(kNB, n - b0);
+        const int b0 = blk * RB, bn = min(RB, n - b0);
         // this thread's slice of the inverted diagonal block, fetched before any wait:
         // row i (lower) or column i (upper), entries l = part + 4 m
-        float lv[kNB / 4];
+        float lv[RB / 4];
 #pragma unroll
-        for (int m = 0; m < kNB / 4; ++m) {
+        for (int m = 0; m < RB / 4; ++m) {
             const int l = part + 4 * m;
-            if (lower) lv[m] = (i < bn) ? Linv[(size_t)(b0 + i) * kNB + l] : 0.0f;
-            else lv[m] = (l < bn && i < bn) ? Linv[(size_t)(b0 + l) * kNB + i] : 0.0f;
+            if (lower) lv[m] = (i < bn) ? Linv[(size_t)(b0 + i) * RB + l] : 0.0f;
+            else lv[m] = (l < bn && i < bn) ? Linv[(size_t)(b0 + l) * RB + i] : 0.0f;
         }
-        for (int idx = tid; idx < NR * kNB; idx += blockDim.x) {
-            const int k = idx / kNB, r = idx % kNB;
+        for (int idx = tid; idx < NR * RB; idx += blockDim.x) {
+            const int k = idx / RB, r = idx % RB;
             acc[k][r] = (r < bn) ? X[(size_t)k * n + b0 + r] : 0.0f;
         }
         const int ndep = lower ? blk : nblk - 1 - blk;
-        float fr[kNB / 4];                          // F[b0 + i][d0 + part + 4 m] of the next dependency
+        float fr[RB / 4];                          // F[b0 + i][d0 + part + 4 m] of the next dependency
         auto fetch = [&](int q) {                   // register path
             const int D = lower ? q : nblk - 1 - q;
-            const int d0 = D * kNB, dn = min(kNB, n - d0);
+            const int d0 = D * RB, dn = min(RB, n - d0);
 #pragma unroll
-            for (int m = 0; m < kNB / 4; ++m) {
+            for (int m = 0; m < RB / 4; ++m) {
                 const int c = part + 4 * m;
                 fr[m] = (i < bn && c < dn) ? F[(size_t)(b0 + i) * n + d0 + c] : 0.0f;
             }
         };
-        auto issue = [&](int q) {                   // ring path: tile q into stage q % kTrsvStages
+        auto issue = [&](int q) {                   // ring path: tile q into stage q % trsv_stages(RB)
             if (q < ndep) {
                 const int D = lower ? q : nblk - 1 - q;
-                const int d0 = D * kNB, dn = min(kNB, n - d0);
-                float* st = ring + (size_t)(q % kTrsvStages) * kNB * kTrsvLd;
+                const int d0 = D * RB, dn = min(RB, n - d0);
+                float* st = ring + (size_t)(q % trsv_stages(RB)) * RB * (RB + 4);
 #pragma unroll
-                for (int u = 0; u < kNB * kNB / 4 / 256; ++u) {
-                    const int ch = tid + 256 * u, row = ch / (kNB / 4), c4 = 4 * (ch % (kNB / 4));
+                for (int u = 0; u < RB / 16; ++u) {
+                    const int ch = tid + 4 * RB * u, row = ch / (RB / 4), c4 = 4 * (ch % (RB / 4));
                     const bool ok = row < bn && c4 < dn;
-                    cp_async16(st + row * kTrsvLd + c4, ok ? F + (size_t)(b0 + row) * n + d0 + c4 : F, ok ? 16 : 0);
+                    cp_async16(st + row * (RB + 4) + c4, ok ? F + (size_t)(b0 + row) * n + d0 + c4 : F, ok ? 16 : 0);
                 }
             }
             cp_async_commit();                      // empty groups keep the count uniform
         };
         if (ASYNC) {
 #pragma unroll
-            for (int q = 0; q < kTrsvStages - 1; ++q) issue(q);
+            for (int q = 0; q < trsv_stages(RB) - 1; ++q) issue(q);
         } else if (ndep > 0) {
             fetch(0);
         }
         __syncthreads();
         for (int q = 0; q < ndep; ++q) {
             const int D = lower ? q : nblk - 1 - q;
-            const int d0 = D * kNB, dn = min(kNB, n - d0);
-            if (ASYNC) issue(q + kTrsvStages - 1);
+            const int d0 = D * RB, dn = min(RB, n - d0);
+            if (ASYNC) issue(q + trsv_stages(RB) - 1);
             int bad = 0;
-            for (int idx = tid; idx < NR * kNB; idx += blockDim.x) {
-                const int k = idx / kNB, c = idx % kNB;
+            for (int idx = tid; idx < NR * RB; idx += blockDim.x) {
+                const int k = idx / RB, c = idx % RB;
                 float y = 0.0f;
                 if (c < dn) {
                     unsigned long long v = 0;
@@ -828,16 +878,16 @@ __global__ void __launch_bounds__(256) k_trsv_pk(int n, const float* __restrict_
                 }
                 yin[k][c] = y;
             }
-            if (ASYNC) cp_async_wait<kTrsvStages - 1>();    // tile q has landed (this thread's part)
+            if (ASYNC) cp_async_wait<trsv_stages(RB) - 1>();    // tile q has landed (this thread's part)
             if (__syncthreads_or(bad)) {
                 if (ASYNC) cp_async_wait<0>();
                 if (tid == 0) atomicOr(err, 1);
                 return;
             }
             if (ASYNC) {
-                const float* row = ring + (size_t)(q % kTrsvStages) * kNB * kTrsvLd + i * kTrsvLd;
+                const float* row = ring + (size_t)(q % trsv_stages(RB)) * RB * (RB + 4) + i * (RB + 4);
 #pragma unroll
-                for (int m = 0; m < kNB / 4; ++m) fr[m] = row[part + 4 * m];
+                for (int m = 0; m < RB / 4; ++m) fr[m] = row[part + 4 * m];
             }
             // acc[k][i] -= sum_c F[b0+i][d0+c] yin[k][c]  (four threads per row)
             float sk[NR];
@@ -845,7 +895,7 @@ __global__ void __launch_bounds__(256) k_trsv_pk(int n, const float* __restrict_
             for (int k = 0; k < NR; ++k) {
                 float v = 0.0f;
 #pragma unroll
-                for (int m = 0; m < kNB / 4; ++m) v += fr[m] * yin[k][part + 4 * m];
+                for (int m = 0; m < RB / 4; ++m) v += fr[m] * yin[k][part + 4 * m];
                 sk[k] = v;
             }
             if (!ASYNC && q + 1 < ndep) fetch(q + 1);
@@ -864,7 +914,7 @@ __global__ void __launch_bounds__(256) k_trsv_pk(int n, const float* __restrict_
         for (int k = 0; k < NR; ++k) {
             float v = 0.0f;
 #pragma unroll
-            for (int m = 0; m < kNB / 4; ++m) v += lv[m] * acc[k][part + 4 * m];
+            for (int m = 0; m < RB / 4; ++m) v += lv[m] * acc[k][part + 4 * m];
             v += __shfl_xor_sync(0xffffffffu, v, 1);
             v += __shfl_xor_sync(0xffffffffu, v, 2);
             if (part == 0 && i < bn) {
@@ -876,39 +926,48 @@ __global__ void __launch_bounds__(256) k_trsv_pk(int n, const float* __restrict_
     }
 }
 
-template <int NR>
-static void pk_launch(int n, const float* F, const float* Linv, float* X, int lower, unsigned long long* pub,
-                      int epoch, int* err, cudaStream_t s) {
-    const bool async = (n % 4) == 0;
-    static int max_blocks[2] = {-1, -1};          // co-resident CTAs of each instantiation
-    auto kern = async ? k_trsv_pk<NR, true> : k_trsv_pk<NR, false>;
-    const size_t smem = async ? kTrsvSmem : 0;
-    if (max_blocks[async] < 0) {
+template <int NR, bool ASYNC, int RB>
+static void pk_launch_rb(int n, const float* F, const float* Linv, float* X, int lower, unsigned long long* pub,
+                         int epoch, int* err, cudaStream_t s) {
+    static int max_blocks = -1;                   // co-resident CTAs of this instantiation
+    auto kern = k_trsv_pk<NR, ASYNC, RB>;
+    const size_t smem = ASYNC ? trsv_smem(RB) : 0;
+    if (max_blocks < 0) {
         int dev = 0, sms = 0, per = 0;
         IGS_CUDA(cudaGetDevice(&dev));
         IGS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        if (async) ensure_dyn_smem((const void*)kern, smem);
-        IGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem));
-        max_blocks[async] = sms * per;
+        if (ASYNC) ensure_dyn_smem((const void*)kern, smem);
+        IGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 4 * RB, smem));
+        max_blocks = sms * per;
     }
-    const int nblk = (n + kNB - 1) / kNB;
-    const int grid = std::max(1, std::min(nblk, max_blocks[async]));
+    const int nblk = (n + RB - 1) / RB;
+    const int grid = std::max(1, std::min(nblk, max_blocks));
     void* args[] = {(void*)&n, (void*)&F, (void*)&Linv, (void*)&X, (void*)&lower, (void*)&pub, (void*)&epoch,
                     (void*)&err};
-    IGS_CUDA(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(256), args, smem, s));
+    IGS_CUDA(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(4 * RB), args, smem, s));
 }
 
-static void launch_trsv_pk(int n, const float* F, const float* Linv, float* X, int nrhs, int lower,
-                           unsigned long long* pub, int epoch, int* err, cudaStream_t s) {
+// 128-row blocks (with the inverses of the 128 x 128 diagonal blocks) where a
+// row of F starts on 16 bytes, else 64-row blocks
+template <int NR>
+static void pk_launch(int n, const float* F, const float* Linv, const float* Linv128, float* X, int lower,
+                      unsigned long long* pub, int epoch, int* err, cudaStream_t s) {
+    if ((n % 4) == 0 && Linv128) pk_launch_rb<NR, true, 128>(n, F, Linv128, X, lower, pub, epoch, err, s);
+    else if ((n % 4) == 0) pk_launch_rb<NR, true, 64>(n, F, Linv, X, lower, pub, epoch, err, s);
+    else pk_launch_rb<NR, false, 64>(n, F, Linv, X, lower, pub, epoch, err, s);
+}
+
+static void launch_trsv_pk(int n, const float* F, const float* Linv, const float* Linv128, float* X, int nrhs,
+                           int lower, unsigned long long* pub, int epoch, int* err, cudaStream_t s) {
     switch (nrhs) {
-        case 1: pk_launch<1>(n, F, Linv, X, lower, pub, epoch, err, s); break;
-        case 2: pk_launch<2>(n, F, Linv, X, lower, pub, epoch, err, s); break;
-        case 3: pk_launch<3>(n, F, Linv, X, lower, pub, epoch, err, s); break;
-        case 4: pk_launch<4>(n, F, Linv, X, lower, pub, epoch, err, s); break;
-        case 5: pk_launch<5>(n, F, Linv, X, lower, pub, epoch, err, s); break;
-        case 6: pk_launch<6>(n, F, Linv, X, lower, pub, epoch, err, s); break;
-        case 7: pk_launch<7>(n, F, Linv, X, lower, pub, epoch, err, s); break;
-        default: pk_launch<8>(n, F, Linv, X, lower, pub, epoch, err, s); break;
+        case 1: pk_launch<1>(n, F, Linv, Linv128, X, lower, pub, epoch, err, s); break;
+        case 2: pk_launch<2>(n, F, Linv, Linv128, X, lower, pub, epoch, err, s); break;
+        case 3: pk_launch<3>(n, F, Linv, Linv128, X, lower, pub, epoch, err, s); break;
+        case 4: pk_launch<4>(n, F, Linv, Linv128, X, lower, pub, epoch, err, s); break;
+        case 5: pk_launch<5>(n, F, Linv, Linv128, X, lower, pub, epoch, err, s); break;
+        case 6: pk_launch<6>(n, F, Linv, Linv128, X, lower, pub, epoch, err, s); break;
+        case 7: pk_launch<7>(n, F, Linv, Linv128, X, lower, pub, epoch, err, s); break;
+        default: pk_launch<8>(n, F, Linv, Linv128, X, lower, pub, epoch, err, s); break;
     }
 }
 
@@ -1651,9 +1710,19 @@ static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent
         IGS_CUDA(cudaEventRecord(evJ, s1));
         IGS_CUDA(cudaStreamWaitEvent(s0, evJ, 0));
     }
+    // the inverses of the diagonal blocks (from diagL and the strictly lower part
+    // of F) on the second stream, beside the mirror (diagonal blocks and upper
+    // triangle of F) on the first
+    IGS_CUDA(cudaEventRecord(evP, s0));
+    IGS_CUDA(cudaStreamWaitEvent(s1, evP, 0));
+    k_diag_inverse<T><<<(n + kNB - 1) / kNB, 256, 0, s1>>>(n, (const T*)p->d_diagL, (T*)p->d_diagLinv);
+    if (std::is_same<T, float>::value && p->d_diagLinv128)
+        k_diag_inverse128<<<(n + 127) / 128, 256, kInv128Smem, s1>>>(n, (const float*)p->d_F,
+                                                                   (const float*)p->d_diagLinv, p->d_diagLinv128);
     const int nft = (n + kTT - 1) / kTT;
     k_finalize<T><<<nft * (nft + 1) / 2, 256, 0, s0>>>(n, F, (const T*)p->d_diagL);
-    k_diag_inverse<T><<<(n + kNB - 1) / kNB, 256, 0, s0>>>(n, (const T*)p->d_diagL, (T*)p->d_diagLinv);
+    IGS_CUDA(cudaEventRecord(evJ, s1));
+    IGS_CUDA(cudaStreamWaitEvent(s0, evJ, 0));
     IGS_CUDA(cudaGetLastError());
 }
 
@@ -1765,9 +1834,17 @@ static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, c
         IGS_CUDA(cudaEventRecord(evJ, s1));
         IGS_CUDA(cudaStreamWaitEvent(s0, evJ, 0));
     }
+    // inverses beside the mirror, as in the unblocked factorisation
+    IGS_CUDA(cudaEventRecord(evP, s0));
+    IGS_CUDA(cudaStreamWaitEvent(s1, evP, 0));
+    k_diag_inverse<float><<<(n + kNB - 1) / kNB, 256, 0, s1>>>(n, (const float*)p->d_diagL, (float*)p->d_diagLinv);
+    if (p->d_diagLinv128)
+        k_diag_inverse128<<<(n + 127) / 128, 256, kInv128Smem, s1>>>(n, (const float*)p->d_F,
+                                                                   (const float*)p->d_diagLinv, p->d_diagLinv128);
     const int nft = (n + kTT - 1) / kTT;
     k_finalize<float><<<nft * (nft + 1) / 2, 256, 0, s0>>>(n, F, (const float*)p->d_diagL);
-    k_diag_inverse<float><<<(n + kNB - 1) / kNB, 256, 0, s0>>>(n, (const float*)p->d_diagL, (float*)p->d_diagLinv);
+    IGS_CUDA(cudaEventRecord(evJ, s1));
+    IGS_CUDA(cudaStreamWaitEvent(s0, evJ, 0));
     IGS_CUDA(cudaGetLastError());
 }
 
@@ -1843,6 +1920,7 @@ static void factor(igs_prob p, cudaStream_t s) {
     ensure_dyn_smem((const void*)k_syrk<T>, (size_t)syrk_smem<T>());
     ensure_dyn_smem((const void*)k_syrk_tc, tc::smem_bytes());
     ensure_dyn_smem((const void*)k_syrk_tcp, tcp_smem_bytes());
+    ensure_dyn_smem((const void*)k_diag_inverse128, kInv128Smem);
     const bool blocked = std::is_same<T, float>::value && n >= kBlockedMinN;
     if (!p->factor_exec && p->factor_runs == 0) {
         // first factorisation of this problem: issue the launch sequence directly
@@ -1872,7 +1950,7 @@ static void factor(igs_prob p, cudaStream_t s) {
         IGS_CUDA(cudaGraphLaunch(p->factor_exec, s));
     }
     p->factor_runs++;
-    p->launches += blocked ? factor_launches_blocked(n) : factor_launches(n);
+    p->launches += (blocked ? factor_launches_blocked(n) : factor_launches(n)) + (p->d_diagLinv128 ? 1 : 0);
     int flag = 0;
     IGS_CUDA(cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     IGS_CUDA(cudaStreamSynchronize(s));
@@ -1900,6 +1978,8 @@ static void prepare_factor(igs_prob p, cudaStream_t s) {
         IGS_CUDA(cudaGetDevice(&dev));
         IGS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         p->coop_ok = coop != 0;
+        if (std::is_same<T, float>::value && p->coop_ok && (n % 4) == 0 && n >= 256)
+            p->d_diagLinv128 = (float*)dev_alloc(p, sizeof(float) * (size_t)n * 128);
         // the factor graph captures these pointers: allocate before capture, keep for the problem's life
         IGS_CUDA(cudaStreamSynchronize(s));
     }
@@ -1948,9 +2028,11 @@ static void refine(igs_prob p, double* d_beta, int nrhs, double* d_alpha, double
         const float* dsc = std::is_same<T, float>::value ? p->d_dscale : nullptr;
         k_cast_in<T><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, src, d_x, scale, n, dsc);
         if (std::is_same<T, float>::value && p->coop_ok) {
-            launch_trsv_pk(n, (const float*)p->d_F, (const float*)p->d_diagLinv, (float*)d_x, nrhs, 1, p->d_tpub,
+            launch_trsv_pk(n, (const float*)p->d_F, (const float*)p->d_diagLinv, p->d_diagLinv128, (float*)d_x, nrhs, 1,
+                           p->d_tpub,
                            ++p->tepoch, p->d_flag, s);
-            launch_trsv_pk(n, (const float*)p->d_F, (const float*)p->d_diagLinv, (float*)d_x, nrhs, 0, p->d_tpub,
+            launch_trsv_pk(n, (const float*)p->d_F, (const float*)p->d_diagLinv, p->d_diagLinv128, (float*)d_x, nrhs, 0,
+                           p->d_tpub,
                            ++p->tepoch, p->d_flag, s);
         } else if (p->coop_ok) {
             launch_trsv_coop<T>(n, (const T*)p->d_F, (const T*)p->d_diagLinv, d_x, nrhs, 1, p->d_tflags,
