@@ -139,9 +139,11 @@ __global__ void __launch_bounds__(256) k_symmetrize_lower_f(int n, const float* 
 // communication) and solves its own row against it; (2) rank-8 update of the
 // columns to the right.
 // A non-positive pivot sets *flag and is replaced by 1.
-constexpr int kPanelThreads = 512;
-constexpr int kPanelRows = 2 * kNB;                        // diagonal block + 64 rows below
-constexpr int kPanelParts = kPanelThreads / kPanelRows;   // threads per row in the update
+// NS > 1 (FP32): each CTA b >= 1 takes 64 NS rows below the diagonal block
+// (PARTS threads per row in the update), so that a tall panel runs in fewer
+// waves of CTAs.
+__host__ __device__ constexpr int panel_rows(int ns) { return (1 + ns) * 64; }   // diagonal block + slices
+__host__ __device__ constexpr int panel_threads(int ns, int parts) { return parts * panel_rows(ns); }
 constexpr int kPB = 8;                                     // inner block width
 
 // Programmatic dependent launch: a kernel of the panel chain lets the next
@@ -154,19 +156,20 @@ template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 
-template <typename T>
-__global__ void __launch_bounds__(kPanelThreads) k_panel(int n, T* __restrict__ F, int k0, int kb,
-                                                         T* __restrict__ diagL, int* __restrict__ flag) {
+template <typename T, int NS, int PARTS>
+__global__ void __launch_bounds__(panel_threads(NS, PARTS)) k_panel(int n, T* __restrict__ F, int k0, int kb,
+                                                                    T* __restrict__ diagL, int* __restrict__ flag) {
+    constexpr int kPanelRows = panel_rows(NS), kPanelThreads = panel_threads(NS, PARTS), kPanelParts = PARTS;
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T (*P)[kPB] = (T (*)[kPB])smem_raw;                     // current 8 columns of L, one row of 8 per row
-    T (*a)[kNB + 1] = (T (*)[kNB + 1])(P + kPanelRows);    // rows 0..63 diagonal block, 64..127 rows below
+    T (*a)[kNB + 1] = (T (*)[kNB + 1])(P + kPanelRows);    // rows 0..63 diagonal block, then the slice
     const int tid = threadIdx.x;
-    const int r0 = k0 + blockIdx.x * kNB;
-    const int nb = blockIdx.x == 0 ? 0 : min(kNB, n - r0);
+    const int r0 = k0 + kNB + ((int)blockIdx.x - 1) * NS * kNB;
+    const int nb = blockIdx.x == 0 ? 0 : min(NS * kNB, n - r0);
     const int rows = kNB + nb;
     // all loads in flight before the first store
     constexpr int kPer = kPanelRows * kNB / kPanelThreads;
@@ -1163,7 +1166,7 @@ __global__ void k_accum(int cnt, const T* __restrict__ dx, double* __restrict__ 
 }
 
 template <typename T>
-static size_t panel_smem() { return (kPanelRows * kPB + kPanelRows * (kNB + 1)) * sizeof(T); }
+static size_t panel_smem(int ns) { return (panel_rows(ns) * kPB + panel_rows(ns) * (kNB + 1)) * sizeof(T); }
 template <typename T>
 static size_t syrk_smem() { return 2 * kST * syrk_ld<T>() * sizeof(T); }
 
@@ -1652,6 +1655,35 @@ static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
     launch_chain(true, kern, grid, block, smem, s, args...);
 }
 
+// Slices per CTA of a panel launch with `below` rows under the diagonal block:
+// one 64-row slice, or more where one-slice CTAs would not all fit at once.
+static int panel_ns(int below, int sms) {
+    const int g1 = 1 + (below + kNB - 1) / kNB;
+    return g1 > sms ? 2 : 1;
+}
+
+template <typename T, int NS, int PARTS>
+static void launch_panel_ns(igs_prob p, int n, T* F, int k0, int kb, int below, cudaStream_t s) {
+    launch_pdl(k_panel<T, NS, PARTS>, dim3(1 + (below + NS * kNB - 1) / (NS * kNB)), dim3(panel_threads(NS, PARTS)),
+               panel_smem<T>(NS), s, n, F, k0, kb, (T*)p->d_diagL, p->d_flag);
+}
+
+// Panel step at column k0: CTA 0 the diagonal block, the others the rows below.
+template <typename T>
+static void launch_panel(igs_prob p, int n, T* F, int k0, int kb, cudaStream_t s) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        IGS_CUDA(cudaGetDevice(&dev));
+        IGS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int below = std::max(0, n - k0 - kNB);
+    if constexpr (std::is_same<T, float>::value) {
+        if (panel_ns(below, sms) == 2) return launch_panel_ns<T, 2, 4>(p, n, F, k0, kb, below, s);
+    }
+    launch_panel_ns<T, 1, 4>(p, n, F, k0, kb, below, s);
+}
+
 template <typename T>
 static void launch_update(igs_prob p, int n, T* F, int k0, int kb, int mode, cudaStream_t s);
 template <>
@@ -1686,9 +1718,7 @@ static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent
     bool pending = false, forked = false;
     for (int k0 = 0; k0 < n; k0 += kNB) {
         const int kb = std::min(kNB, n - k0);
-        const int rows = n - k0;
-        launch_pdl(k_panel<T>, dim3((rows + kNB - 1) / kNB), dim3(kPanelThreads), panel_smem<T>(), s0, n, F, k0, kb,
-                   (T*)p->d_diagL, p->d_flag);
+        launch_panel<T>(p, n, F, k0, kb, s0);
         const int rem = n - k0 - kb;
         if (rem <= 0) continue;
         const int nt = (rem + kST - 1) / kST;
@@ -1787,9 +1817,7 @@ static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, c
         bool side = false;                                            // a side update of this block is pending
         for (int k0 = K0; k0 < K0 + kbo; k0 += kNB) {
             const int kb = std::min(kNB, n - k0);
-            const int rows = n - k0;
-            launch_pdl(k_panel<float>, dim3((rows + kNB - 1) / kNB), dim3(kPanelThreads), panel_smem<float>(), s0, n,
-                       F, k0, kb, (float*)p->d_diagL, p->d_flag);
+            launch_panel<float>(p, n, F, k0, kb, s0);
             const int inner = (K0 + kbo - (k0 + kb) + kST - 1) / kST;   // column tiles left in this block
             if (inner <= 0) continue;
             const int nt = (n - k0 - kb + kST - 1) / kST;
@@ -1916,7 +1944,8 @@ static void capture_factor(igs_prob p, bool blocked) {
 template <typename T>
 static void factor(igs_prob p, cudaStream_t s) {
     const int n = p->plan.n;
-    ensure_dyn_smem((const void*)k_panel<T>, (size_t)panel_smem<T>());
+    ensure_dyn_smem((const void*)k_panel<T, 1, 4>, panel_smem<T>(1));
+    if constexpr (std::is_same<T, float>::value) ensure_dyn_smem((const void*)k_panel<T, 2, 4>, panel_smem<T>(2));
     ensure_dyn_smem((const void*)k_syrk<T>, (size_t)syrk_smem<T>());
     ensure_dyn_smem((const void*)k_syrk_tc, tc::smem_bytes());
     ensure_dyn_smem((const void*)k_syrk_tcp, tcp_smem_bytes());
