@@ -142,6 +142,11 @@ __global__ void __launch_bounds__(256) k_symmetrize_lower_f(int n, const float* 
 // NS > 1 (FP32): each CTA b >= 1 takes 64 NS rows below the diagonal block
 // (PARTS threads per row in the update), so that a tall panel runs in fewer
 // waves of CTAs.
+// FUSE (FP32, kp >= 0): the CTA first applies the previous panel's update to
+// its rows of this column block, A[i][k0 + l] -= sum_m L[i][kp + m]
+// L[k0 + l][kp + m] (the right-looking update of the next column block, here
+// instead of a launch of its own on the panel chain), from the previous
+// panel's 64 columns of the same rows staged in shared memory.
 __host__ __device__ constexpr int panel_rows(int ns) { return (1 + ns) * 64; }   // diagonal block + slices
 __host__ __device__ constexpr int panel_threads(int ns, int parts) { return parts * panel_rows(ns); }
 constexpr int kPB = 8;                                     // inner block width
@@ -156,24 +161,27 @@ template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 
-template <typename T, int NS, int PARTS>
-__global__ void __launch_bounds__(panel_threads(NS, PARTS)) k_panel(int n, T* __restrict__ F, int k0, int kb,
+template <typename T, int NS, int PARTS, bool FUSE>
+__global__ void __launch_bounds__(panel_threads(NS, PARTS)) k_panel(int n, T* __restrict__ F, int k0, int kb, int kp,
                                                                     T* __restrict__ diagL, int* __restrict__ flag) {
     constexpr int kPanelRows = panel_rows(NS), kPanelThreads = panel_threads(NS, PARTS), kPanelParts = PARTS;
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
+    constexpr int LP = kNB + 16 / (int)sizeof(T);          // row stride of the staged previous panel
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T (*P)[kPB] = (T (*)[kPB])smem_raw;                     // current 8 columns of L, one row of 8 per row
     T (*a)[kNB + 1] = (T (*)[kNB + 1])(P + kPanelRows);    // rows 0..63 diagonal block, then the slice
+    T (*Lp)[LP] = (T (*)[LP])(a + kPanelRows);              // FUSE: the same rows of the previous panel
     const int tid = threadIdx.x;
     const int r0 = k0 + kNB + ((int)blockIdx.x - 1) * NS * kNB;
     const int nb = blockIdx.x == 0 ? 0 : min(NS * kNB, n - r0);
     const int rows = kNB + nb;
+    const bool fuse = FUSE && kp >= 0;
     // all loads in flight before the first store
     constexpr int kPer = kPanelRows * kNB / kPanelThreads;
-    T v[kPer];
+    T v[kPer], w[FUSE ? kPer : 1];
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
         const int idx = tid + q * kPanelThreads, i = idx / kNB, l = idx % kNB;
@@ -183,13 +191,49 @@ __global__ void __launch_bounds__(panel_threads(NS, PARTS)) k_panel(int n, T* __
         } else {
             v[q] = (i < rows) ? F[(size_t)(r0 + i - kNB) * n + k0 + l] : (T)0;
         }
+        if (FUSE && fuse) {
+            const int row = i < kNB ? (i < kb ? k0 + i : -1) : (i < rows ? r0 + i - kNB : -1);
+            w[FUSE ? q : 0] = row >= 0 ? F[(size_t)row * n + kp + l] : (T)0;
+        }
     }
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
         const int idx = tid + q * kPanelThreads;
         a[idx / kNB][idx % kNB] = v[q];
+        if (FUSE && fuse) Lp[idx / kNB][idx % kNB] = w[FUSE ? q : 0];
     }
     __syncthreads();
+    if (FUSE && fuse) {
+        // thread (ri, ci): rows ri + RG r (r < RR), columns ci + 16 c (c < 4); a
+        // quarter-warp reads eight distinct staged rows (odd stride in 16-byte
+        // units) or one row (broadcast)
+        constexpr int RG = kPanelThreads / 16, RR = kPanelRows / RG;
+        const int ri = tid / 16, ci = tid % 16;
+        T acc[RR][4];
+#pragma unroll
+        for (int r = 0; r < RR; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = (T)0;
+#pragma unroll 2
+        for (int m0 = 0; m0 < kNB; m0 += VN) {
+            V xr[RR], xc[4];
+#pragma unroll
+            for (int r = 0; r < RR; ++r) xr[r] = *(const V*)&Lp[ri + RG * r][m0];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) xc[c] = *(const V*)&Lp[ci + 16 * c][m0];
+#pragma unroll
+            for (int u = 0; u < VN; ++u)
+#pragma unroll
+                for (int r = 0; r < RR; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[r][c] += vget<T>(xr[r], u) * vget<T>(xc[c], u);
+        }
+#pragma unroll
+        for (int r = 0; r < RR; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) a[ri + RG * r][ci + 16 * c] -= acc[r][c];
+        __syncthreads();
+    }
     const int i = tid % kPanelRows, part = tid / kPanelRows;
 #pragma unroll 1
     for (int c0 = 0; c0 < kNB; c0 += kPB) {
@@ -1166,7 +1210,10 @@ __global__ void k_accum(int cnt, const T* __restrict__ dx, double* __restrict__ 
 }
 
 template <typename T>
-static size_t panel_smem(int ns) { return (panel_rows(ns) * kPB + panel_rows(ns) * (kNB + 1)) * sizeof(T); }
+static size_t panel_smem(int ns, bool fuse) {
+    return (panel_rows(ns) * kPB + panel_rows(ns) * (kNB + 1) + (fuse ? panel_rows(ns) * (kNB + 16 / sizeof(T)) : 0)) *
+           sizeof(T);
+}
 template <typename T>
 static size_t syrk_smem() { return 2 * kST * syrk_ld<T>() * sizeof(T); }
 
@@ -1655,22 +1702,19 @@ static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
     launch_chain(true, kern, grid, block, smem, s, args...);
 }
 
-// Slices per CTA of a panel launch with `below` rows under the diagonal block:
-// one 64-row slice, or more where one-slice CTAs would not all fit at once.
-static int panel_ns(int below, int sms) {
-    const int g1 = 1 + (below + kNB - 1) / kNB;
-    return g1 > sms ? 2 : 1;
+// Panel step at column k0: CTA 0 the diagonal block, the others the rows
+// below, 64 per CTA or, where those CTAs would not all fit at once (FP32),
+// 192 per CTA.  FP32 panels apply the update by the previous panel kp of
+// their own column block first (kp < 0: none).
+template <typename T, int NS, int PARTS, bool FUSE>
+static void launch_panel_ns(igs_prob p, int n, T* F, int k0, int kb, int kp, int below, cudaStream_t s) {
+    launch_pdl(k_panel<T, NS, PARTS, FUSE>, dim3(1 + (below + NS * kNB - 1) / (NS * kNB)),
+               dim3(panel_threads(NS, PARTS)), panel_smem<T>(NS, FUSE), s, n, F, k0, kb, kp, (T*)p->d_diagL,
+               p->d_flag);
 }
 
-template <typename T, int NS, int PARTS>
-static void launch_panel_ns(igs_prob p, int n, T* F, int k0, int kb, int below, cudaStream_t s) {
-    launch_pdl(k_panel<T, NS, PARTS>, dim3(1 + (below + NS * kNB - 1) / (NS * kNB)), dim3(panel_threads(NS, PARTS)),
-               panel_smem<T>(NS), s, n, F, k0, kb, (T*)p->d_diagL, p->d_flag);
-}
-
-// Panel step at column k0: CTA 0 the diagonal block, the others the rows below.
 template <typename T>
-static void launch_panel(igs_prob p, int n, T* F, int k0, int kb, cudaStream_t s) {
+static void launch_panel(igs_prob p, int n, T* F, int k0, int kb, int kp, cudaStream_t s) {
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -1679,9 +1723,11 @@ static void launch_panel(igs_prob p, int n, T* F, int k0, int kb, cudaStream_t s
     }
     const int below = std::max(0, n - k0 - kNB);
     if constexpr (std::is_same<T, float>::value) {
-        if (panel_ns(below, sms) == 2) return launch_panel_ns<T, 2, 4>(p, n, F, k0, kb, below, s);
+        if (1 + (below + kNB - 1) / kNB > sms) return launch_panel_ns<T, 3, 2, true>(p, n, F, k0, kb, kp, below, s);
+        return launch_panel_ns<T, 1, 4, true>(p, n, F, k0, kb, kp, below, s);
+    } else {
+        launch_panel_ns<T, 1, 4, false>(p, n, F, k0, kb, -1, below, s);
     }
-    launch_panel_ns<T, 1, 4>(p, n, F, k0, kb, below, s);
 }
 
 template <typename T>
@@ -1705,10 +1751,11 @@ void launch_update<float>(igs_prob p, int n, float* F, int k0, int kb, int mode,
 }
 
 // One factorisation as a two-stream launch sequence (captured into a graph):
-// s0 carries panel k, the update of column block k+1 and panel k+1; s1 the
-// rest of the update of step k, concurrent with panel k+1.  Ordering: the
-// first-column update of step k waits for the rest-update of step k-1 (both
-// touch column block k+1); the rest-update of step k waits for panel k.
+// s0 carries panel k, the update of column block k+1 and panel k+1 (FP32: the
+// panel k+1 applies that update itself); s1 the rest of the update of step k,
+// concurrent with panel k+1.  Ordering: the first-column update of step k
+// (FP32: panel k+1) waits for the rest-update of step k-1 (both touch column
+// block k+1); the rest-update of step k waits for panel k.
 template <typename T>
 static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent_t evP, cudaEvent_t evB,
                          cudaEvent_t evJ) {
@@ -1716,9 +1763,32 @@ static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent
     T* F = (T*)p->d_F;
     IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s0));
     bool pending = false, forked = false;
-    for (int k0 = 0; k0 < n; k0 += kNB) {
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32: panel j updates its own column block by panel j - 1; the rest of
+        // step j's update (beyond column block j + 1) on s1, after panel j.  Panel
+        // j waits for the rest-update of step j - 2 (which touched its columns):
+        // the completion events alternate by the parity of j.
+        cudaEvent_t evSide[2] = {evB, evJ};
+        bool side[2] = {false, false};
+        for (int k0 = 0; k0 < n; k0 += kNB) {
+            const int kb = std::min(kNB, n - k0), j = k0 / kNB;
+            if (side[j & 1]) {
+                IGS_CUDA(cudaStreamWaitEvent(s0, evSide[j & 1], 0));
+                side[j & 1] = false;
+            }
+            launch_panel<T>(p, n, F, k0, kb, k0 > 0 ? k0 - kNB : -1, s0);
+            if (n - k0 - kb <= kST) continue;
+            IGS_CUDA(cudaEventRecord(evP, s0));
+            IGS_CUDA(cudaStreamWaitEvent(s1, evP, 0));
+            forked = true;
+            launch_update<T>(p, n, F, k0, kb, 2, s1);
+            IGS_CUDA(cudaEventRecord(evSide[j & 1], s1));
+            side[j & 1] = true;
+        }
+    }
+    for (int k0 = 0; k0 < n && !std::is_same<T, float>::value; k0 += kNB) {
         const int kb = std::min(kNB, n - k0);
-        launch_panel<T>(p, n, F, k0, kb, s0);
+        launch_panel<T>(p, n, F, k0, kb, -1, s0);
         const int rem = n - k0 - kb;
         if (rem <= 0) continue;
         const int nt = (rem + kST - 1) / kST;
@@ -1812,29 +1882,28 @@ static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, c
     float* F = (float*)p->d_F;
     IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s0));
     bool pending = false, forked = false;
+    cudaEvent_t evSide[2] = {evS, evJ};      // in-block side updates by parity (evJ recorded again at the end)
     for (int K0 = 0; K0 < n; K0 += kOB) {
         const int kbo = std::min(kOB, n - K0);
-        bool side = false;                                            // a side update of this block is pending
+        bool side[2] = {false, false};           // side updates of this block pending, by parity of the step
         for (int k0 = K0; k0 < K0 + kbo; k0 += kNB) {
-            const int kb = std::min(kNB, n - k0);
-            launch_panel<float>(p, n, F, k0, kb, s0);
+            const int kb = std::min(kNB, n - k0), j = (k0 - K0) / kNB;
+            // panel j updates its own columns by panel j - 1 of the block, after the
+            // side update of step j - 2 (which touched them; events by parity of j)
+            if (side[j & 1]) {
+                IGS_CUDA(cudaStreamWaitEvent(s0, evSide[j & 1], 0));
+                side[j & 1] = false;
+            }
+            launch_panel<float>(p, n, F, k0, kb, k0 > K0 ? k0 - kNB : -1, s0);
             const int inner = (K0 + kbo - (k0 + kb) + kST - 1) / kST;   // column tiles left in this block
-            if (inner <= 0) continue;
+            if (inner <= 1) continue;
+            // the block's columns beyond the next panel's on the third stream
             const int nt = (n - k0 - kb + kST - 1) / kST;
-            // the next panel's columns on the chain, after the previous panel's side update
-            // (both touch them); the block's later columns on the third stream
-            if (side) {
-                IGS_CUDA(cudaStreamWaitEvent(s0, evS, 0));
-                side = false;
-            }
-            if (inner > 1) IGS_CUDA(cudaEventRecord(evQ, s0));
-            launch_pdl(k_syrk<float>, dim3(nt), dim3(256), syrk_smem<float>(), s0, n, F, k0, kb, 1);
-            if (inner > 1) {
-                IGS_CUDA(cudaStreamWaitEvent(s2, evQ, 0));
-                k_syrk<float><<<dim3(nt, inner - 1), 256, syrk_smem<float>(), s2>>>(n, F, k0, kb, 4);
-                IGS_CUDA(cudaEventRecord(evS, s2));
-                side = true;
-            }
+            IGS_CUDA(cudaEventRecord(evQ, s0));
+            IGS_CUDA(cudaStreamWaitEvent(s2, evQ, 0));
+            k_syrk<float><<<dim3(nt, inner - 1), 256, syrk_smem<float>(), s2>>>(n, F, k0, kb, 4);
+            IGS_CUDA(cudaEventRecord(evSide[j & 1], s2));
+            side[j & 1] = true;
         }
         const int rem = n - K0 - kbo;
         if (rem <= 0) continue;
@@ -1880,20 +1949,19 @@ static int factor_launches_blocked(int n) {
     int c = 2;
     for (int K0 = 0; K0 < n; K0 += kOB) {
         const int kbo = std::min(kOB, n - K0);
-        for (int k0 = K0; k0 < K0 + kbo; k0 += kNB)
-            c += 1 + (k0 + kNB < K0 + kbo ? 1 : 0) + (k0 + 2 * kNB < K0 + kbo ? 1 : 0);
+        for (int k0 = K0; k0 < K0 + kbo; k0 += kNB) c += 1 + (k0 + 2 * kNB < K0 + kbo ? 1 : 0);
         const int rem = n - K0 - kbo;
         if (rem > 0) c += (rem > kOB) ? 3 : 2;
     }
     return c;
 }
 
-static int factor_launches(int n) {
+static int factor_launches(int n, bool fused) {
     int c = 2;
     for (int k0 = 0; k0 < n; k0 += kNB) {
         ++c;
         const int rem = n - k0 - kNB;
-        if (rem > 0) c += (rem > kST) ? 2 : 1;
+        if (rem > 0) c += (rem > kST) ? 2 - fused : 1 - fused;
     }
     return c;
 }
@@ -1944,8 +2012,12 @@ static void capture_factor(igs_prob p, bool blocked) {
 template <typename T>
 static void factor(igs_prob p, cudaStream_t s) {
     const int n = p->plan.n;
-    ensure_dyn_smem((const void*)k_panel<T, 1, 4>, panel_smem<T>(1));
-    if constexpr (std::is_same<T, float>::value) ensure_dyn_smem((const void*)k_panel<T, 2, 4>, panel_smem<T>(2));
+    if constexpr (std::is_same<T, float>::value) {
+        ensure_dyn_smem((const void*)k_panel<T, 1, 4, true>, panel_smem<T>(1, true));
+        ensure_dyn_smem((const void*)k_panel<T, 3, 2, true>, panel_smem<T>(3, true));
+    } else {
+        ensure_dyn_smem((const void*)k_panel<T, 1, 4, false>, panel_smem<T>(1, false));
+    }
     ensure_dyn_smem((const void*)k_syrk<T>, (size_t)syrk_smem<T>());
     ensure_dyn_smem((const void*)k_syrk_tc, tc::smem_bytes());
     ensure_dyn_smem((const void*)k_syrk_tcp, tcp_smem_bytes());
@@ -1979,7 +2051,7 @@ static void factor(igs_prob p, cudaStream_t s) {
         IGS_CUDA(cudaGraphLaunch(p->factor_exec, s));
     }
     p->factor_runs++;
-    p->launches += (blocked ? factor_launches_blocked(n) : factor_launches(n)) + (p->d_diagLinv128 ? 1 : 0);
+    p->launches += (blocked ? factor_launches_blocked(n) : factor_launches(n, std::is_same<T, float>::value)) + (p->d_diagLinv128 ? 1 : 0);
     int flag = 0;
     IGS_CUDA(cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     IGS_CUDA(cudaStreamSynchronize(s));
