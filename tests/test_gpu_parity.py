@@ -321,3 +321,27 @@ def test_blocked_factor_large_n(ctx):
         assert np.linalg.norm(As @ alpha[0] - beta) <= 1e-9 * np.linalg.norm(beta)
     finally:
         p.close()
+
+
+def test_tall_panels_large_n(ctx):
+    """MIXED tier at n = 9800: the first panels have more 64-row slices below
+    their diagonal block than a GB300 has SMs, so they run on 192-row CTAs
+    (9736 rows below the first diagonal block = 50 x 192 + 136, a ragged last
+    CTA; 9800 = 153 x 64 + 8, a ragged last panel), each applying the previous
+    panel's update to its rows first.  The refined solution must satisfy the
+    FP64 system of the assembled matrix, checked on the host."""
+    g = lib()
+    curve = wl.star_curve()
+    n, d, nref = 9800, 3, 1
+    p = Prob(ctx, curve, n, d, nref, g.IGS_MIXED)
+    try:
+        A = p.assemble()
+        xy = g.igs_rhs_points(p.prob)
+        beta = g.igs_build_rhs(p.prob, wl.Harmonic("log").value(xy[:, 0], xy[:, 1])[None, :])[0]
+        alpha, res = g.igs_solve(p.prob)
+        assert res[0] <= 1e-10
+        assert g.igs_problem_timing(p.prob).ir_iterations <= 4
+        r = 0.5 * (A @ alpha[0] + A.T @ alpha[0]) - beta
+        assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(beta)
+    finally:
+        p.close()
