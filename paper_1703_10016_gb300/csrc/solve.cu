@@ -451,11 +451,23 @@ __global__ void __launch_bounds__(256) k_syrk(int n, T* __restrict__ F, int k0, 
 // Diagonal blocks back into F, and U = L^T into the upper triangle: one
 // 64 x 64 tile pair per CTA (tiles align with the 64-wide diagonal blocks),
 // the lower tile read row by row and written transposed through shared memory.
+// Tile columns bj0 .. bj0 + w - 1 (w > 0: grid x over the tile rows from the
+// diagonal down, y over the columns) or all from bj0 on (w = 0: CTAs numbered
+// over that lower triangle of tiles).
 template <typename T>
-__global__ void __launch_bounds__(256) k_finalize(int n, T* __restrict__ F, const T* __restrict__ diagL) {
+__global__ void __launch_bounds__(256) k_finalize(int n, T* __restrict__ F, const T* __restrict__ diagL, int bj0,
+                                                  int w) {
     __shared__ T t[kTT][kTT + 1];
     int bi, bj;
-    tri_decode(blockIdx.x, bi, bj);
+    if (w > 0) {
+        bj = bj0 + (int)blockIdx.y;
+        bi = bj + (int)blockIdx.x;
+        if (bi >= (n + kTT - 1) / kTT) return;
+    } else {
+        tri_decode(blockIdx.x, bi, bj);
+        bi += bj0;
+        bj += bj0;
+    }
     const int i0 = bi * kTT, j0 = bj * kTT;
     const int c = threadIdx.x % kTT, r4 = threadIdx.x / kTT;
     for (int r = r4; r < kTT; r += 4) {
@@ -1820,7 +1832,7 @@ static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent
         k_diag_inverse128<<<(n + 127) / 128, 256, kInv128Smem, s1>>>(n, (const float*)p->d_F,
                                                                    (const float*)p->d_diagLinv, p->d_diagLinv128);
     const int nft = (n + kTT - 1) / kTT;
-    k_finalize<T><<<nft * (nft + 1) / 2, 256, 0, s0>>>(n, F, (const T*)p->d_diagL);
+    k_finalize<T><<<nft * (nft + 1) / 2, 256, 0, s0>>>(n, F, (const T*)p->d_diagL, 0, 0);
     IGS_CUDA(cudaEventRecord(evJ, s1));
     IGS_CUDA(cudaStreamWaitEvent(s0, evJ, 0));
     IGS_CUDA(cudaGetLastError());
@@ -1882,6 +1894,7 @@ static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, c
     float* F = (float*)p->d_F;
     IGS_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s0));
     bool pending = false, forked = false;
+    int mirrored = 0;                        // columns below which U = L^T is written (outer-block mirrors)
     cudaEvent_t evSide[2] = {evS, evJ};      // in-block side updates by parity (evJ recorded again at the end)
     for (int K0 = 0; K0 < n; K0 += kOB) {
         const int kbo = std::min(kOB, n - K0);
@@ -1925,6 +1938,12 @@ static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, c
             tcb_launch(n, F, img, K0, kbo, first, ntc - first, p->d_flag, s1);
             IGS_CUDA(cudaEventRecord(evB, s1));
             pending = true;
+            // the mirror of this outer block (its rows are final: later updates touch
+            // rows of later blocks only), on s1 after the update it must not delay
+            const int nft = (n + kTT - 1) / kTT;
+            k_finalize<float><<<dim3(nft - K0 / kTT, kbo / kTT), 256, 0, s1>>>(n, F, (const float*)p->d_diagL,
+                                                                             K0 / kTT, kbo / kTT);
+            mirrored = K0 + kbo;
         }
     }
     if (forked) {
@@ -1938,8 +1957,8 @@ static void issue_factor_blocked(igs_prob p, cudaStream_t s0, cudaStream_t s1, c
     if (p->d_diagLinv128)
         k_diag_inverse128<<<(n + 127) / 128, 256, kInv128Smem, s1>>>(n, (const float*)p->d_F,
                                                                    (const float*)p->d_diagLinv, p->d_diagLinv128);
-    const int nft = (n + kTT - 1) / kTT;
-    k_finalize<float><<<nft * (nft + 1) / 2, 256, 0, s0>>>(n, F, (const float*)p->d_diagL);
+    const int nft = (n + kTT - 1) / kTT, m = nft - mirrored / kTT;   // tile columns not yet mirrored
+    k_finalize<float><<<m * (m + 1) / 2, 256, 0, s0>>>(n, F, (const float*)p->d_diagL, mirrored / kTT, 0);
     IGS_CUDA(cudaEventRecord(evJ, s1));
     IGS_CUDA(cudaStreamWaitEvent(s0, evJ, 0));
     IGS_CUDA(cudaGetLastError());
@@ -1951,7 +1970,7 @@ static int factor_launches_blocked(int n) {
         const int kbo = std::min(kOB, n - K0);
         for (int k0 = K0; k0 < K0 + kbo; k0 += kNB) c += 1 + (k0 + 2 * kNB < K0 + kbo ? 1 : 0);
         const int rem = n - K0 - kbo;
-        if (rem > 0) c += (rem > kOB) ? 3 : 2;
+        if (rem > 0) c += (rem > kOB) ? 4 : 2;
     }
     return c;
 }
