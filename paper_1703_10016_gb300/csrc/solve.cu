@@ -336,8 +336,9 @@ __global__ void __launch_bounds__(panel_threads(NS, PARTS)) k_panel(int n, T* __
 // F[i][j] -= sum_l F[i][k0+l] F[j][k0+l] for i >= j >= k0 + kb, 64 x 64 tiles.
 // `mode` picks the tiles: 0 all, 1 the first tile column only (the next
 // panel's columns, updated first so that the next panel can start), 2 all
-// but the first tile column.  CTAs are numbered over the lower triangle of
-// tiles only.  The panel rows are staged row-major (coalesced 16-byte loads);
+// but the first tile column (CTAs numbered over the lower triangle of tiles
+// only), 3 the tile columns below gridDim.y, 4 the tile columns 1 ..
+// gridDim.y, all rows below.  The panel rows are staged row-major (coalesced 16-byte loads);
 // thread (tx, ty) owns rows ty + 16 r and columns tx + 16 c (r, c < 4) and
 // reads 16-byte vectors along l (odd row stride in 16-byte units: the
 // quarter-warps hit distinct banks).
@@ -1840,10 +1841,10 @@ static void issue_factor(igs_prob p, cudaStream_t s0, cudaStream_t s1, cudaEvent
 
 // MIXED tier, large n: the same panels, with the trailing update blocked by
 // outer column blocks of kOB = 8 panels.  Inside an outer block each panel
-// updates only the remaining columns of that block (SIMT): the next panel's
-// columns on s0 (mode 1), the block's later columns on a third stream s2
-// beside the next panel (mode 4; the next mode-1 update waits for it, both
-// touching the columns after the next panel); after the
+// updates only the remaining columns of that block: the next panel's columns
+// in the next panel itself, the block's later columns (SIMT, mode 4) on a
+// third stream s2 beside the next panel (the panel after next waits for it,
+// both touching its columns); after the
 // block's last panel the rest of the matrix is updated once with K = kOB on
 // the tensor cores.  Look-ahead as in issue_factor, one level up: the next
 // outer block's columns are updated first on s0; the rest of the outer update
